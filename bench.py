@@ -1,0 +1,319 @@
+"""Benchmark of the DENSER hot path on one GB300 (or N, one independent street per rank).
+
+One step = the whole hot path over one synthetic driving street: reset the map;
+for each of 200 depth maps (1241x376, f = 718 px, poses 0.5 m apart along a 100 m
+road) allocate blocks and fuse; 200 primal-dual iterations with the FP64 energy
+and gap at the end; extract keys, f, w, Omega and u.  Inputs are resident in HBM
+when the timed region starts.
+
+value = allocated voxels x primal-dual iterations / step time (voxel-updates/s per
+primal-dual iteration, fusion and extraction included in the time).
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same
+workload (the first frames of the same street, as many iterations as frames).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_VOXEL_ITER = {0: 48, 1: 28, 2: 28}  # FP32 / FP16 / BF16 storage of u, u_bar, p
+WORKLOAD = "driving street 100 m: 200 depth maps 1241x376, f=718 px, 0.1 m voxels, 8^3 blocks, mu 0.3 m, 200 PD iters"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_inputs(seed, frames=None):
+    from synth.scenes import street_scene
+    scene = street_scene(seed=seed)
+    depths = scene.depth_maps(frames)
+    return scene, depths
+
+
+# ------------------------------------------------------------- reference arm
+def oracle_sample(scene, depths, n, iters):
+    """Oracle alloc+fuse of n frames then ``iters`` iterations; returns (voxel-updates, seconds)."""
+    from oracle import denser_oracle as O
+    cam = scene.camera
+    K = O.Intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    t0 = time.perf_counter()
+    g = O.SparseGrid(O.Params())
+    for k in range(n):
+        O.alloc_blocks(g, depths[k], K, scene.poses[k])
+        O.fuse_depth(g, depths[k], K, scene.poses[k])
+    O.regularize(g, iters)
+    dt = time.perf_counter() - t0
+    return g.n_blocks * 512 * iters, dt, g.n_blocks
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = 2
+    scene, depths = make_inputs(0, range(n))
+    for _ in range(args.warmup):
+        oracle_sample(scene, depths, n, n)
+    tot_u, tot_t, nb = 0, 0.0, 0
+    for _ in range(args.steps):
+        u, t, nb = oracle_sample(scene, depths, n, n)
+        tot_u += u
+        tot_t += t
+    v = tot_u / tot_t
+    sample = f"first {n} frames of the street (alloc+fuse) then {n} PD iterations on their {nb} blocks, FP64 numpy"
+    line = {"impl": "reference", "metric": "voxel-updates/s per primal-dual iteration", "value": v,
+            "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "voxel-updates/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="denser", choices=["denser", "reference"])
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--frames", type=int, default=200)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1604_03734_gb300 import build as B
+    B.build()
+    from paper_1604_03734_gb300 import native as N
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # inputs: each rank fuses its own street (independent problems: weak scaling)
+    scene, depths_np = make_inputs(seed=rank, frames=range(args.frames))
+    cam = scene.camera
+    K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    depths_host = torch.from_numpy(depths_np).pin_memory()
+    depths_dev = depths_host.to(dev)
+    poses = scene.poses[:args.frames]
+    stream = torch.cuda.current_stream(dev)
+
+    m = N.DenserMap(device=local, max_blocks=1 << 17, hash_slots=1 << 20, precision=args.precision)
+    ctx = m.ctx
+
+    def pipeline(depth_src, outs):
+        N.denser_reset(ctx, stream)
+        for k in range(args.frames):
+            N.denser_alloc_blocks(ctx, depth_src[k], K, poses[k], 0, stream)
+            N.denser_fuse_depth(ctx, depth_src[k], K, poses[k], 0, stream)
+        st = N.denser_regularize(ctx, args.iters, 0.0, 0, stream)
+        N.denser_extract(ctx, outs["coords"], outs["f"], outs["w"], outs["omega"], outs["u"],
+                         outs["cap"], stream)
+        return st
+
+    def outputs(nb, device):
+        pin = device.type == "cpu"
+        mk = (lambda *s, dt: torch.empty(*s, dtype=dt, pin_memory=True)) if pin else \
+            (lambda *s, dt: torch.empty(*s, dtype=dt, device=device))
+        return {"coords": mk(nb, 4, dt=torch.int32), "f": mk(nb, 512, dt=torch.float32),
+                "w": mk(nb, 512, dt=torch.float32), "omega": mk(nb, 512, dt=torch.uint8),
+                "u": mk(nb, 512, dt=torch.float32), "cap": nb}
+
+    # size the outputs with one untimed pass
+    probe = {"coords": None, "f": None, "w": None, "omega": None, "u": None, "cap": 0}
+    pipeline(depths_dev, probe)
+    nb = N.denser_num_blocks(ctx, stream)
+    out_dev = outputs(nb, dev)
+    out_host = outputs(nb, torch.device("cpu"))
+
+    for _ in range(args.warmup):
+        pipeline(depths_dev, out_dev)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    l0 = N.denser_launch_count(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweep_ms, sweep_launches = 0.0, 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st = pipeline(depths_dev, out_dev)
+            sweep_ms += st.sweep_ms
+            sweep_launches += st.sweep_launches
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = N.denser_launch_count(ctx) - l0
+    step_ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+        dist.barrier()
+
+    nvox = nb * 512
+    updates = nvox * args.iters
+    value = updates * world / (step_ms / 1e3)
+
+    # end to end: host depth maps (pinned) in, host results out, through the C ABI
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        pipeline(depths_host, out_host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = 2 * args.frames * cam.width * cam.height * 4   # each map staged for alloc and for fusion
+    d2h = nb * (16 + 512 * (4 + 4 + 1 + 4))
+
+    hbm, peak_kind = peaks()
+    sweep_avg_ms = sweep_ms / max(sweep_launches, 1)
+    bpv = BYTES_PER_VOXEL_ITER[args.precision]
+    achieved = bpv * nvox / (sweep_avg_ms / 1e3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        n = 3
+        sc, dn = make_inputs(0, range(n))
+        u, t, nbs = oracle_sample(sc, dn, n, n)
+        cpu = {"value": u / t, "unit": "voxel-updates/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"first {n} frames of the street (alloc+fuse) then {n} PD iterations on their "
+                         f"{nbs} blocks, FP64 numpy, {t:.1f} s"}
+
+    line = {
+        "metric": "voxel-updates/s per primal-dual iteration", "value": value, "unit": "voxel-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f32", 1: "f16-storage/f32", 2: "bf16-storage/f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": args.frames, "iters": args.iters, "blocks": nb,
+                   "voxels": nvox, "parallelism": f"{world} independent streets" if world > 1 else "1 GPU",
+                   "l2": f"working set {bpv * nvox / 1e9:.2f} GB per sweep > 129 MB L2, no flush",
+                   "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),
+                   "pd_share_of_step": sweep_ms / args.steps / step_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "sweep_kernel<float>",
+                     "peak_kind": peak_kind, "bytes_per_voxel": bpv},
+        "e2e": {"value": updates * world / (e2e_ms / 1e3), "unit": "voxel-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

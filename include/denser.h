@@ -1,0 +1,190 @@
+/*
+ * denser.h -- C ABI of the DENSER hot path on one GPU (sm_103a).
+ *
+ * The library fuses depth maps into a truncated signed-distance field held in
+ * a hashing voxel grid of 8x8x8 voxel blocks, and regularises it with the
+ * Omega-aware total-variation primal-dual solver of the paper
+ * (Tanner, Pinies, Paz, Newman: "DENSER Cities", Section III).
+ *
+ * Conventions
+ *   - Camera frame: x right, y down, z forward.  A pose T_gc is a 4x4 float64
+ *     row-major matrix mapping camera coordinates to global coordinates.
+ *   - Voxel (i, j, k) has its centre at ((i+0.5)s, (j+0.5)s, (k+0.5)s), s the voxel
+ *     size.  It lives in block (floor(i/8), floor(j/8), floor(k/8)) at local offset
+ *     l = lx + 8*ly + 64*lz, lx = i - 8*floor(i/8).
+ *   - A block is identified by (segment, bx, by, bz); blocks of different segments
+ *     are never neighbours.  segment in [0, 126]; |bx|, |by|, |bz| < 2^18.
+ *   - Per-voxel fields are stored block-major: field[block][512].  The dual field p
+ *     is stored component-major: p[3][block][512].
+ *   - Block indices: every allocation call appends its new blocks in ascending
+ *     (segment, bz, by, bx) order, after all blocks allocated earlier.
+ *   - Depth maps are float32 [height][width]; a pixel is valid when finite and > 0.
+ *
+ * Pointers
+ *   Every buffer argument may be device memory or host memory (pinned or
+ *   pageable); the library looks the pointer up with cudaPointerGetAttributes and
+ *   stages host memory through its own device buffers.  The caller owns every
+ *   buffer it passes; the context owns the hash table, the block pool and the
+ *   primal-dual state.
+ *
+ * Streams and errors
+ *   `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls enqueue
+ *   work on it and return without waiting unless stated.  Every call returns 0
+ *   (DENSER_OK) or a negative DENSER_ERR_* code and sets a message readable with
+ *   denser_last_error.  Argument errors leave the context unchanged.  Errors
+ *   detected on the device (hash or pool full, coordinates out of range, a wait
+ *   that ran out) are sticky: they are reported by the next call that waits for
+ *   the stream (denser_sync, denser_alloc_blocks with n_new_out, denser_regularize,
+ *   denser_energy, denser_extract*, denser_load_*) and are cleared by denser_reset.
+ *   A context is used by one host thread at a time.
+ */
+#ifndef DENSER_H
+#define DENSER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DENSER_OK 0
+#define DENSER_ERR_INVALID_ARG (-1)
+#define DENSER_ERR_HASH_FULL (-2)   /* a key found no free slot within the probe limit */
+#define DENSER_ERR_POOL_FULL (-3)   /* more blocks than max_blocks (or max_new_blocks per call) */
+#define DENSER_ERR_CUDA (-4)        /* a CUDA runtime call failed; see denser_last_error */
+#define DENSER_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define DENSER_ERR_RANGE (-6)       /* a block coordinate outside +-2^18 or a bad segment */
+
+#define DENSER_FP32 0
+#define DENSER_FP16 1
+#define DENSER_BF16 2
+
+typedef struct denser_ctx denser_ctx;
+
+/* Method constants and capacities.  Defaults (denser_default_params): Table I of
+ * the paper, 10 cm voxels: lambda 0.8, sigma 0.5, tau 1/6, theta 1.0; mu 0.3 m. */
+typedef struct {
+    double voxel_size;        /* s, metres */
+    double mu;                /* truncation distance behind the surface, metres (Eq. 1) */
+    double lambda;            /* data-term weight (Eq. 2) */
+    double sigma;             /* dual step sigma_p (Section III-C, step 2) */
+    double tau;               /* primal step (Section III-C, step 3) */
+    double theta;             /* relaxation (Section III-C, step 4) */
+    uint32_t hash_slots;      /* power of two, > max_blocks */
+    uint32_t max_blocks;      /* block pool capacity */
+    uint32_t max_new_blocks;  /* new blocks one allocation call may add (0: max_blocks) */
+    int32_t precision;        /* DENSER_FP32 / FP16 / BF16 storage of u, u_bar, p */
+    int32_t gap_every;        /* evaluate the primal-dual gap every this many iterations (0: never) */
+    int32_t reserved;
+} denser_params;
+
+typedef struct {
+    double fx, fy, cx, cy;    /* pixels; pixel (x, y) covers [x, x+1) x [y, y+1) */
+    int32_t width, height;
+} denser_intrinsics;
+
+typedef struct {
+    int32_t iters;            /* iterations run by this call */
+    int32_t converged;        /* 1 when gap/|primal| <= gap_tol was reached */
+    double primal;            /* P(u) after the last iteration (FP64 reduction) */
+    double dual;              /* D(p) after the last iteration */
+    double gap;               /* primal - dual */
+    double rel_gap;           /* gap / |primal| */
+    double sweep_ms;          /* device time of the primal-dual sweeps (CUDA events) */
+    double total_ms;          /* device time of the whole call */
+    int32_t sweep_launches;   /* sweep kernel launches timed in sweep_ms */
+    int32_t gap_evals;        /* gap evaluations done inside the loop */
+    int64_t n_blocks;         /* allocated blocks */
+    int64_t n_omega;          /* voxels in Omega (observed) */
+} denser_reg_stats;
+
+/* Fills *p with the defaults above (hash 2^20 slots, 65536 blocks, FP32). */
+void denser_default_params(denser_params* p);
+
+/* Creates a context on CUDA device `device` and allocates its pool, hash table and
+ * state (about 46 B x 512 per block of capacity in FP32).  *out receives the context. */
+int denser_create(const denser_params* params, int32_t device, denser_ctx** out);
+
+/* Frees the context and everything it owns.  NULL is ignored. */
+void denser_destroy(denser_ctx* ctx);
+
+/* Empties the map (no blocks), zeroes the state and clears sticky errors. */
+int denser_reset(denser_ctx* ctx, void* stream);
+
+/* Message of the last error on this context ("" if none).  Valid until the next call. */
+const char* denser_last_error(const denser_ctx* ctx);
+
+/* Waits for `stream` and returns the sticky device error, if any. */
+int denser_sync(denser_ctx* ctx, void* stream);
+
+/* Allocation (Section III-A, "Fusing Data"): every block that holds a sample of a
+ * valid pixel's ray at depths z = d + n*s/2, n = -N..N, N = ceil(mu/(s/2)), z > 0,
+ * is allocated (f = w = 0) if absent.  Sample positions and block keys are computed
+ * in float64 in the order the oracle states (bit-exact block sets and indices).
+ * depth: float32 [height][width]; K: intrinsics; T_gc: 16 float64 (host memory);
+ * segment: block-key segment.  n_new_out (host, may be NULL): number of new blocks;
+ * when non-NULL the call waits for the stream. */
+int denser_alloc_blocks(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
+                        const double T_gc[16], int32_t segment, void* stream,
+                        int32_t* n_new_out);
+
+/* Projective fusion, Eq. 1 (Section III-A, steps 1-4): every allocated voxel of
+ * `segment` is projected into the depth map (nearest pixel = floor of the
+ * projection); where the pixel is valid and u_SDF = d - z_c >= -mu, w += 1 and
+ * f = (min(1, u_SDF/mu) + w_old f_old) / w.  The update decision is taken in
+ * float64 (bit-exact with the oracle); f is accumulated in float32. */
+int denser_fuse_depth(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
+                      const double T_gc[16], int32_t segment, void* stream);
+
+/* Regularisation (Section III-B/C): Chambolle-Pock iterations on the Omega-aware
+ * TV-L2 energy over the allocated blocks, Omega = {w > 0}:
+ *   p <- P(p + sigma grad_Omega u_bar),  P(q) = q / max(1, |q|_2)      (Eq. 3)
+ *   u <- (u + tau div_Omega p + tau lambda w f) / (1 + tau lambda w)  on Omega (Eq. 4)
+ *   u_bar <- u + theta (u - u_old)
+ * start: 0 = from p = u = u_bar = 0 (step 1), 1 = resume from the current state.
+ * Runs max_iters iterations, or stops earlier once gap/|P| <= gap_tol (gap_tol > 0
+ * and params.gap_every > 0).  Waits for the stream when `out` is non-NULL or a gap
+ * check is due; `out` (host, may be NULL) receives the statistics. */
+int denser_regularize(denser_ctx* ctx, int32_t max_iters, double gap_tol, int32_t start,
+                      void* stream, denser_reg_stats* out);
+
+/* FP64 primal and dual energies of the current state (waits for the stream):
+ *   P(u) = sum_Omega |grad u|_2 + (lambda/2) sum_Omega w (u - f)^2
+ *   D(p) = sum_Omega [ -f div p - (div p)^2 / (2 lambda w) ]
+ * primal, dual: host pointers (either may be NULL). */
+int denser_energy(denser_ctx* ctx, double* primal, double* dual, void* stream);
+
+/* Copies the map out in block-index order (waits for the stream).  Any output may
+ * be NULL.  coords: int32 [n][4] (segment, bx, by, bz); f, w, u: float32 [n][512];
+ * omega: uint8 [n][512] (1 = observed).  capacity_blocks: rows the outputs hold;
+ * fewer than the map's blocks is DENSER_ERR_INVALID_ARG.  n_blocks_out: host. */
+int denser_extract(denser_ctx* ctx, int32_t* coords, float* f, float* w, uint8_t* omega,
+                   float* u, int64_t capacity_blocks, int64_t* n_blocks_out, void* stream);
+
+/* Copies the relaxed primal u_bar [n][512] and the dual p [3][n][512] out (float32,
+ * converted from the storage precision).  Either may be NULL. */
+int denser_extract_dual(denser_ctx* ctx, float* u_bar, float* p, int64_t capacity_blocks,
+                        void* stream);
+
+/* Appends n blocks with the given coordinates (int32 [n][4]) and fusion state
+ * (f, w float32 [n][512]; NULL = zeros) in the given order, with zero primal-dual
+ * state.  A coordinate already in the map is DENSER_ERR_INVALID_ARG. */
+int denser_load_blocks(denser_ctx* ctx, const int32_t* coords, const float* f, const float* w,
+                       int64_t n, void* stream);
+
+/* Overwrites the primal-dual state of all n = n_blocks blocks: u, u_bar [n][512],
+ * p [3][n][512] float32 (converted to the storage precision).  NULL = zeros. */
+int denser_load_state(denser_ctx* ctx, const float* u, const float* u_bar, const float* p,
+                      int64_t n, void* stream);
+
+/* Number of allocated blocks (waits for the stream); negative on error. */
+int64_t denser_num_blocks(denser_ctx* ctx, void* stream);
+
+/* Kernels this context has launched since it was created. */
+uint64_t denser_launch_count(const denser_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DENSER_H */

@@ -1,0 +1,313 @@
+// Block allocation into the hashing voxel grid (Section III-A, "Fusing Data").
+//
+// One allocation call runs five kernels on the caller's stream, with every count
+// kept on the device (no host round trip):
+//   alloc_keys    one thread per pixel; the band samples of the pixel's ray give block
+//                 keys (float64, fixed operation order); warp peers with the same key
+//                 elect one leader (match.any) that inserts it by CAS into the open-
+//                 addressing table and appends it to the call's new-key list;
+//   sort_chunks   bitonic sort of the new keys, kSortChunk keys per CTA in shared memory;
+//   rank_assign   global rank of each new key = its rank in its chunk plus a binary
+//                 search in every other chunk; block index = blocks so far + rank, which
+//                 makes indices independent of insertion order;
+//   pool_init     zero the new blocks' fields;
+//   commit        publish the new block count.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace denser {
+
+namespace {
+
+struct AllocArgs {
+    double fx, fy, cx, cy;
+    double h;   // sample spacing s/2
+    double bs;  // block size 8 s
+    double R[9];
+    double t[3];
+    int W, H, N, seg;
+};
+
+__device__ inline void report(int32_t* counters, int32_t bit) { atomicOr(counters + kErrorBits, bit); }
+
+// Inserts `key`; returns true if this call created it.
+__device__ bool hash_insert(const DeviceMap& m, unsigned long long key) {
+    const uint32_t h = hash_key(key);
+    for (int i = 0; i < kMaxProbe; ++i) {
+        const uint32_t slot = (h + (uint32_t)i) & m.slot_mask;
+        unsigned long long cur = __ldcg(m.hash_keys + slot);
+        if (cur == key) return false;
+        if (cur == kEmptyKey) {
+            cur = atomicCAS(m.hash_keys + slot, kEmptyKey, key);
+            if (cur == kEmptyKey) {
+                const int pos = atomicAdd(m.counters + kNumNew, 1);
+                if (pos < (int)m.max_new) {
+                    m.new_keys[pos] = key;
+                    m.new_slots[pos] = slot;
+                } else {
+                    report(m.counters, kErrNewFull);
+                }
+                return true;
+            }
+            if (cur == key) return false;
+        }
+    }
+    report(m.counters, kErrHashFull);
+    return false;
+}
+
+// Block key of band sample n of pixel (x, y) with depth d, or kEmptyKey when z <= 0.
+// The float64 operations follow the oracle's order one by one; the _rn intrinsics keep
+// the compiler from contracting them into fused multiply-adds.
+__device__ unsigned long long sample_key(const AllocArgs& a, int x, int y, double d, int n, bool* range_err) {
+    const double z = __dadd_rn(d, __dmul_rn((double)n, a.h));
+    if (!(z > 0.0)) return kEmptyKey;
+    const double uu = __dsub_rn(__dadd_rn((double)x, 0.5), a.cx);
+    const double vv = __dsub_rn(__dadd_rn((double)y, 0.5), a.cy);
+    const double X = __ddiv_rn(__dmul_rn(uu, z), a.fx);
+    const double Y = __ddiv_rn(__dmul_rn(vv, z), a.fy);
+    const double Z = z;
+    double k[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double g = __dadd_rn(
+            __dadd_rn(__dadd_rn(__dmul_rn(a.R[3 * r + 0], X), __dmul_rn(a.R[3 * r + 1], Y)), __dmul_rn(a.R[3 * r + 2], Z)),
+            a.t[r]);
+        k[r] = floor(__ddiv_rn(g, a.bs));
+    }
+    if (!(k[0] >= -kCoordBias && k[0] < kCoordBias && k[1] >= -kCoordBias && k[1] < kCoordBias &&
+          k[2] >= -kCoordBias && k[2] < kCoordBias)) {
+        *range_err = true;
+        return kEmptyKey;
+    }
+    return pack_key(a.seg, (int32_t)k[0], (int32_t)k[1], (int32_t)k[2]);
+}
+
+__global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
+    const int npix = a.W * a.H;
+    const int lane = threadIdx.x & 31;
+    bool range_err = false;
+    // The loop bound is warp-uniform so every lane reaches the warp collectives.
+    for (int base = blockIdx.x * blockDim.x; base < npix; base += gridDim.x * blockDim.x) {
+        const int pix = base + (int)threadIdx.x;
+        float dv = pix < npix ? __ldg(depth + pix) : 0.0f;
+        const bool valid = pix < npix && isfinite(dv) && dv > 0.0f;
+        const int x = pix % a.W, y = pix / a.W;
+        unsigned long long last = kEmptyKey;
+        for (int n = -a.N; n <= a.N; ++n) {
+            unsigned long long key = kEmptyKey;
+            if (valid) {
+                key = sample_key(a, x, y, (double)dv, n, &range_err);
+                if (key == last) key = kEmptyKey;  // consecutive samples in one block
+                else if (key != kEmptyKey) last = key;
+            }
+            const unsigned active = __ballot_sync(0xffffffffu, key != kEmptyKey);
+            if (key != kEmptyKey) {
+                const unsigned peers = __match_any_sync(active, key);
+                if (lane == __ffs(peers) - 1) hash_insert(m, key);
+            }
+        }
+    }
+    if (range_err) report(m.counters, kErrRange);
+}
+
+__global__ void __launch_bounds__(1024) sort_chunks_kernel(DeviceMap m) {
+    __shared__ unsigned long long sk[kSortChunk];
+    __shared__ uint32_t ss[kSortChunk];
+    const int n = min(m.counters[kNumNew], (int)m.max_new);
+    const int base = blockIdx.x * kSortChunk;
+    if (base >= n) return;
+    const int cnt = min(kSortChunk, n - base);
+    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+        sk[i] = i < cnt ? m.new_keys[base + i] : kEmptyKey;
+        ss[i] = i < cnt ? m.new_slots[base + i] : 0u;
+    }
+    __syncthreads();
+    for (int k = 2; k <= kSortChunk; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long a = sk[i], b = sk[ixj];
+                    if ((a > b) == up) {
+                        sk[i] = b;
+                        sk[ixj] = a;
+                        const uint32_t t = ss[i];
+                        ss[i] = ss[ixj];
+                        ss[ixj] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        m.new_keys[base + i] = sk[i];
+        m.new_slots[base + i] = ss[i];
+    }
+}
+
+__global__ void rank_assign_kernel(DeviceMap m) {
+    const int n = min(m.counters[kNumNew], (int)m.max_new);
+    const int nb = m.counters[kNumBlocks];
+    const int nchunks = (n + kSortChunk - 1) / kSortChunk;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long key = m.new_keys[i];
+        const int c = i / kSortChunk;
+        long long rank = i - c * kSortChunk;
+        for (int c2 = 0; c2 < nchunks; ++c2) {
+            if (c2 == c) continue;
+            int lo = c2 * kSortChunk, hi = min(lo + kSortChunk, n);
+            const int first = lo;
+            while (lo < hi) {  // lower bound
+                const int mid = (lo + hi) >> 1;
+                if (m.new_keys[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            rank += lo - first;
+        }
+        const long long idx = nb + rank;
+        const uint32_t slot = m.new_slots[i];
+        if (idx < (long long)m.max_blocks) {
+            int32_t s, x, y, z;
+            unpack_key(key, &s, &x, &y, &z);
+            reinterpret_cast<int4*>(m.coords)[idx] = make_int4(s, x, y, z);
+            m.hash_vals[slot] = (int32_t)idx;
+        } else {
+            m.hash_vals[slot] = -2;
+            report(m.counters, kErrPoolFull);
+        }
+    }
+}
+
+struct ZeroRegions {
+    char* base[11];
+    size_t esize[11];
+};
+
+// Zeroes blocks [first, first + count) of every per-voxel field; first/count come from
+// the device counters when `from_counters` is set (allocation) or from the arguments.
+__global__ void zero_blocks_kernel(DeviceMap m, ZeroRegions z, int nreg, int from_counters, long long first_arg,
+                                   long long count_arg) {
+    long long first = first_arg, count = count_arg;
+    if (from_counters) {
+        const int n = min(m.counters[kNumNew], (int)m.max_new);
+        first = m.counters[kNumBlocks];
+        count = min((long long)n, (long long)m.max_blocks - first);
+    }
+    if (count <= 0) return;
+    for (int r = 0; r < nreg; ++r) {
+        const size_t bytes_per_block = (size_t)kBlockVoxels * z.esize[r];
+        uint4* p = reinterpret_cast<uint4*>(z.base[r] + (size_t)first * bytes_per_block);
+        const size_t n16 = (size_t)count * bytes_per_block / 16;
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+            p[i] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+__global__ void commit_kernel(DeviceMap m) {
+    const int inserted = m.counters[kNumNew];
+    const int n = min(inserted, (int)m.max_new);
+    const int nb = m.counters[kNumBlocks];
+    const int added = (int)min((long long)n, (long long)m.max_blocks - nb);
+    m.counters[kLastNew] = added;
+    m.counters[kNumBlocks] = nb + added;
+    m.counters[kNumNew] = 0;
+}
+
+__global__ void load_blocks_kernel(DeviceMap m, const int32_t* __restrict__ coords, long long n, long long base) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int4 c = reinterpret_cast<const int4*>(coords)[i];
+        if (!key_in_range(c.x, c.y, c.z, c.w)) {
+            report(m.counters, kErrRange);
+            continue;
+        }
+        const unsigned long long key = pack_key(c.x, c.y, c.z, c.w);
+        const uint32_t h = hash_key(key);
+        bool done = false;
+        for (int p = 0; p < kMaxProbe && !done; ++p) {
+            const uint32_t slot = (h + (uint32_t)p) & m.slot_mask;
+            const unsigned long long prev = atomicCAS(m.hash_keys + slot, kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                m.hash_vals[slot] = (int32_t)(base + i);
+                reinterpret_cast<int4*>(m.coords)[base + i] = c;
+                done = true;
+            } else if (prev == key) {
+                report(m.counters, kErrDuplicate);
+                done = true;
+            }
+        }
+        if (!done) report(m.counters, kErrHashFull);
+    }
+}
+
+__global__ void set_count_kernel(DeviceMap m, int32_t n) { m.counters[kNumBlocks] = n; }
+
+ZeroRegions all_regions(denser_ctx* c, int* nreg) {
+    ZeroRegions z;
+    const size_t mb = (size_t)c->d.max_blocks * kBlockVoxels;
+    int r = 0;
+    z.base[r] = (char*)c->d.f, z.esize[r++] = 4;
+    z.base[r] = (char*)c->d.w, z.esize[r++] = 4;
+    z.base[r] = (char*)c->d.u, z.esize[r++] = c->elem_size;
+    for (int k = 0; k < 2; ++k) z.base[r] = (char*)c->d.ub[k], z.esize[r++] = c->elem_size;
+    for (int k = 0; k < 2; ++k)
+        for (int a = 0; a < 3; ++a) z.base[r] = (char*)c->d.p[k] + a * mb * c->elem_size, z.esize[r++] = c->elem_size;
+    *nreg = r;
+    return z;
+}
+
+}  // namespace
+
+int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, const double* T, int32_t segment,
+                 cudaStream_t s) {
+    AllocArgs a;
+    a.fx = K->fx, a.fy = K->fy, a.cx = K->cx, a.cy = K->cy;
+    a.h = 0.5 * c->prm.voxel_size;
+    a.bs = 8.0 * c->prm.voxel_size;
+    for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) a.R[3 * r + q] = T[4 * r + q];
+        a.t[r] = T[4 * r + 3];
+    }
+    a.W = K->width, a.H = K->height;
+    a.N = (int)ceil(c->prm.mu / a.h - 1e-9);
+    a.seg = segment;
+    const int npix = a.W * a.H;
+    alloc_keys_kernel<<<grid_for(c->sm_count, npix, 256, 8), 256, 0, s>>>(depth, a, c->d);
+    const int chunks = (int)((c->d.max_new + kSortChunk - 1) / kSortChunk);
+    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->d);
+    rank_assign_kernel<<<grid_for(c->sm_count, c->d.max_new, 256, 4), 256, 0, s>>>(c->d);
+    int nreg;
+    ZeroRegions z = all_regions(c, &nreg);
+    zero_blocks_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d, z, nreg, 1, 0, 0);
+    commit_kernel<<<1, 1, 0, s>>>(c->d);
+    c->launches += 5;
+    c->nbr_valid_blocks = -1;
+    return cuda_check(c, cudaGetLastError(), "allocation kernels");
+}
+
+int launch_load_blocks(denser_ctx* c, const int32_t* coords_dev, int64_t n, int64_t base, cudaStream_t s) {
+    load_blocks_kernel<<<grid_for(c->sm_count, n, 256, 4), 256, 0, s>>>(c->d, coords_dev, n, base);
+    int nreg;
+    ZeroRegions z = all_regions(c, &nreg);
+    zero_blocks_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d, z, nreg, 0, base, n);
+    set_count_kernel<<<1, 1, 0, s>>>(c->d, (int32_t)(base + n));
+    c->launches += 3;
+    c->nbr_valid_blocks = -1;
+    return cuda_check(c, cudaGetLastError(), "load_blocks kernels");
+}
+
+int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s) {
+    int nreg;
+    ZeroRegions z = all_regions(c, &nreg);
+    // skip f and w (regions 0, 1)
+    ZeroRegions zs;
+    for (int r = 2; r < nreg; ++r) zs.base[r - 2] = z.base[r], zs.esize[r - 2] = z.esize[r];
+    zero_blocks_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d, zs, nreg - 2, 0, first_block, n_blocks);
+    c->launches += 1;
+    return cuda_check(c, cudaGetLastError(), "zero state kernel");
+}
+
+}  // namespace denser

@@ -1,0 +1,546 @@
+// C ABI of the DENSER hot path: context, argument checks, host/device staging,
+// the regularisation loop and the copies out.  The kernels live in alloc.cu,
+// fuse.cu and regularize.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+
+using namespace denser;
+
+namespace denser {
+
+int set_error(denser_ctx* c, int code, const std::string& m) {
+    if (c) c->msg = m;
+    return code;
+}
+
+int cuda_check(denser_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return DENSER_OK;
+    return set_error(c, DENSER_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace denser
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure_stage(denser_ctx* c, size_t bytes) {
+    if (c->stage_bytes >= bytes) return DENSER_OK;
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    int rc = cuda_check(c, cudaMalloc(&c->stage, bytes), "cudaMalloc(stage)");
+    if (rc) return rc;
+    c->stage_bytes = bytes;
+    return DENSER_OK;
+}
+
+int ensure_conv(denser_ctx* c, size_t bytes) {
+    if (c->conv_bytes >= bytes) return DENSER_OK;
+    if (c->conv_scratch) cudaFree(c->conv_scratch);
+    c->conv_scratch = nullptr;
+    c->conv_bytes = 0;
+    int rc = cuda_check(c, cudaMalloc(&c->conv_scratch, bytes), "cudaMalloc(convert scratch)");
+    if (rc) return rc;
+    c->conv_bytes = bytes;
+    return DENSER_OK;
+}
+
+// Returns a device pointer holding `bytes` of `src`: src itself when it is device
+// memory, else a copy in the context's staging buffer.
+int device_input(denser_ctx* c, const void* src, size_t bytes, cudaStream_t s, const void** out) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return DENSER_OK;
+    }
+    int rc = ensure_stage(c, bytes);
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemcpyAsync(c->stage, src, bytes, cudaMemcpyDefault, s), "copy input to device");
+    if (rc) return rc;
+    *out = c->stage;
+    return DENSER_OK;
+}
+
+int device_error_code(denser_ctx* c, int32_t bits) {
+    if (!bits) return DENSER_OK;
+    if (bits & kErrHashFull) return set_error(c, DENSER_ERR_HASH_FULL, "hash table full (probe limit reached)");
+    if (bits & (kErrPoolFull | kErrNewFull))
+        return set_error(c, DENSER_ERR_POOL_FULL, "block pool or per-call new-block capacity exhausted");
+    if (bits & kErrRange) return set_error(c, DENSER_ERR_RANGE, "block coordinate out of range (|b| >= 2^18)");
+    if (bits & kErrTimeout) return set_error(c, DENSER_ERR_TIMEOUT, "device-side wait gave up");
+    if (bits & kErrDuplicate) return set_error(c, DENSER_ERR_INVALID_ARG, "block already present in the map");
+    return set_error(c, DENSER_ERR_CUDA, "unknown device error bits");
+}
+
+// Waits for the stream and refreshes the host copy of the counters.
+int read_counters(denser_ctx* c, cudaStream_t s) {
+    int rc = cuda_check(c, cudaMemcpyAsync(c->h_counters, c->d.counters, kNumCounters * sizeof(int32_t),
+                                           cudaMemcpyDeviceToHost, s),
+                        "read counters");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+    if (rc) return rc;
+    return device_error_code(c, c->h_counters[kErrorBits]);
+}
+
+bool valid_intrinsics(const denser_intrinsics* K) {
+    return K && K->width > 0 && K->height > 0 && (int64_t)K->width * K->height < (1ll << 31) &&
+           isfinite(K->fx) && isfinite(K->fy) && isfinite(K->cx) && isfinite(K->cy) && K->fx > 0 && K->fy > 0;
+}
+
+bool valid_pose(const double* T) {
+    if (!T) return false;
+    for (int i = 0; i < 16; ++i)
+        if (!isfinite(T[i])) return false;
+    return T[12] == 0.0 && T[13] == 0.0 && T[14] == 0.0 && T[15] == 1.0;
+}
+
+template <typename F>
+int guarded(denser_ctx* c, F&& fn) {
+    if (!c) return DENSER_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    c->msg.clear();
+    return fn();
+}
+
+int copy_out(denser_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t s, const char* what) {
+    return cuda_check(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s), what);
+}
+
+// Copies a stored-precision field out as float32.
+int copy_state_out(denser_ctx* c, float* dst, const void* src, int64_t n, cudaStream_t s) {
+    if (c->prm.precision == DENSER_FP32) return copy_out(c, dst, src, (size_t)n * 4, s, "copy state out");
+    int rc = ensure_conv(c, (size_t)n * 4);
+    if (rc) return rc;
+    rc = launch_convert_state(c, src, c->conv_scratch, n, true, s);
+    if (rc) return rc;
+    return copy_out(c, dst, c->conv_scratch, (size_t)n * 4, s, "copy state out");
+}
+
+int copy_state_in(denser_ctx* c, void* dst, const float* src, int64_t n, cudaStream_t s) {
+    if (!src) return cuda_check(c, cudaMemsetAsync(dst, 0, (size_t)n * c->elem_size, s), "zero state");
+    if (c->prm.precision == DENSER_FP32) return copy_out(c, dst, src, (size_t)n * 4, s, "copy state in");
+    int rc = ensure_conv(c, (size_t)n * 4);
+    if (rc) return rc;
+    rc = copy_out(c, c->conv_scratch, src, (size_t)n * 4, s, "copy state in");
+    if (rc) return rc;
+    return launch_convert_state(c, c->conv_scratch, (float*)dst, n, false, s);
+}
+
+int energy_now(denser_ctx* c, int64_t nb, cudaStream_t s, double* P, double* D) {
+    int rc = launch_energy(c, nb, s);
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemcpyAsync(c->h_energy, c->d.partials + 2 * kEnergyGrid, 2 * sizeof(double),
+                                       cudaMemcpyDeviceToHost, s),
+                    "read energies");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+    if (rc) return rc;
+    *P = c->h_energy[0];
+    *D = c->h_energy[1];
+    return DENSER_OK;
+}
+
+void free_all(denser_ctx* c) {
+    void* ptrs[] = {c->d.hash_keys, c->d.hash_vals, c->d.coords, c->d.f, c->d.w, c->d.u, c->d.ub[0], c->d.ub[1],
+                    c->d.p[0], c->d.p[1], c->d.omega_bits, c->d.nbr, c->d.counters, c->d.new_keys,
+                    c->d.new_slots, c->d.visible, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_counters) cudaFreeHost(c->h_counters);
+    if (c->h_energy) cudaFreeHost(c->h_energy);
+}
+
+}  // namespace
+
+extern "C" {
+
+void denser_default_params(denser_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->voxel_size = 0.1;
+    p->mu = 0.3;
+    p->lambda = 0.8;
+    p->sigma = 0.5;
+    p->tau = 1.0 / 6.0;
+    p->theta = 1.0;
+    p->hash_slots = 1u << 20;
+    p->max_blocks = 65536;
+    p->max_new_blocks = 0;
+    p->precision = DENSER_FP32;
+    p->gap_every = 0;
+}
+
+int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
+    if (!prm || !out) return DENSER_ERR_INVALID_ARG;
+    *out = nullptr;
+    const denser_params& p = *prm;
+    if (!(p.voxel_size > 0) || !(p.mu > 0) || !(p.lambda > 0) || !(p.sigma > 0) || !(p.tau > 0) ||
+        !(p.theta >= 0) || !isfinite(p.voxel_size) || !isfinite(p.mu) || p.max_blocks == 0 ||
+        p.max_blocks > (1u << 30) / kBlockVoxels * 2 || p.hash_slots < 2 || (p.hash_slots & (p.hash_slots - 1)) ||
+        p.hash_slots <= p.max_blocks || p.precision < DENSER_FP32 || p.precision > DENSER_BF16 || p.gap_every < 0)
+        return DENSER_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DENSER_ERR_CUDA;
+    }
+    denser_ctx* c = new denser_ctx();
+    memset(&c->d, 0, sizeof(c->d));
+    c->prm = p;
+    c->device = device;
+    c->cur = 0;
+    c->nbr_valid_blocks = -1;
+    c->stage = nullptr, c->stage_bytes = 0, c->hstage = nullptr, c->hstage_bytes = 0;
+    c->omega_bytes = nullptr, c->conv_scratch = nullptr, c->conv_bytes = 0;
+    c->h_counters = nullptr, c->h_energy = nullptr;
+    c->launches = 0;
+    c->elem_size = p.precision == DENSER_FP32 ? 4 : 2;
+    DeviceGuard g(device);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    const size_t mb = p.max_blocks;
+    const size_t nv = mb * kBlockVoxels;
+    const size_t max_new = p.max_new_blocks ? std::min<size_t>(p.max_new_blocks, mb) : mb;
+    c->d.max_blocks = (uint32_t)mb;
+    c->d.max_new = (uint32_t)max_new;
+    c->d.slot_mask = p.hash_slots - 1;
+    struct Req {
+        void** ptr;
+        size_t bytes;
+    } reqs[] = {{(void**)&c->d.hash_keys, (size_t)p.hash_slots * 8},
+                {(void**)&c->d.hash_vals, (size_t)p.hash_slots * 4},
+                {(void**)&c->d.coords, mb * 16},
+                {(void**)&c->d.f, nv * 4},
+                {(void**)&c->d.w, nv * 4},
+                {(void**)&c->d.u, nv * c->elem_size},
+                {(void**)&c->d.ub[0], nv * c->elem_size},
+                {(void**)&c->d.ub[1], nv * c->elem_size},
+                {(void**)&c->d.p[0], 3 * nv * c->elem_size},
+                {(void**)&c->d.p[1], 3 * nv * c->elem_size},
+                {(void**)&c->d.omega_bits, mb * 64},
+                {(void**)&c->d.nbr, mb * kNeighbours * 4},
+                {(void**)&c->d.counters, kNumCounters * 4},
+                {(void**)&c->d.new_keys, max_new * 8},
+                {(void**)&c->d.new_slots, max_new * 4},
+                {(void**)&c->d.visible, mb * 4},
+                {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2) * 8}};
+    for (auto& r : reqs) {
+        if (cudaMalloc(r.ptr, r.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_all(c);
+            delete c;
+            return DENSER_ERR_CUDA;
+        }
+    }
+    if (cudaMallocHost((void**)&c->h_counters, kNumCounters * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_energy, 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return DENSER_ERR_CUDA;
+    }
+    if (denser_reset(c, nullptr) != DENSER_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return DENSER_ERR_CUDA;
+    }
+    *out = c;
+    return DENSER_OK;
+}
+
+void denser_destroy(denser_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        cudaDeviceSynchronize();
+        free_all(c);
+    }
+    delete c;
+}
+
+int denser_reset(denser_ctx* c, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc;
+        if ((rc = cuda_check(c, cudaMemsetAsync(c->d.hash_keys, 0xff, (size_t)c->prm.hash_slots * 8, s), "reset")))
+            return rc;
+        if ((rc = cuda_check(c, cudaMemsetAsync(c->d.hash_vals, 0xff, (size_t)c->prm.hash_slots * 4, s), "reset")))
+            return rc;
+        if ((rc = cuda_check(c, cudaMemsetAsync(c->d.counters, 0, kNumCounters * 4, s), "reset"))) return rc;
+        c->cur = 0;
+        c->nbr_valid_blocks = -1;
+        return DENSER_OK;
+    });
+}
+
+const char* denser_last_error(const denser_ctx* c) { return c ? c->msg.c_str() : "null context"; }
+
+int denser_sync(denser_ctx* c, void* stream) {
+    return guarded(c, [&]() -> int { return read_counters(c, (cudaStream_t)stream); });
+}
+
+int denser_alloc_blocks(denser_ctx* c, const float* depth, const denser_intrinsics* K, const double T_gc[16],
+                        int32_t segment, void* stream, int32_t* n_new_out) {
+    return guarded(c, [&]() -> int {
+        if (!depth || !valid_intrinsics(K) || !valid_pose(T_gc) || segment < 0 || segment > kMaxSegment)
+            return set_error(c, DENSER_ERR_INVALID_ARG, "alloc_blocks: bad depth, intrinsics, pose or segment");
+        cudaStream_t s = (cudaStream_t)stream;
+        const void* dd;
+        int rc = device_input(c, depth, (size_t)K->width * K->height * 4, s, &dd);
+        if (rc) return rc;
+        rc = launch_alloc(c, (const float*)dd, K, T_gc, segment, s);
+        if (rc) return rc;
+        if (n_new_out) {
+            rc = read_counters(c, s);
+            *n_new_out = c->h_counters[kLastNew];
+            return rc;
+        }
+        return DENSER_OK;
+    });
+}
+
+int denser_fuse_depth(denser_ctx* c, const float* depth, const denser_intrinsics* K, const double T_gc[16],
+                      int32_t segment, void* stream) {
+    return guarded(c, [&]() -> int {
+        if (!depth || !valid_intrinsics(K) || !valid_pose(T_gc) || segment < 0 || segment > kMaxSegment)
+            return set_error(c, DENSER_ERR_INVALID_ARG, "fuse_depth: bad depth, intrinsics, pose or segment");
+        cudaStream_t s = (cudaStream_t)stream;
+        const void* dd;
+        int rc = device_input(c, depth, (size_t)K->width * K->height * 4, s, &dd);
+        if (rc) return rc;
+        return launch_fuse(c, (const float*)dd, K, T_gc, segment, s);
+    });
+}
+
+int denser_regularize(denser_ctx* c, int32_t max_iters, double gap_tol, int32_t start, void* stream,
+                      denser_reg_stats* out) {
+    return guarded(c, [&]() -> int {
+        if (max_iters < 0 || !(gap_tol >= 0) || (start != 0 && start != 1))
+            return set_error(c, DENSER_ERR_INVALID_ARG, "regularize: bad max_iters, gap_tol or start");
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        const size_t nv = (size_t)nb * kBlockVoxels;
+        const size_t pstride_bytes = (size_t)c->d.max_blocks * kBlockVoxels * c->elem_size;
+        cudaEvent_t e0, e1, a0, a1;
+        cudaEventCreate(&e0), cudaEventCreate(&e1), cudaEventCreate(&a0), cudaEventCreate(&a1);
+        struct EvFree {
+            cudaEvent_t* e;
+            ~EvFree() {
+                for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+            }
+        };
+        cudaEvent_t evs[4] = {e0, e1, a0, a1};
+        EvFree ef{evs};
+        cudaEventRecord(e0, s);
+        rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s);
+        if (rc) return rc;
+        if (start == 0 && nb > 0) {
+            rc = cuda_check(c, cudaMemsetAsync(c->d.u, 0, nv * c->elem_size, s), "zero u");
+            if (!rc) rc = cuda_check(c, cudaMemsetAsync(c->d.ub[c->cur], 0, nv * c->elem_size, s), "zero u_bar");
+            for (int a = 0; a < 3 && !rc; ++a)
+                rc = cuda_check(c, cudaMemsetAsync((char*)c->d.p[c->cur] + a * pstride_bytes, 0, nv * c->elem_size, s),
+                                "zero p");
+            if (rc) return rc;
+        }
+        const bool check_gap = gap_tol > 0 && c->prm.gap_every > 0;
+        double sweep_ms = 0.0;
+        int launches = 0, gap_evals = 0, converged = 0, it = 0;
+        double P = NAN, D = NAN;
+        bool have_energy = false;
+        while (it < max_iters) {
+            int batch = max_iters - it;
+            if (check_gap) batch = std::min(batch, c->prm.gap_every - (it % c->prm.gap_every));
+            cudaEventRecord(a0, s);
+            for (int k = 0; k < batch; ++k) {
+                rc = launch_sweep(c, nb, s);
+                if (rc) return rc;
+            }
+            cudaEventRecord(a1, s);
+            it += batch;
+            launches += nb > 0 ? batch : 0;
+            const bool gap_due = check_gap && it % c->prm.gap_every == 0;
+            if (gap_due || out) {
+                // events complete once the stream reaches them
+                if ((rc = cuda_check(c, cudaEventSynchronize(a1), "event synchronize"))) return rc;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a0, a1);
+                sweep_ms += ms;
+            }
+            if (gap_due) {
+                if ((rc = energy_now(c, nb, s, &P, &D))) return rc;
+                have_energy = true;
+                ++gap_evals;
+                if ((P - D) <= gap_tol * fabs(P)) {
+                    converged = 1;
+                    break;
+                }
+            } else {
+                have_energy = false;
+            }
+        }
+        if (out) {
+            if (!have_energy && (rc = energy_now(c, nb, s, &P, &D))) return rc;
+            cudaEventRecord(e1, s);
+            if ((rc = read_counters(c, s))) return rc;
+            float tot = 0.f;
+            cudaEventElapsedTime(&tot, e0, e1);
+            memset(out, 0, sizeof(*out));
+            out->iters = it;
+            out->converged = converged || (gap_tol > 0 && (P - D) <= gap_tol * fabs(P));
+            out->primal = P;
+            out->dual = D;
+            out->gap = P - D;
+            out->rel_gap = P != 0 ? (P - D) / fabs(P) : 0.0;
+            out->sweep_ms = sweep_ms;
+            out->total_ms = tot;
+            out->sweep_launches = launches;
+            out->gap_evals = gap_evals;
+            out->n_blocks = nb;
+            out->n_omega = -1;
+        }
+        return DENSER_OK;
+    });
+}
+
+int denser_energy(denser_ctx* c, double* primal, double* dual, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if ((rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s))) return rc;
+        double P, D;
+        if ((rc = energy_now(c, nb, s, &P, &D))) return rc;
+        if (primal) *primal = P;
+        if (dual) *dual = D;
+        return DENSER_OK;
+    });
+}
+
+int denser_extract(denser_ctx* c, int32_t* coords, float* f, float* w, uint8_t* omega, float* u,
+                   int64_t capacity_blocks, int64_t* n_blocks_out, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if (n_blocks_out) *n_blocks_out = nb;
+        if ((coords || f || w || omega || u) && capacity_blocks < nb)
+            return set_error(c, DENSER_ERR_INVALID_ARG, "extract: capacity_blocks < number of blocks");
+        const size_t nv = (size_t)nb * kBlockVoxels;
+        if (nb == 0) return DENSER_OK;
+        if (coords && (rc = copy_out(c, coords, c->d.coords, (size_t)nb * 16, s, "copy coords"))) return rc;
+        if (f && (rc = copy_out(c, f, c->d.f, nv * 4, s, "copy f"))) return rc;
+        if (w && (rc = copy_out(c, w, c->d.w, nv * 4, s, "copy w"))) return rc;
+        if (u && (rc = copy_state_out(c, u, c->d.u, (int64_t)nv, s))) return rc;
+        if (omega) {
+            uint8_t* dst = omega;
+            if (!is_device_ptr(omega)) {
+                if ((rc = ensure_conv(c, nv))) return rc;
+                dst = (uint8_t*)c->conv_scratch;
+            }
+            if ((rc = launch_omega_bytes(c, nb, dst, s))) return rc;
+            if (dst != omega && (rc = copy_out(c, omega, dst, nv, s, "copy omega"))) return rc;
+        }
+        return cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+    });
+}
+
+int denser_extract_dual(denser_ctx* c, float* u_bar, float* p, int64_t capacity_blocks, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if ((u_bar || p) && capacity_blocks < nb)
+            return set_error(c, DENSER_ERR_INVALID_ARG, "extract_dual: capacity_blocks < number of blocks");
+        const int64_t nv = nb * kBlockVoxels;
+        if (nb == 0) return DENSER_OK;
+        if (u_bar && (rc = copy_state_out(c, u_bar, c->d.ub[c->cur], nv, s))) return rc;
+        if (p) {
+            const size_t pstride = (size_t)c->d.max_blocks * kBlockVoxels * c->elem_size;
+            for (int a = 0; a < 3; ++a)
+                if ((rc = copy_state_out(c, p + a * nv, (char*)c->d.p[c->cur] + a * pstride, nv, s))) return rc;
+        }
+        return cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+    });
+}
+
+int denser_load_blocks(denser_ctx* c, const int32_t* coords, const float* f, const float* w, int64_t n,
+                       void* stream) {
+    return guarded(c, [&]() -> int {
+        if (n < 0 || (n > 0 && !coords)) return set_error(c, DENSER_ERR_INVALID_ARG, "load_blocks: bad arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t base = c->h_counters[kNumBlocks];
+        if (base + n > (int64_t)c->d.max_blocks)
+            return set_error(c, DENSER_ERR_POOL_FULL, "load_blocks: more blocks than max_blocks");
+        if (n == 0) return DENSER_OK;
+        const void* cd;
+        if ((rc = device_input(c, coords, (size_t)n * 16, s, &cd))) return rc;
+        if ((rc = launch_load_blocks(c, (const int32_t*)cd, n, base, s))) return rc;
+        const size_t nv = (size_t)n * kBlockVoxels;
+        if (f && (rc = copy_out(c, c->d.f + (size_t)base * kBlockVoxels, f, nv * 4, s, "copy f in"))) return rc;
+        if (w && (rc = copy_out(c, c->d.w + (size_t)base * kBlockVoxels, w, nv * 4, s, "copy w in"))) return rc;
+        return read_counters(c, s);
+    });
+}
+
+int denser_load_state(denser_ctx* c, const float* u, const float* u_bar, const float* p, int64_t n, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if (n != nb) return set_error(c, DENSER_ERR_INVALID_ARG, "load_state: n must equal the number of blocks");
+        if (nb == 0) return DENSER_OK;
+        const int64_t nv = nb * kBlockVoxels;
+        if ((rc = copy_state_in(c, c->d.u, u, nv, s))) return rc;
+        if ((rc = copy_state_in(c, c->d.ub[c->cur], u_bar, nv, s))) return rc;
+        const size_t pstride = (size_t)c->d.max_blocks * kBlockVoxels * c->elem_size;
+        for (int a = 0; a < 3; ++a)
+            if ((rc = copy_state_in(c, (char*)c->d.p[c->cur] + a * pstride, p ? p + a * nv : nullptr, nv, s)))
+                return rc;
+        return read_counters(c, s);
+    });
+}
+
+int64_t denser_num_blocks(denser_ctx* c, void* stream) {
+    if (!c) return DENSER_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    int rc = read_counters(c, (cudaStream_t)stream);
+    if (rc) return rc;
+    return c->h_counters[kNumBlocks];
+}
+
+uint64_t denser_launch_count(const denser_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Internal declarations shared by the DENSER CUDA translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/denser.h"
+
+namespace denser {
+
+constexpr int kBlock = 8;
+constexpr int kBlockVoxels = 512;
+constexpr int kNeighbours = 12;
+constexpr int kMaxProbe = 512;             // linear-probe limit of the hash table
+constexpr int kSortChunk = 2048;           // keys sorted per CTA before the rank merge
+constexpr int kSweepThreads = 512;
+
+// ---------------------------------------------------------------- block keys
+// 64-bit key: bits 0-18 bx + 2^18, 19-37 by + 2^18, 38-56 bz + 2^18, 57-63 segment.
+// Ascending keys = ascending (segment, bz, by, bx).  Segment 127 is reserved, so the
+// all-ones word never is a key and marks an empty hash slot.
+constexpr int kCoordBits = 19;
+constexpr int32_t kCoordBias = 1 << 18;
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int32_t kMaxSegment = 126;
+
+__host__ __device__ inline bool key_in_range(int32_t seg, long long bx, long long by, long long bz) {
+    return seg >= 0 && seg <= kMaxSegment && bx >= -kCoordBias && bx < kCoordBias &&
+           by >= -kCoordBias && by < kCoordBias && bz >= -kCoordBias && bz < kCoordBias;
+}
+
+__host__ __device__ inline unsigned long long pack_key(int32_t seg, int32_t bx, int32_t by, int32_t bz) {
+    return (unsigned long long)(uint32_t)(bx + kCoordBias) |
+           ((unsigned long long)(uint32_t)(by + kCoordBias) << kCoordBits) |
+           ((unsigned long long)(uint32_t)(bz + kCoordBias) << (2 * kCoordBits)) |
+           ((unsigned long long)(uint32_t)seg << (3 * kCoordBits));
+}
+
+__host__ __device__ inline void unpack_key(unsigned long long k, int32_t* seg, int32_t* bx, int32_t* by,
+                                           int32_t* bz) {
+    const unsigned long long m = (1ull << kCoordBits) - 1;
+    *bx = (int32_t)(k & m) - kCoordBias;
+    *by = (int32_t)((k >> kCoordBits) & m) - kCoordBias;
+    *bz = (int32_t)((k >> (2 * kCoordBits)) & m) - kCoordBias;
+    *seg = (int32_t)(k >> (3 * kCoordBits));
+}
+
+// Spatial hash of Teschner et al. (large primes XORed), plus the segment.
+__host__ __device__ inline uint32_t hash_key(unsigned long long k) {
+    int32_t s, x, y, z;
+    unpack_key(k, &s, &x, &y, &z);
+    return ((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349669u) ^ ((uint32_t)z * 83492791u) ^
+           ((uint32_t)s * 2654435761u);
+}
+
+// --------------------------------------------------------- device-side words
+enum Counter {
+    kNumBlocks = 0,    // allocated blocks
+    kNumNew = 1,       // keys inserted by the running allocation call
+    kLastNew = 2,      // blocks added by the last allocation call
+    kErrorBits = 3,    // sticky error flags (ErrorBit)
+    kNumVisible = 4,   // blocks selected for the running fusion call
+    kDepthMaxBits = 5, // max valid depth of the running fusion call (float bits)
+    kNumCounters = 8
+};
+
+enum ErrorBit : int32_t {
+    kErrHashFull = 1,
+    kErrPoolFull = 2,
+    kErrNewFull = 4,
+    kErrRange = 8,
+    kErrTimeout = 16,
+    kErrDuplicate = 32,
+};
+
+// Storage of the primal-dual fields.
+template <typename T> struct Store;
+template <> struct Store<float> {
+    __device__ static float ld(const float* p) { return *p; }
+    __device__ static void st(float* p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    __device__ static float ld(const __half* p) { return __half2float(*p); }
+    __device__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// All device pointers of one context.
+struct DeviceMap {
+    unsigned long long* hash_keys;  // [slots]
+    int32_t* hash_vals;             // [slots] block index; -1 pending, -2 rejected
+    uint32_t slot_mask;
+    int32_t* coords;                // [max_blocks][4] (segment, bx, by, bz)
+    float* f;                       // [max_blocks][512]
+    float* w;                       // [max_blocks][512]
+    void* u;                        // [max_blocks][512] storage type
+    void* ub[2];                    // ping-pong u_bar
+    void* p[2];                     // ping-pong p, [3][max_blocks][512]
+    uint32_t* omega_bits;           // [max_blocks][16]
+    int32_t* nbr;                   // [max_blocks][12]
+    int32_t* counters;              // [kNumCounters]
+    unsigned long long* new_keys;   // [max_new] inserted keys of the running call
+    uint32_t* new_slots;            // [max_new]
+    int32_t* visible;               // [max_blocks] fusion work list
+    double* partials;               // [kEnergyGrid][2] energy partial sums
+    uint32_t max_blocks;
+    uint32_t max_new;
+};
+
+constexpr int kEnergyGrid = 1216;  // 8 CTAs per SM on 152 SMs
+
+}  // namespace denser
+
+// ------------------------------------------------------------------ the context
+struct denser_ctx {
+    denser_params prm;
+    int device;
+    int sm_count;
+    denser::DeviceMap d;
+    size_t elem_size;          // bytes per stored u / u_bar / p element
+    int cur;                   // which ping-pong buffer holds the current u_bar and p
+    int64_t nbr_valid_blocks;  // blocks covered by the neighbour table (-1: rebuild)
+    float* stage;              // device staging for host inputs
+    size_t stage_bytes;
+    void* hstage;              // pinned host staging for host outputs
+    size_t hstage_bytes;
+    uint8_t* omega_bytes;      // extract scratch
+    float* conv_scratch;       // float32 staging of converted state
+    size_t conv_bytes;
+    int32_t* h_counters;       // pinned copy of the device counters
+    double* h_energy;          // pinned [2]
+    unsigned long long launches;
+    std::string msg;
+};
+
+namespace denser {
+
+// Launchers implemented in the .cu files (all enqueue on `s`).
+int launch_alloc(denser_ctx* c, const float* depth_dev, const denser_intrinsics* K, const double* T,
+                 int32_t segment, cudaStream_t s);
+int launch_fuse(denser_ctx* c, const float* depth_dev, const denser_intrinsics* K, const double* T,
+                int32_t segment, cudaStream_t s);
+int launch_load_blocks(denser_ctx* c, const int32_t* coords_dev, int64_t n, int64_t base, cudaStream_t s);
+int launch_prepare_regularize(denser_ctx* c, int64_t n_blocks, bool rebuild_nbr, cudaStream_t s);
+int launch_sweep(denser_ctx* c, int64_t n_blocks, cudaStream_t s);
+int launch_energy(denser_ctx* c, int64_t n_blocks, cudaStream_t s);
+int launch_omega_bytes(denser_ctx* c, int64_t n_blocks, uint8_t* out, cudaStream_t s);
+int launch_convert_state(denser_ctx* c, const void* src, float* dst, int64_t n, bool to_float,
+                         cudaStream_t s);
+int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s);
+
+int set_error(denser_ctx* c, int code, const std::string& m);
+int cuda_check(denser_ctx* c, cudaError_t e, const char* what);
+
+}  // namespace denser
+
+namespace denser {
+
+// Lookup of a block key; returns the block index or -1 (absent, pending or rejected).
+__device__ inline int32_t hash_lookup(const DeviceMap& m, unsigned long long key) {
+    const uint32_t h = hash_key(key);
+    for (int i = 0; i < kMaxProbe; ++i) {
+        const uint32_t slot = (h + (uint32_t)i) & m.slot_mask;
+        const unsigned long long k = __ldcg(m.hash_keys + slot);
+        if (k == key) return __ldcg(m.hash_vals + slot);
+        if (k == kEmptyKey) return -1;
+    }
+    return -1;
+}
+
+// Neighbour slots of the 12-entry table: 6 faces, then the 6 (low, high) edges that
+// the fused primal-dual sweep reads.
+__host__ __device__ inline void neighbour_offset(int i, int* dx, int* dy, int* dz) {
+    const signed char t[kNeighbours][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {-1, 0, 0},
+                                           {0, -1, 0}, {0, 0, -1}, {-1, 1, 0}, {-1, 0, 1},
+                                           {1, -1, 0}, {0, -1, 1}, {1, 0, -1}, {0, 1, -1}};
+    *dx = t[i][0];
+    *dy = t[i][1];
+    *dz = t[i][2];
+}
+
+inline int grid_for(int sm_count, long long work, int threads, int per_sm) {
+    long long g = (work + threads - 1) / threads;
+    long long cap = (long long)sm_count * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace denser

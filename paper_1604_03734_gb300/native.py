@@ -1,0 +1,289 @@
+"""ctypes binding of libdenser.so: the C ABI of include/denser.h, same names.
+
+Argument marshalling only.  Every computation runs in the library's CUDA
+kernels; if the library is missing this module raises instead of falling back
+to anything else.  Buffers may be torch tensors (CPU or CUDA) or numpy arrays;
+they must be contiguous and of the dtype the C function documents.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+DENSER_OK = 0
+DENSER_ERR_INVALID_ARG = -1
+DENSER_ERR_HASH_FULL = -2
+DENSER_ERR_POOL_FULL = -3
+DENSER_ERR_CUDA = -4
+DENSER_ERR_TIMEOUT = -5
+DENSER_ERR_RANGE = -6
+DENSER_FP32, DENSER_FP16, DENSER_BF16 = 0, 1, 2
+
+# every symbol include/denser.h declares
+EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_reset",
+           "denser_last_error", "denser_sync", "denser_alloc_blocks", "denser_fuse_depth",
+           "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual",
+           "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count")
+
+
+class denser_params(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_double), ("mu", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("theta", ctypes.c_double),
+                ("hash_slots", ctypes.c_uint32), ("max_blocks", ctypes.c_uint32),
+                ("max_new_blocks", ctypes.c_uint32), ("precision", ctypes.c_int32),
+                ("gap_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class denser_intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
+                ("cy", ctypes.c_double), ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class denser_reg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("primal", ctypes.c_double),
+                ("dual", ctypes.c_double), ("gap", ctypes.c_double), ("rel_gap", ctypes.c_double),
+                ("sweep_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("sweep_launches", ctypes.c_int32), ("gap_evals", ctypes.c_int32),
+                ("n_blocks", ctypes.c_int64), ("n_omega", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DenserError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"denser error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_vp, _i32, _i64, _u64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_1604_03734_gb300.build.build()")
+        L = ctypes.CDLL(LIB)
+        P = ctypes.POINTER
+        sig = {
+            "denser_default_params": (None, [P(denser_params)]),
+            "denser_create": (_i32, [P(denser_params), _i32, P(_vp)]),
+            "denser_destroy": (None, [_vp]),
+            "denser_reset": (_i32, [_vp, _vp]),
+            "denser_last_error": (ctypes.c_char_p, [_vp]),
+            "denser_sync": (_i32, [_vp, _vp]),
+            "denser_alloc_blocks": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp, P(_i32)]),
+            "denser_fuse_depth": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp]),
+            "denser_regularize": (_i32, [_vp, _i32, _dbl, _i32, _vp, P(denser_reg_stats)]),
+            "denser_energy": (_i32, [_vp, P(_dbl), P(_dbl), _vp]),
+            "denser_extract": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, P(_i64), _vp]),
+            "denser_extract_dual": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+            "denser_load_blocks": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
+            "denser_load_state": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
+            "denser_num_blocks": (_i64, [_vp, _vp]),
+            "denser_launch_count": (_u64, [_vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------- marshalling
+def _ptr(buf, dtype=None):
+    """Raw address of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if buf is None:
+        return None
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffer must be C-contiguous")
+        if dtype is not None and buf.dtype != np.dtype(dtype):
+            raise TypeError(f"expected {np.dtype(dtype)}, got {buf.dtype}")
+        return buf.ctypes.data
+    import torch
+    if isinstance(buf, torch.Tensor):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None:
+            want = {np.float32: torch.float32, np.int32: torch.int32, np.uint8: torch.uint8,
+                    np.float64: torch.float64}[dtype]
+            if buf.dtype != want:
+                raise TypeError(f"expected {want}, got {buf.dtype}")
+        return buf.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(ctx, rc):
+    if rc != DENSER_OK:
+        msg = lib().denser_last_error(ctx)
+        raise DenserError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _pose(T):
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    return a, a.ctypes.data_as(ctypes.POINTER(_dbl))
+
+
+def intrinsics(fx, fy, cx, cy, width, height) -> denser_intrinsics:
+    return denser_intrinsics(float(fx), float(fy), float(cx), float(cy), int(width), int(height))
+
+
+# ------------------------------------------------------------ the C calls
+def denser_default_params(**overrides) -> denser_params:
+    p = denser_params()
+    lib().denser_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+def denser_create(params: denser_params, device: int = 0):
+    ctx = _vp()
+    rc = lib().denser_create(ctypes.byref(params), device, ctypes.byref(ctx))
+    if rc != DENSER_OK:
+        raise DenserError(rc, "denser_create failed")
+    return ctx
+
+
+def denser_destroy(ctx):
+    lib().denser_destroy(ctx)
+
+
+def denser_reset(ctx, stream=None):
+    return _check(ctx, lib().denser_reset(ctx, _stream(stream)))
+
+
+def denser_last_error(ctx) -> str:
+    m = lib().denser_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def denser_sync(ctx, stream=None):
+    return _check(ctx, lib().denser_sync(ctx, _stream(stream)))
+
+
+def denser_alloc_blocks(ctx, depth, K: denser_intrinsics, T_gc, segment=0, stream=None, count=False):
+    """Returns the number of new blocks when ``count`` (waits), else None."""
+    keep, tp = _pose(T_gc)
+    n = _i32(0)
+    _check(ctx, lib().denser_alloc_blocks(ctx, _ptr(depth, np.float32), ctypes.byref(K), tp, segment,
+                                          _stream(stream), ctypes.byref(n) if count else None))
+    return n.value if count else None
+
+
+def denser_fuse_depth(ctx, depth, K: denser_intrinsics, T_gc, segment=0, stream=None):
+    keep, tp = _pose(T_gc)
+    return _check(ctx, lib().denser_fuse_depth(ctx, _ptr(depth, np.float32), ctypes.byref(K), tp, segment,
+                                               _stream(stream)))
+
+
+def denser_regularize(ctx, max_iters, gap_tol=0.0, start=0, stream=None, stats=True):
+    st = denser_reg_stats()
+    _check(ctx, lib().denser_regularize(ctx, int(max_iters), float(gap_tol), int(start), _stream(stream),
+                                        ctypes.byref(st) if stats else None))
+    return st if stats else None
+
+
+def denser_energy(ctx, stream=None):
+    P, D = _dbl(), _dbl()
+    _check(ctx, lib().denser_energy(ctx, ctypes.byref(P), ctypes.byref(D), _stream(stream)))
+    return P.value, D.value
+
+
+def denser_extract(ctx, coords=None, f=None, w=None, omega=None, u=None, capacity_blocks=0, stream=None):
+    n = _i64(0)
+    _check(ctx, lib().denser_extract(ctx, _ptr(coords, np.int32), _ptr(f, np.float32), _ptr(w, np.float32),
+                                     _ptr(omega, np.uint8), _ptr(u, np.float32), int(capacity_blocks),
+                                     ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def denser_extract_dual(ctx, u_bar=None, p=None, capacity_blocks=0, stream=None):
+    return _check(ctx, lib().denser_extract_dual(ctx, _ptr(u_bar, np.float32), _ptr(p, np.float32),
+                                                 int(capacity_blocks), _stream(stream)))
+
+
+def denser_load_blocks(ctx, coords, f=None, w=None, n=None, stream=None):
+    n = len(coords) if n is None else n
+    return _check(ctx, lib().denser_load_blocks(ctx, _ptr(coords, np.int32), _ptr(f, np.float32),
+                                                _ptr(w, np.float32), int(n), _stream(stream)))
+
+
+def denser_load_state(ctx, u=None, u_bar=None, p=None, n=0, stream=None):
+    return _check(ctx, lib().denser_load_state(ctx, _ptr(u, np.float32), _ptr(u_bar, np.float32),
+                                               _ptr(p, np.float32), int(n), _stream(stream)))
+
+
+def denser_num_blocks(ctx, stream=None) -> int:
+    n = lib().denser_num_blocks(ctx, _stream(stream))
+    if n < 0:
+        _check(ctx, int(n))
+    return int(n)
+
+
+def denser_launch_count(ctx) -> int:
+    return int(lib().denser_launch_count(ctx))
+
+
+# ------------------------------------------------------------ convenience
+class DenserMap:
+    """Owns one context; numpy-returning helpers built on the calls above."""
+
+    def __init__(self, device=0, **params):
+        self.params = denser_default_params(**params)
+        self.ctx = denser_create(self.params, device)
+
+    def close(self):
+        if self.ctx is not None:
+            denser_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def snapshot(self, dual=False):
+        """Host copies: coords [n,4], f, w, u [n,512], omega bool [n,512] (+ u_bar, p)."""
+        n = denser_num_blocks(self.ctx)
+        out = {"coords": np.zeros((n, 4), np.int32), "f": np.zeros((n, 512), np.float32),
+               "w": np.zeros((n, 512), np.float32), "omega": np.zeros((n, 512), np.uint8),
+               "u": np.zeros((n, 512), np.float32)}
+        denser_extract(self.ctx, out["coords"], out["f"], out["w"], out["omega"], out["u"], n)
+        if dual:
+            out["u_bar"] = np.zeros((n, 512), np.float32)
+            out["p"] = np.zeros((3, n, 512), np.float32)
+            denser_extract_dual(self.ctx, out["u_bar"], out["p"], n)
+        return out
