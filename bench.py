@@ -163,6 +163,7 @@ def main():
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default=None, help="sweep_kernel,order,ctas_per_sm (default: the library's)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -195,6 +196,8 @@ def main():
 
     m = N.DenserMap(device=local, max_blocks=1 << 17, hash_slots=1 << 20, precision=args.precision)
     ctx = m.ctx
+    if args.schedule:
+        N.denser_set_schedule(ctx, *[int(v) for v in args.schedule.split(",")])
 
     def pipeline(depth_src, outs):
         N.denser_reset(ctx, stream)
@@ -301,8 +304,9 @@ def main():
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),
                    "pd_share_of_step": sweep_ms / args.steps / step_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "sweep_kernel<float>",
-                     "peak_kind": peak_kind, "bytes_per_voxel": bpv},
+                     "frac": achieved / hbm, "traffic": None, "kernel": ["sweep_kernel", "sweep_pipe_kernel", "sweep_rows_kernel"][N.denser_get_schedule(ctx)["sweep_kernel"]],
+                     "peak_kind": peak_kind, "bytes_per_voxel": bpv,
+                     "schedule": N.denser_get_schedule(ctx)},
         "e2e": {"value": updates * world / (e2e_ms / 1e3), "unit": "voxel-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

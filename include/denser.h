@@ -98,6 +98,21 @@ typedef struct {
     int64_t n_omega;          /* voxels in Omega (observed) */
 } denser_reg_stats;
 
+/* Launch schedule of the primal-dual sweep.  Every schedule computes the same
+ * iterates; only speed differs (chosen by the autotuner).
+ *   sweep_kernel  0: staged (each CTA loads a block, then computes it),
+ *                 1: pipelined (cp.async prefetch of the next block while computing),
+ *                 2: rows (one thread per 8-voxel x-row, vector loads; the default)
+ *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
+ *                 (neighbours are visited close together, so halos hit in L2)
+ *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default) */
+typedef struct {
+    int32_t sweep_kernel;
+    int32_t order;
+    int32_t ctas_per_sm;
+    int32_t reserved;
+} denser_schedule;
+
 /* Fills *p with the defaults above (hash 2^20 slots, 65536 blocks, FP32). */
 void denser_default_params(denser_params* p);
 
@@ -176,6 +191,11 @@ int denser_load_blocks(denser_ctx* ctx, const int32_t* coords, const float* f, c
  * p [3][n][512] float32 (converted to the storage precision).  NULL = zeros. */
 int denser_load_state(denser_ctx* ctx, const float* u, const float* u_bar, const float* p,
                       int64_t n, void* stream);
+
+/* Sets / reads the sweep schedule (see denser_schedule).  Out-of-range fields are
+ * DENSER_ERR_INVALID_ARG. */
+int denser_set_schedule(denser_ctx* ctx, const denser_schedule* sch);
+int denser_get_schedule(const denser_ctx* ctx, denser_schedule* sch);
 
 /* Number of allocated blocks (waits for the stream); negative on error. */
 int64_t denser_num_blocks(denser_ctx* ctx, void* stream);

@@ -14,6 +14,8 @@
 //   commit        publish the new block count.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace denser {
@@ -26,6 +28,10 @@ struct AllocArgs {
     double bs;  // block size 8 s
     double R[9];
     double t[3];
+    double ifx, ify, ibs;  // 1/fx, 1/fy, 1/bs (float32 fast path only)
+    int Ti[3];             // floor(t / bs)
+    float tf[3];           // t / bs - Ti, in [0, 1)
+    float hf;              // h as float32
     int W, H, N, seg;
 };
 
@@ -84,6 +90,44 @@ __device__ unsigned long long sample_key(const AllocArgs& a, int x, int y, doubl
     return pack_key(a.seg, (int32_t)k[0], (int32_t)k[1], (int32_t)k[2]);
 }
 
+// Float32 evaluation of sample n's key with a forward error bound.  The key of a
+// sample is floor(t/bs + z D), D = R (u/fx, v/fy, 1) / bs the pixel's ray step per
+// metre of depth in block units (computed once per pixel in float64, rounded to
+// float32), z = d + n h.  Returns 1 when every floor is certified (key or kEmptyKey
+// for z <= 0 in *key), 0 when the float64 path must decide.
+__device__ inline int sample_key_f32(const AllocArgs& a, const float* D, float d, int n, bool* range_err,
+                                     unsigned long long* key) {
+    const float eps = 9.53674316e-7f;  // 2^-20
+    const float nh = (float)a.N * a.hf;
+    const float z = fmaf((float)n, a.hf, d);
+    const float ez = eps * (fabsf(d) + nh) + 1e-30f;
+    if (z < -ez) {
+        *key = kEmptyKey;
+        return 1;
+    }
+    if (!(z > ez)) return 0;
+    float kf[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float q = fmaf(z, D[r], a.tf[r]);
+        const float e = eps * (fabsf(D[r]) * (z + nh) + fabsf(q) + 1.0f);
+        const float lo = floorf(q - e);
+        if (lo != floorf(q + e)) return 0;
+        kf[r] = lo;
+    }
+    const float lim = (float)kCoordBias;
+    long long k0 = (long long)a.Ti[0] + (long long)kf[0], k1 = (long long)a.Ti[1] + (long long)kf[1],
+              k2 = (long long)a.Ti[2] + (long long)kf[2];
+    if (!(fabsf(kf[0]) < 4.0f * lim && fabsf(kf[1]) < 4.0f * lim && fabsf(kf[2]) < 4.0f * lim) ||
+        !key_in_range(a.seg, k0, k1, k2)) {
+        *range_err = true;
+        *key = kEmptyKey;
+        return 1;
+    }
+    *key = pack_key(a.seg, (int32_t)k0, (int32_t)k1, (int32_t)k2);
+    return 1;
+}
+
 __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
     const int npix = a.W * a.H;
     const int lane = threadIdx.x & 31;
@@ -94,11 +138,19 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
         float dv = pix < npix ? __ldg(depth + pix) : 0.0f;
         const bool valid = pix < npix && isfinite(dv) && dv > 0.0f;
         const int x = pix % a.W, y = pix / a.W;
+        float D[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+            const double ua = ((double)x + 0.5 - a.cx) * a.ifx;
+            const double va = ((double)y + 0.5 - a.cy) * a.ify;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) D[r] = (float)((a.R[3 * r] * ua + a.R[3 * r + 1] * va + a.R[3 * r + 2]) * a.ibs);
+        }
         unsigned long long last = kEmptyKey;
         for (int n = -a.N; n <= a.N; ++n) {
             unsigned long long key = kEmptyKey;
             if (valid) {
-                key = sample_key(a, x, y, (double)dv, n, &range_err);
+                if (!sample_key_f32(a, D, dv, n, &range_err, &key))
+                    key = sample_key(a, x, y, (double)dv, n, &range_err);
                 if (key == last) key = kEmptyKey;  // consecutive samples in one block
                 else if (key != kEmptyKey) last = key;
             }
@@ -112,21 +164,27 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
     if (range_err) report(m.counters, kErrRange);
 }
 
-__global__ void __launch_bounds__(1024) sort_chunks_kernel(DeviceMap m) {
+// Sorts (key, val) pairs in place in chunks of kSortChunk (bitonic network in shared
+// memory over the next power of two >= the chunk's count).  *count may exceed
+// capacity; only the first `capacity` pairs exist.
+__global__ void __launch_bounds__(1024) sort_chunks_kernel(unsigned long long* keys, uint32_t* vals,
+                                                           const int32_t* count, int capacity) {
     __shared__ unsigned long long sk[kSortChunk];
     __shared__ uint32_t ss[kSortChunk];
-    const int n = min(m.counters[kNumNew], (int)m.max_new);
+    const int n = min(*count, capacity);
     const int base = blockIdx.x * kSortChunk;
     if (base >= n) return;
     const int cnt = min(kSortChunk, n - base);
-    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
-        sk[i] = i < cnt ? m.new_keys[base + i] : kEmptyKey;
-        ss[i] = i < cnt ? m.new_slots[base + i] : 0u;
+    int size = 64;
+    while (size < cnt) size <<= 1;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+        sk[i] = i < cnt ? keys[base + i] : kEmptyKey;
+        ss[i] = i < cnt ? vals[base + i] : 0u;
     }
     __syncthreads();
-    for (int k = 2; k <= kSortChunk; k <<= 1) {
+    for (int k = 2; k <= size; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+            for (int i = threadIdx.x; i < size; i += blockDim.x) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
                     const bool up = (i & k) == 0;
@@ -144,31 +202,45 @@ __global__ void __launch_bounds__(1024) sort_chunks_kernel(DeviceMap m) {
         }
     }
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        m.new_keys[base + i] = sk[i];
-        m.new_slots[base + i] = ss[i];
+        keys[base + i] = sk[i];
+        vals[base + i] = ss[i];
     }
+}
+
+// Global rank of element i among n distinct keys sorted in chunks: its position in
+// its own chunk plus, for every other chunk, the number of keys below it.
+__device__ long long global_rank(const unsigned long long* keys, int n, int i) {
+    const unsigned long long key = keys[i];
+    const int nchunks = (n + kSortChunk - 1) / kSortChunk;
+    const int c = i / kSortChunk;
+    long long rank = i - c * kSortChunk;
+    for (int c2 = 0; c2 < nchunks; ++c2) {
+        if (c2 == c) continue;
+        int lo = c2 * kSortChunk, hi = min(lo + kSortChunk, n);
+        const int first = lo;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (keys[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        rank += lo - first;
+    }
+    return rank;
+}
+
+__global__ void order_scatter_kernel(const unsigned long long* keys, const uint32_t* vals, const int32_t* count,
+                                     int capacity, int32_t* order) {
+    const int n = min(*count, capacity);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        order[global_rank(keys, n, i)] = (int32_t)vals[i];
 }
 
 __global__ void rank_assign_kernel(DeviceMap m) {
     const int n = min(m.counters[kNumNew], (int)m.max_new);
     const int nb = m.counters[kNumBlocks];
-    const int nchunks = (n + kSortChunk - 1) / kSortChunk;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const unsigned long long key = m.new_keys[i];
-        const int c = i / kSortChunk;
-        long long rank = i - c * kSortChunk;
-        for (int c2 = 0; c2 < nchunks; ++c2) {
-            if (c2 == c) continue;
-            int lo = c2 * kSortChunk, hi = min(lo + kSortChunk, n);
-            const int first = lo;
-            while (lo < hi) {  // lower bound
-                const int mid = (lo + hi) >> 1;
-                if (m.new_keys[mid] < key) lo = mid + 1;
-                else hi = mid;
-            }
-            rank += lo - first;
-        }
-        const long long idx = nb + rank;
+        const long long idx = nb + global_rank(m.new_keys, n, i);
         const uint32_t slot = m.new_slots[i];
         if (idx < (long long)m.max_blocks) {
             int32_t s, x, y, z;
@@ -179,6 +251,16 @@ __global__ void rank_assign_kernel(DeviceMap m) {
             m.hash_vals[slot] = -2;
             report(m.counters, kErrPoolFull);
         }
+    }
+}
+
+__global__ void order_keys_kernel(const int32_t* coords, const int32_t* count, unsigned long long* keys,
+                                  uint32_t* vals) {
+    const int n = *count;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+        const int4 k = reinterpret_cast<const int4*>(coords)[b];
+        keys[b] = pack_key(k.x, k.y, k.z, k.w);
+        vals[b] = (uint32_t)b;
     }
 }
 
@@ -273,11 +355,20 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
     }
     a.W = K->width, a.H = K->height;
     a.N = (int)ceil(c->prm.mu / a.h - 1e-9);
+    a.ifx = 1.0 / a.fx, a.ify = 1.0 / a.fy, a.ibs = 1.0 / a.bs;
+    for (int r = 0; r < 3; ++r) {
+        const double tb = a.t[r] / a.bs;
+        const double ti = floor(tb);
+        a.Ti[r] = (int)std::max(-2.0 * kCoordBias, std::min(2.0 * kCoordBias, ti));
+        a.tf[r] = (float)(tb - (double)a.Ti[r]);
+    }
+    a.hf = (float)a.h;
     a.seg = segment;
     const int npix = a.W * a.H;
     alloc_keys_kernel<<<grid_for(c->sm_count, npix, 256, 8), 256, 0, s>>>(depth, a, c->d);
     const int chunks = (int)((c->d.max_new + kSortChunk - 1) / kSortChunk);
-    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->d);
+    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->d.new_keys, c->d.new_slots, c->d.counters + kNumNew,
+                                               (int)c->d.max_new);
     rank_assign_kernel<<<grid_for(c->sm_count, c->d.max_new, 256, 4), 256, 0, s>>>(c->d);
     int nreg;
     ZeroRegions z = all_regions(c, &nreg);
@@ -285,6 +376,7 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
     commit_kernel<<<1, 1, 0, s>>>(c->d);
     c->launches += 5;
     c->nbr_valid_blocks = -1;
+    c->order_valid_blocks = -1;
     return cuda_check(c, cudaGetLastError(), "allocation kernels");
 }
 
@@ -296,7 +388,23 @@ int launch_load_blocks(denser_ctx* c, const int32_t* coords_dev, int64_t n, int6
     set_count_kernel<<<1, 1, 0, s>>>(c->d, (int32_t)(base + n));
     c->launches += 3;
     c->nbr_valid_blocks = -1;
+    c->order_valid_blocks = -1;
     return cuda_check(c, cudaGetLastError(), "load_blocks kernels");
+}
+
+// Visiting order of the sweep: block indices sorted by key (segment, bz, by, bx).
+int launch_block_order(denser_ctx* c, int64_t n_blocks, cudaStream_t s) {
+    if (n_blocks <= 0) return DENSER_OK;
+    const int32_t* cnt = c->d.counters + kNumBlocks;
+    order_keys_kernel<<<grid_for(c->sm_count, n_blocks, 256, 8), 256, 0, s>>>(c->d.coords, cnt, c->order_keys,
+                                                                              c->order_vals);
+    const int chunks = (int)((n_blocks + kSortChunk - 1) / kSortChunk);
+    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->order_keys, c->order_vals, cnt, (int)c->d.max_blocks);
+    order_scatter_kernel<<<grid_for(c->sm_count, n_blocks, 256, 8), 256, 0, s>>>(c->order_keys, c->order_vals, cnt,
+                                                                                 (int)c->d.max_blocks, c->order);
+    c->launches += 3;
+    c->order_valid_blocks = n_blocks;
+    return cuda_check(c, cudaGetLastError(), "block order kernels");
 }
 
 int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s) {

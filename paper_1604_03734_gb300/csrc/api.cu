@@ -169,7 +169,8 @@ int energy_now(denser_ctx* c, int64_t nb, cudaStream_t s, double* P, double* D) 
 void free_all(denser_ctx* c) {
     void* ptrs[] = {c->d.hash_keys, c->d.hash_vals, c->d.coords, c->d.f, c->d.w, c->d.u, c->d.ub[0], c->d.ub[1],
                     c->d.p[0], c->d.p[1], c->d.omega_bits, c->d.nbr, c->d.counters, c->d.new_keys,
-                    c->d.new_slots, c->d.visible, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch};
+                    c->d.new_slots, c->d.visible, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch,
+                    c->order, c->order_keys, c->order_vals};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -220,6 +221,12 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->omega_bytes = nullptr, c->conv_scratch = nullptr, c->conv_bytes = 0;
     c->h_counters = nullptr, c->h_energy = nullptr;
     c->launches = 0;
+    c->sched.sweep_kernel = 2;
+    c->sched.order = 1;
+    c->sched.ctas_per_sm = 0;
+    c->sched.reserved = 0;
+    c->order = nullptr, c->order_keys = nullptr, c->order_vals = nullptr;
+    c->order_valid_blocks = -1;
     c->elem_size = p.precision == DENSER_FP32 ? 4 : 2;
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -247,8 +254,11 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
                 {(void**)&c->d.counters, kNumCounters * 4},
                 {(void**)&c->d.new_keys, max_new * 8},
                 {(void**)&c->d.new_slots, max_new * 4},
-                {(void**)&c->d.visible, mb * 4},
-                {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2) * 8}};
+                {(void**)&c->d.visible, mb * 32},
+                {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2) * 8},
+                {(void**)&c->order, mb * 4},
+                {(void**)&c->order_keys, mb * 8},
+                {(void**)&c->order_vals, mb * 4}};
     for (auto& r : reqs) {
         if (cudaMalloc(r.ptr, r.bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -264,7 +274,8 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
         delete c;
         return DENSER_ERR_CUDA;
     }
-    if (denser_reset(c, nullptr) != DENSER_OK || cudaDeviceSynchronize() != cudaSuccess) {
+    if (configure_kernels(c) != DENSER_OK || denser_reset(c, nullptr) != DENSER_OK ||
+        cudaDeviceSynchronize() != cudaSuccess) {
         free_all(c);
         delete c;
         return DENSER_ERR_CUDA;
@@ -294,6 +305,7 @@ int denser_reset(denser_ctx* c, void* stream) {
         if ((rc = cuda_check(c, cudaMemsetAsync(c->d.counters, 0, kNumCounters * 4, s), "reset"))) return rc;
         c->cur = 0;
         c->nbr_valid_blocks = -1;
+        c->order_valid_blocks = -1;
         return DENSER_OK;
     });
 }
@@ -531,6 +543,23 @@ int denser_load_state(denser_ctx* c, const float* u, const float* u_bar, const f
                 return rc;
         return read_counters(c, s);
     });
+}
+
+int denser_set_schedule(denser_ctx* c, const denser_schedule* sch) {
+    if (!c || !sch) return DENSER_ERR_INVALID_ARG;
+    if (sch->sweep_kernel < 0 || sch->sweep_kernel > 2 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
+        sch->ctas_per_sm > 8)
+        return set_error(c, DENSER_ERR_INVALID_ARG, "set_schedule: field out of range");
+    c->sched = *sch;
+    c->sched.reserved = 0;
+    c->order_valid_blocks = -1;
+    return DENSER_OK;
+}
+
+int denser_get_schedule(const denser_ctx* c, denser_schedule* sch) {
+    if (!c || !sch) return DENSER_ERR_INVALID_ARG;
+    *sch = c->sched;
+    return DENSER_OK;
 }
 
 int64_t denser_num_blocks(denser_ctx* c, void* stream) {

@@ -108,7 +108,7 @@ struct DeviceMap {
     int32_t* counters;              // [kNumCounters]
     unsigned long long* new_keys;   // [max_new] inserted keys of the running call
     uint32_t* new_slots;            // [max_new]
-    int32_t* visible;               // [max_blocks] fusion work list
+    int32_t* visible;               // [max_blocks] fusion work list (32-byte entries)
     double* partials;               // [kEnergyGrid][2] energy partial sums
     uint32_t max_blocks;
     uint32_t max_new;
@@ -137,6 +137,11 @@ struct denser_ctx {
     int32_t* h_counters;       // pinned copy of the device counters
     double* h_energy;          // pinned [2]
     unsigned long long launches;
+    denser_schedule sched;     // sweep schedule
+    int32_t* order;            // [max_blocks] sweep visiting order (sorted keys)
+    unsigned long long* order_keys;  // [max_blocks] scratch of the order sort
+    uint32_t* order_vals;      // [max_blocks]
+    int64_t order_valid_blocks;  // blocks covered by `order` (-1: rebuild)
     std::string msg;
 };
 
@@ -155,6 +160,10 @@ int launch_omega_bytes(denser_ctx* c, int64_t n_blocks, uint8_t* out, cudaStream
 int launch_convert_state(denser_ctx* c, const void* src, float* dst, int64_t n, bool to_float,
                          cudaStream_t s);
 int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s);
+int launch_sort_pairs(denser_ctx* c, unsigned long long* keys, uint32_t* vals, const int32_t* count, int capacity,
+                      cudaStream_t s);
+int launch_block_order(denser_ctx* c, int64_t n_blocks, cudaStream_t s);
+int configure_kernels(denser_ctx* c);
 
 int set_error(denser_ctx* c, int code, const std::string& m);
 int cuda_check(denser_ctx* c, cudaError_t e, const char* what);

@@ -7,9 +7,13 @@
 //               planes and the far limit d_max + mu); survivors go to a work list.
 //               A culled block provably has no voxel that Eq. 1 would update;
 //   fuse        one CTA per listed block, 128 threads x 4 consecutive voxels; f and w
-//               move as float4.  The projection and the update test run in float64 in
-//               the oracle's operation order, so the set of updated voxels (and so w)
-//               is bit-exact; f is accumulated in float32.
+//               move as float4.  Each integer decision (the pixel a voxel projects to,
+//               z_c > 0, u_SDF >= -mu) is first taken in float32 together with a
+//               forward error bound; when the bound cannot certify it, the voxel is
+//               recomputed in float64 in the oracle's exact operation order.  So the set
+//               of updated voxels (and w) is bit-exact while float64, which runs at a
+//               small fraction of the float32 rate on this GPU, is used for well under
+//               1% of voxels.  f is accumulated in float32.
 #include <math.h>
 
 #include "common.cuh"
@@ -24,17 +28,44 @@ struct FuseArgs {
     double fx, fy, cx, cy, s, mu;
     double plane[4][3];  // unit normals of the four side planes (camera frame)
     double radius;       // bounding-sphere radius of a block's voxel centres, padded
+    float M[9];          // s R^T: camera-frame step per local voxel index (float32)
+    float fxf, fyf, cxf, cyf, muf, sf;
     int W, H, seg;
 };
 
-__global__ void depth_max_kernel(const float* __restrict__ depth, int n, int32_t* counters) {
+// A block selected for fusion, with the camera-frame centre of its voxel (0,0,0)
+// split into float32 high and low parts (hi + lo = the float64 value to ~2^-48).
+struct VisBlock {
+    int b;
+    float hi[3];
+    float lo[3];
+    float delta;  // bound on the float32 camera-coordinate error of any voxel of the block
+};
+static_assert(sizeof(VisBlock) == 32, "VisBlock is 32 bytes");
+
+__global__ void __launch_bounds__(256) depth_max_kernel(const float* __restrict__ depth, int n, int32_t* counters) {
+    __shared__ float red[8];
     float mx = 0.0f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int n4 = ((reinterpret_cast<uintptr_t>(depth) & 15) == 0) ? n / 4 : 0;
+    const float4* d4 = reinterpret_cast<const float4*>(depth);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+        const float4 v = __ldg(d4 + i);
+        if (isfinite(v.x)) mx = fmaxf(mx, v.x);
+        if (isfinite(v.y)) mx = fmaxf(mx, v.y);
+        if (isfinite(v.z)) mx = fmaxf(mx, v.z);
+        if (isfinite(v.w)) mx = fmaxf(mx, v.w);
+    }
+    for (int i = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float d = __ldg(depth + i);
-        if (isfinite(d) && d > mx) mx = d;
+        if (isfinite(d)) mx = fmaxf(mx, d);
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0 && mx > 0.0f) atomicMax(counters + kDepthMaxBits, __float_as_int(mx));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, red[i]);
+        if (mx > 0.0f) atomicMax(counters + kDepthMaxBits, __float_as_int(mx));
+    }
 }
 
 __device__ inline void to_camera(const FuseArgs& a, double gx, double gy, double gz, double* c) {
@@ -64,9 +95,49 @@ __global__ void cull_kernel(DeviceMap m, FuseArgs a) {
         for (int q = 0; q < 4; ++q)
             out |= a.plane[q][0] * c[0] + a.plane[q][1] * c[1] + a.plane[q][2] * c[2] < -r;
         if (out) continue;
+        double c0[3];
+        to_camera(a, __dmul_rn(__dadd_rn((double)(8 * k.y), 0.5), a.s), __dmul_rn(__dadd_rn((double)(8 * k.z), 0.5), a.s),
+                  __dmul_rn(__dadd_rn((double)(8 * k.w), 0.5), a.s), c0);
+        VisBlock vb;
+        vb.b = b;
+        double amax = 0.0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            vb.hi[e] = (float)c0[e];
+            vb.lo[e] = (float)(c0[e] - (double)vb.hi[e]);
+            amax = fmax(amax, fabs(c0[e]));
+        }
+        // x = (hi + M l) + lo in float32: two roundings of |x| <= amax + 14 s, plus the
+        // rounding of M (|M| <= s) times |l| <= 7; 2^-21 leaves a factor >= 4 of margin.
+        vb.delta = (float)(ldexp(amax + 1.0 + 30.0 * a.s, -21));
         const int pos = atomicAdd(m.counters + kNumVisible, 1);
-        m.visible[pos] = b;
+        reinterpret_cast<VisBlock*>(m.visible)[pos] = vb;
     }
+}
+
+// Exact float64 decision and value for voxel (i, j, k), in the oracle's order.
+__device__ bool fuse_voxel_f64(const float* __restrict__ depth, const FuseArgs& a, int i, int j, int k, float* ut) {
+    double c[3];
+    to_camera(a, __dmul_rn(__dadd_rn((double)i, 0.5), a.s), __dmul_rn(__dadd_rn((double)j, 0.5), a.s),
+              __dmul_rn(__dadd_rn((double)k, 0.5), a.s), c);
+    if (!(c[2] > 0.0)) return false;
+    const double pxf = floor(__dadd_rn(__ddiv_rn(__dmul_rn(a.fx, c[0]), c[2]), a.cx));
+    const double pyf = floor(__dadd_rn(__ddiv_rn(__dmul_rn(a.fy, c[1]), c[2]), a.cy));
+    if (!(pxf >= 0.0 && pxf < (double)a.W && pyf >= 0.0 && pyf < (double)a.H)) return false;
+    const float d = __ldg(depth + (size_t)pyf * a.W + (size_t)pxf);
+    if (!(isfinite(d) && d > 0.0f)) return false;
+    const double usdf = __dsub_rn((double)d, c[2]);
+    if (usdf < -a.mu) return false;
+    *ut = (float)fmin(1.0, __ddiv_rn(usdf, a.mu));
+    return true;
+}
+
+// floor() of a float32 projection value v with error bound e, certified when
+// floor(v - e) == floor(v + e); returns false when undecided.
+__device__ inline bool certified_floor(float v, float e, float* out) {
+    const float lo = floorf(v - e), hi = floorf(v + e);
+    *out = lo;
+    return lo == hi;
 }
 
 __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ depth, DeviceMap m, FuseArgs a) {
@@ -74,35 +145,73 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
     const int t = threadIdx.x;
     const int l0 = 4 * t;
     const int lx0 = l0 & 7, ly = (l0 >> 3) & 7, lz = l0 >> 6;
-    for (int k = blockIdx.x; k < nv; k += gridDim.x) {
-        const int b = m.visible[k];
-        const int4 key = reinterpret_cast<const int4*>(m.coords)[b];
+    const float eps = 4.76837158e-7f;  // 2^-21
+    const VisBlock* __restrict__ vis = reinterpret_cast<const VisBlock*>(m.visible);
+    for (int kb = blockIdx.x; kb < nv; kb += gridDim.x) {
+        const VisBlock vb = vis[kb];
+        const int b = vb.b;
         float4* fp = reinterpret_cast<float4*>(m.f + (size_t)b * kBlockVoxels) + t;
         float4* wp = reinterpret_cast<float4*>(m.w + (size_t)b * kBlockVoxels) + t;
         float4 f4 = *fp, w4 = *wp;
         float fv[4] = {f4.x, f4.y, f4.z, f4.w};
         float wv[4] = {w4.x, w4.y, w4.z, w4.w};
         bool any = false;
-        const double gy = __dmul_rn(__dadd_rn((double)(8 * key.z + ly), 0.5), a.s);
-        const double gz = __dmul_rn(__dadd_rn((double)(8 * key.w + lz), 0.5), a.s);
+        const float dl = vb.delta;
+        // local offsets along y and z are shared by the thread's four voxels
+        const float myz[3] = {fmaf(a.M[1], (float)ly, a.M[2] * (float)lz), fmaf(a.M[4], (float)ly, a.M[5] * (float)lz),
+                              fmaf(a.M[7], (float)ly, a.M[8] * (float)lz)};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const double gx = __dmul_rn(__dadd_rn((double)(8 * key.y + lx0 + q), 0.5), a.s);
-            double c[3];
-            to_camera(a, gx, gy, gz, c);
-            if (!(c[2] > 0.0)) continue;
-            const double pxf = floor(__dadd_rn(__ddiv_rn(__dmul_rn(a.fx, c[0]), c[2]), a.cx));
-            const double pyf = floor(__dadd_rn(__ddiv_rn(__dmul_rn(a.fy, c[1]), c[2]), a.cy));
-            if (!(pxf >= 0.0 && pxf < (double)a.W && pyf >= 0.0 && pyf < (double)a.H)) continue;
-            const float d = __ldg(depth + (size_t)pyf * a.W + (size_t)pxf);
-            if (!(isfinite(d) && d > 0.0f)) continue;
-            const double usdf = __dsub_rn((double)d, c[2]);
-            if (usdf < -a.mu) continue;
-            const float ut = (float)fmin(1.0, __ddiv_rn(usdf, a.mu));
-            const float wn = wv[q] + 1.0f;
-            fv[q] = (ut + wv[q] * fv[q]) / wn;
-            wv[q] = wn;
-            any = true;
+            const float lx = (float)(lx0 + q);
+            const float mx = fmaf(a.M[0], lx, myz[0]);
+            const float my = fmaf(a.M[3], lx, myz[1]);
+            const float mz = fmaf(a.M[6], lx, myz[2]);
+            const float x = (vb.hi[0] + mx) + vb.lo[0];
+            const float y = (vb.hi[1] + my) + vb.lo[1];
+            const float z = (vb.hi[2] + mz) + vb.lo[2];
+            int decided = 0;  // 1: certified in float32
+            bool upd = false;
+            float ut = 0.0f;
+            if (z + dl <= 0.0f) {
+                decided = 1;  // certainly behind the camera
+            } else if (z - dl > 0.0f) {
+                const float inv = __frcp_rn(z);
+                const float rx = x * inv, ry = y * inv;
+                const float px = fmaf(a.fxf, rx, a.cxf);
+                const float py = fmaf(a.fyf, ry, a.cyf);
+                const float g = 2.0f * dl / (z - dl);
+                const float ex = a.fxf * g * (1.0f + fabsf(rx)) + eps * (a.fxf * fabsf(rx) + fabsf(px) + fabsf(a.cxf)) + 1e-6f;
+                const float ey = a.fyf * g * (1.0f + fabsf(ry)) + eps * (a.fyf * fabsf(ry) + fabsf(py) + fabsf(a.cyf)) + 1e-6f;
+                float pxi, pyi;
+                if (certified_floor(px, ex, &pxi) && certified_floor(py, ey, &pyi)) {
+                    if (!(pxi >= 0.0f && pxi < (float)a.W && pyi >= 0.0f && pyi < (float)a.H)) {
+                        decided = 1;
+                    } else {
+                        const float d = __ldg(depth + (size_t)pyi * a.W + (size_t)pxi);
+                        if (!(isfinite(d) && d > 0.0f)) {
+                            decided = 1;
+                        } else {
+                            // u_SDF = d - z with z = hi + mz + lo; d - hi is (nearly) exact
+                            const float dh = d - vb.hi[2];
+                            const float us = (dh - mz) - vb.lo[2];
+                            const float eu = eps * (fabsf(dh) + fabsf(mz) + fabsf(us) + 30.0f * a.sf) + 1e-7f;
+                            if (fabsf(us + a.muf) > eu) {
+                                decided = 1;
+                                upd = us >= -a.muf;
+                                ut = fminf(1.0f, us / a.muf);
+                            }
+                        }
+                    }
+                }
+            }
+            if (!decided) upd = fuse_voxel_f64(depth, a, 8 * m.coords[4 * b + 1] + lx0 + q, 8 * m.coords[4 * b + 2] + ly,
+                                               8 * m.coords[4 * b + 3] + lz, &ut);
+            if (upd) {
+                const float wn = wv[q] + 1.0f;
+                fv[q] = (ut + wv[q] * fv[q]) / wn;
+                wv[q] = wn;
+                any = true;
+            }
         }
         if (any) {
             *fp = make_float4(fv[0], fv[1], fv[2], fv[3]);
@@ -139,9 +248,12 @@ int launch_fuse(denser_ctx* c, const float* depth, const denser_intrinsics* K, c
         for (int e = 0; e < 3; ++e) a.plane[q][e] = raw[q][e] / n;
     }
     a.radius = 3.5 * c->prm.voxel_size * sqrt(3.0) * (1.0 + 1e-9) + 1e-6;
+    for (int e = 0; e < 9; ++e) a.M[e] = (float)(a.Ri[e] * a.s);
+    a.fxf = (float)a.fx, a.fyf = (float)a.fy, a.cxf = (float)a.cx, a.cyf = (float)a.cy;
+    a.muf = (float)a.mu, a.sf = (float)a.s;
     cudaMemsetAsync(c->d.counters + kNumVisible, 0, 2 * sizeof(int32_t), s);
     const int npix = a.W * a.H;
-    depth_max_kernel<<<grid_for(c->sm_count, npix, 256, 4), 256, 0, s>>>(depth, npix, c->d.counters);
+    depth_max_kernel<<<grid_for(c->sm_count, (npix + 3) / 4, 256, 2), 256, 0, s>>>(depth, npix, c->d.counters);
     cull_kernel<<<grid_for(c->sm_count, c->d.max_blocks, 256, 4), 256, 0, s>>>(c->d, a);
     fuse_kernel<<<c->sm_count * 16, 128, 0, s>>>(depth, c->d, a);
     c->launches += 3;

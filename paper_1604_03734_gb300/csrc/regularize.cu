@@ -128,20 +128,56 @@ __device__ inline void stage_tiles(Tiles& s, int b, const T* __restrict__ vsrc, 
     __syncthreads();
 }
 
+// Arithmetic shared by every sweep variant, with explicit rounding so that all of
+// them produce bit-identical iterates.
+// Dual update of one voxel, Eq. 3: q = p + sigma grad; p' = q / max(1, |q|_2).  Inside
+// the unit ball p' = q exactly; outside, q is scaled by the hardware reciprocal square
+// root of |q|^2 (relative error below 2^-22).
+__device__ inline void dual_update(float p0, float p1, float p2, float g0, float g1, float g2, float sigma,
+                                   float* out) {
+    const float q0 = __fmaf_rn(sigma, g0, p0);
+    const float q1 = __fmaf_rn(sigma, g1, p1);
+    const float q2 = __fmaf_rn(sigma, g2, p2);
+    const float n2 = __fmaf_rn(q2, q2, __fmaf_rn(q1, q1, __fmul_rn(q0, q0)));
+    const float sc = n2 > 1.0f ? rsqrtf(n2) : 1.0f;
+    out[0] = __fmul_rn(q0, sc), out[1] = __fmul_rn(q1, sc), out[2] = __fmul_rn(q2, sc);
+}
+
+// Masked forward difference of Eq. 3.
+__device__ inline float masked_diff(bool e, float next, float here) { return e ? __fsub_rn(next, here) : 0.0f; }
+
+// Eq. 4 as the negative adjoint: own minus backward terms per axis, summed x, y, z.
+__device__ inline float div_terms(bool ex, float px, bool exm, float pxm, bool ey, float py, bool eym, float pym,
+                                  bool ez, float pz, bool ezm, float pzm) {
+    const float d0 = __fsub_rn(ex ? px : 0.0f, exm ? pxm : 0.0f);
+    const float d1 = __fsub_rn(ey ? py : 0.0f, eym ? pym : 0.0f);
+    const float d2 = __fsub_rn(ez ? pz : 0.0f, ezm ? pzm : 0.0f);
+    return __fadd_rn(__fadd_rn(d0, d1), d2);
+}
+
+// Primal proximal step on Omega and the relaxation.
+__device__ inline void primal_update(bool o, float uo, float dv, float fv, float wv, float tau, float tau_lam,
+                                     float theta, float* un, float* ubn) {
+    float u = uo;
+    if (o) {
+        const float ut = __fmaf_rn(tau, dv, uo);
+        const float tlw = __fmul_rn(tau_lam, wv);
+        u = __fmul_rn(__fmaf_rn(tlw, fv, ut), __frcp_rn(__fadd_rn(1.0f, tlw)));
+    }
+    *un = u;
+    *ubn = __fmaf_rn(theta, __fsub_rn(u, uo), u);
+}
+
 // Dual step at tile position (x, y, z): p <- P(p + sigma grad_Omega u_bar), Eq. 3.
 __device__ inline void dual_step(Tiles& s, int x, int y, int z, float sigma, float* out) {
     const int c = t10(x, y, z);
     const bool o = s.om[c];
     const float u0 = s.v[c];
-    const float g0 = (o && s.om[c + 1]) ? s.v[c + 1] - u0 : 0.0f;
-    const float g1 = (o && s.om[c + kTile]) ? s.v[c + kTile] - u0 : 0.0f;
-    const float g2 = (o && s.om[c + kTile * kTile]) ? s.v[c + kTile * kTile] - u0 : 0.0f;
+    const float g0 = masked_diff(o && s.om[c + 1], s.v[c + 1], u0);
+    const float g1 = masked_diff(o && s.om[c + kTile], s.v[c + kTile], u0);
+    const float g2 = masked_diff(o && s.om[c + kTile * kTile], s.v[c + kTile * kTile], u0);
     const int q = t9(x, y, z);
-    const float q0 = s.p[0][q] + sigma * g0;
-    const float q1 = s.p[1][q] + sigma * g1;
-    const float q2 = s.p[2][q] + sigma * g2;
-    const float m = fmaxf(1.0f, sqrtf(q0 * q0 + q1 * q1 + q2 * q2));
-    out[0] = q0 / m, out[1] = q1 / m, out[2] = q2 / m;
+    dual_update(s.p[0][q], s.p[1][q], s.p[2][q], g0, g1, g2, sigma, out);
 }
 
 // Omega-aware divergence at a block voxel, Eq. 4 as the negative adjoint of Eq. 3.
@@ -149,12 +185,9 @@ __device__ inline float divergence(const Tiles& s, int x, int y, int z) {
     const int c = t10(x, y, z);
     const int q = t9(x, y, z);
     const bool o = s.om[c];
-    const float d0 = ((o && s.om[c + 1]) ? s.p[0][q] : 0.0f) - ((o && s.om[c - 1]) ? s.p[0][q - 1] : 0.0f);
-    const float d1 = ((o && s.om[c + kTile]) ? s.p[1][q] : 0.0f) -
-                     ((o && s.om[c - kTile]) ? s.p[1][q - kPTile] : 0.0f);
-    const float d2 = ((o && s.om[c + kTile * kTile]) ? s.p[2][q] : 0.0f) -
-                     ((o && s.om[c - kTile * kTile]) ? s.p[2][q - kPTile * kPTile] : 0.0f);
-    return (d0 + d1) + d2;
+    return div_terms(o && s.om[c + 1], s.p[0][q], o && s.om[c - 1], s.p[0][q - 1], o && s.om[c + kTile], s.p[1][q],
+                     o && s.om[c - kTile], s.p[1][q - kPTile], o && s.om[c + kTile * kTile], s.p[2][q],
+                     o && s.om[c - kTile * kTile], s.p[2][q - kPTile * kPTile]);
 }
 
 template <typename T>
@@ -168,6 +201,7 @@ struct SweepArgs {
     const float* w;
     const uint32_t* bits;
     const int32_t* nbr;
+    const int32_t* order;  // visiting order of the blocks (NULL: index order)
     size_t pstride;
     int n_blocks;
     float sigma, tau, tau_lam, theta;
@@ -203,19 +237,514 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs<T> a) {
             }
         }
         __syncthreads();
-        float un = uo;
-        if (oc) {
-            const float ut = uo + a.tau * divergence(s, lx, ly, lz);
-            const float tlw = a.tau_lam * wv;
-            un = (ut + tlw * fv) / (1.0f + tlw);
-        }
-        const float ubn = un + a.theta * (un - uo);
+        float un, ubn;
+        primal_update(oc, uo, oc ? divergence(s, lx, ly, lz) : 0.0f, fv, wv, a.tau, a.tau_lam, a.theta, &un, &ubn);
         Store<T>::st(a.u + v, un);
         Store<T>::st(a.ub_out + v, ubn);
 #pragma unroll
         for (int c = 0; c < 3; ++c) Store<T>::st(a.p_out + c * a.pstride + v, pc[c]);
         __syncthreads();  // the tiles are reused by the next block
     }
+}
+
+// ----------------------------------------------------------- pipelined sweep
+// The same stencil as sweep_kernel, restructured for latency: a persistent CTA walks
+// its blocks and, while it computes block k, cp.async copies already bring block k+1
+// (core fields as 16-byte chunks, halo voxels and the neighbours' Omega words as
+// 4-byte words) into the other half of a double-buffered shared-memory stage, and the
+// neighbour row of block k+2 into a three-entry ring.  Block k's stage is then decoded
+// into the padded float tiles the stencil functions read.
+__device__ inline void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ inline void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Raw stage of one block (bytes; every part 16-byte aligned).
+template <typename T>
+struct StageLayout {
+    static constexpr int E = (int)sizeof(T);
+    static constexpr int kUb = 0;
+    static constexpr int kP = kUb + kBlockVoxels * E;
+    static constexpr int kU = kP + 3 * kBlockVoxels * E;
+    static constexpr int kF = kU + kBlockVoxels * E;
+    static constexpr int kW = kF + kBlockVoxels * 4;
+    static constexpr int kBits = kW + kBlockVoxels * 4;
+    static constexpr int kNBits = kBits + 64;
+    static constexpr int kHaloUb = kNBits + kNeighbours * 64;
+    static constexpr int kHaloP = kHaloUb + kHalo * 4;
+    static constexpr int kBytes = kHaloP + 3 * kLowHalo * 4;
+    // 16-byte chunks of the contiguous core part (u_bar, p, u, f, w, Omega bits)
+    static constexpr int kCoreChunks = kNBits / 16;
+};
+
+// Low-face index (0..191) of halo entry hid, or -1.
+__device__ inline int low_index(int hid) {
+    if (hid >= 64 && hid < 128) return hid - 64;
+    if (hid >= 192 && hid < 256) return hid - 192 + 64;
+    if (hid >= 320 && hid < 384) return hid - 320 + 128;
+    return -1;
+}
+__device__ inline int low_hid(int li) { return li < 64 ? li + 64 : (li < 128 ? li - 64 + 192 : li - 128 + 320); }
+
+// Element e of a 4-byte word that holds element offset `off` of a T array.
+template <typename T>
+__device__ inline float word_elem(uint32_t w, int off) {
+    if constexpr (sizeof(T) == 4) {
+        return __uint_as_float(w);
+    } else {
+        const unsigned short h = (off & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
+        T v;
+        memcpy(&v, &h, 2);
+        return Store<T>::ld(&v);
+    }
+}
+
+template <typename T>
+__device__ inline const void* word_addr(const T* base, size_t off) {
+    return reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(base + off) & ~(uintptr_t)3);
+}
+
+// Issues the copies of block b's core and its neighbour row (for the ring).
+template <typename T>
+__device__ inline void issue_core(const SweepArgs<T>& a, char* st, int b, int* nbr_slot_next, int b_next, int t) {
+    using L = StageLayout<T>;
+    const size_t v0 = (size_t)b * kBlockVoxels;
+    for (int c = t; c < L::kCoreChunks; c += kSweepThreads) {
+        const int off = c * 16;
+        const char* src;
+        if (off < L::kP) src = reinterpret_cast<const char*>(a.ub_in + v0) + off;
+        else if (off < L::kU) {
+            const int q = off - L::kP, comp = q / (kBlockVoxels * L::E);
+            src = reinterpret_cast<const char*>(a.p_in + comp * a.pstride + v0) + (q - comp * kBlockVoxels * L::E);
+        } else if (off < L::kF) src = reinterpret_cast<const char*>(a.u + v0) + (off - L::kU);
+        else if (off < L::kW) src = reinterpret_cast<const char*>(a.f + v0) + (off - L::kF);
+        else if (off < L::kBits) src = reinterpret_cast<const char*>(a.w + v0) + (off - L::kW);
+        else src = reinterpret_cast<const char*>(a.bits + (size_t)b * 16) + (off - L::kBits);
+        cp_async16(st + off, src);
+    }
+    if (b_next >= 0 && t < 3) cp_async16(nbr_slot_next + 4 * t, a.nbr + (size_t)b_next * kNeighbours + 4 * t);
+}
+
+// Issues the halo copies of block b (needs its neighbour row in shared memory).
+template <typename T>
+__device__ inline void issue_halo(const SweepArgs<T>& a, char* st, const int* nb, int t) {
+    using L = StageLayout<T>;
+    if (t < kHalo) {
+        const HaloPos h = halo_pos(t);
+        const int n = nb[h.slot];
+        if (n >= 0) cp_async4(st + L::kHaloUb + 4 * t, word_addr(a.ub_in, (size_t)n * kBlockVoxels + h.src));
+    }
+    for (int i = t; i < 3 * kLowHalo; i += kSweepThreads) {
+        const int comp = i / kLowHalo, li = i - comp * kLowHalo;
+        const HaloPos h = halo_pos(low_hid(li));
+        const int n = nb[h.slot];
+        if (n >= 0)
+            cp_async4(st + L::kHaloP + 4 * i, word_addr(a.p_in + comp * a.pstride, (size_t)n * kBlockVoxels + h.src));
+    }
+    if (t < kNeighbours * 4) {
+        const int e = t >> 2, q = t & 3;
+        const int n = nb[e];
+        if (n >= 0) cp_async16(st + L::kNBits + 64 * e + 16 * q, a.bits + (size_t)n * 16 + 4 * q);
+    }
+}
+
+// Decodes a completed stage into the stencil tiles; returns the core voxel's values.
+template <typename T>
+__device__ inline void decode_stage(Tiles& s, const char* st, const int* nb, int t, int lx, int ly, int lz, bool& oc) {
+    using L = StageLayout<T>;
+    const T* cub = reinterpret_cast<const T*>(st + L::kUb);
+    const T* cp = reinterpret_cast<const T*>(st + L::kP);
+    const uint32_t* bits = reinterpret_cast<const uint32_t*>(st + L::kBits);
+    oc = (bits[t >> 5] >> (t & 31)) & 1u;
+    const int c = t10(lx, ly, lz), q = t9(lx, ly, lz);
+    s.v[c] = Store<T>::ld(cub + t);
+    s.om[c] = oc;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s.p[k][q] = Store<T>::ld(cp + k * kBlockVoxels + t);
+    if (t < kHalo) {
+        const HaloPos h = halo_pos(t);
+        const int n = nb[h.slot];
+        const int hc = t10(h.tx, h.ty, h.tz);
+        float hv = 0.0f;
+        bool ho = false;
+        if (n >= 0) {
+            hv = word_elem<T>(reinterpret_cast<const uint32_t*>(st + L::kHaloUb)[t], h.src);
+            const uint32_t* nbits = reinterpret_cast<const uint32_t*>(st + L::kNBits) + 16 * h.slot;
+            ho = (nbits[h.src >> 5] >> (h.src & 31)) & 1u;
+        }
+        s.v[hc] = hv;
+        s.om[hc] = ho;
+        const int li = low_index(t);
+        if (li >= 0) {
+            const int hq = t9(h.tx, h.ty, h.tz);
+            const uint32_t* hp = reinterpret_cast<const uint32_t*>(st + L::kHaloP);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s.p[k][hq] = n >= 0 ? word_elem<T>(hp[k * kLowHalo + li], h.src) : 0.0f;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSweepThreads, 2) sweep_pipe_kernel(SweepArgs<T> a) {
+    using L = StageLayout<T>;
+    extern __shared__ __align__(16) char smem[];
+    Tiles& s = *reinterpret_cast<Tiles*>(smem);
+    char* stage0 = smem + ((sizeof(Tiles) + 15) / 16) * 16;
+    int* ring = reinterpret_cast<int*>(stage0 + 2 * L::kBytes);  // [3][12]
+    const int t = threadIdx.x;
+    const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+    const int G = gridDim.x;
+    int b = blockIdx.x;
+    if (b >= a.n_blocks) return;
+    auto block_at = [&](int k) -> int {
+        const int i = blockIdx.x + k * G;
+        return i < a.n_blocks ? (a.order ? __ldg(a.order + i) : i) : -1;
+    };
+    int b_cur = block_at(0);
+    // prologue: neighbour row of the first block, then its core and halos
+    if (t < kNeighbours) ring[t] = __ldg(a.nbr + (size_t)b_cur * kNeighbours + t);
+    __syncthreads();
+    issue_core<T>(a, stage0, b_cur, ring + kNeighbours, block_at(1), t);
+    issue_halo<T>(a, stage0, ring, t);
+    cp_async_commit();
+    for (int k = 0; b_cur >= 0; ++k) {
+        char* st = stage0 + (k & 1) * L::kBytes;
+        const int* nb = ring + (k % 3) * kNeighbours;
+        cp_async_wait_all();
+        __syncthreads();
+        const int b_next = block_at(k + 1);
+        if (b_next >= 0) {
+            char* st2 = stage0 + ((k + 1) & 1) * L::kBytes;
+            issue_core<T>(a, st2, b_next, ring + ((k + 2) % 3) * kNeighbours, block_at(k + 2), t);
+            issue_halo<T>(a, st2, ring + ((k + 1) % 3) * kNeighbours, t);
+            cp_async_commit();
+        }
+        bool oc;
+        decode_stage<T>(s, st, nb, t, lx, ly, lz, oc);
+        const float uo = Store<T>::ld(reinterpret_cast<const T*>(st + L::kU) + t);
+        const float fv = reinterpret_cast<const float*>(st + L::kF)[t];
+        const float wv = reinterpret_cast<const float*>(st + L::kW)[t];
+        __syncthreads();
+        float pc[3], ph[3];
+        dual_step(s, lx, ly, lz, a.sigma, pc);
+        int hx = 0, hy = 0, hz = 0;
+        if (t < kLowHalo) {
+            low_pos(t, &hx, &hy, &hz);
+            dual_step(s, hx, hy, hz, a.sigma, ph);
+        }
+        __syncthreads();
+        {
+            const int q = t9(lx, ly, lz);
+            s.p[0][q] = pc[0], s.p[1][q] = pc[1], s.p[2][q] = pc[2];
+            if (t < kLowHalo) {
+                const int qh = t9(hx, hy, hz);
+                s.p[0][qh] = ph[0], s.p[1][qh] = ph[1], s.p[2][qh] = ph[2];
+            }
+        }
+        __syncthreads();
+        float un, ubn;
+        primal_update(oc, uo, oc ? divergence(s, lx, ly, lz) : 0.0f, fv, wv, a.tau, a.tau_lam, a.theta, &un, &ubn);
+        const size_t v = (size_t)b_cur * kBlockVoxels + t;
+        Store<T>::st(a.u + v, un);
+        Store<T>::st(a.ub_out + v, ubn);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Store<T>::st(a.p_out + c * a.pstride + v, pc[c]);
+        b_cur = b_next;
+    }
+}
+
+// --------------------------------------------------------------- row sweep
+// One 64-thread CTA per block at a time (grid-stride over the visiting order); thread
+// r owns the x-row (ly, lz) = (r & 7, r >> 3), i.e. 8 consecutive voxels that move as
+// 16-byte vectors.  x-neighbours stay in registers; only the y/z-neighbour rows and the
+// block faces pass through shared memory.  Every thread also takes the dual step at
+// the voxel just behind its row (the -x face), and the threads on the low y and z
+// faces take it on the neighbour rows behind them, because the divergence reads
+// p^{k+1} one voxel behind the block.
+constexpr int kRowThreads = 64;
+
+__device__ inline int r10(int ly, int lz) { return (ly + 1) + 10 * (lz + 1); }
+__device__ inline int r9(int ly, int lz) { return (ly + 1) + 9 * (lz + 1); }
+
+struct __align__(16) RowTiles {
+    float ub[100][8];        // u_bar rows (ly, lz) in [-1, 8]^2
+    float py[81][8];         // new p_y on rows (ly, lz) in [-1, 7]^2
+    float pz[81][8];         // new p_z
+    float pfy[3][8][8];      // old p on the -y face rows (-1, lz)
+    float pfz[3][8][8];      // old p on the -z face rows (ly, -1)
+    float xhp[100];          // u_bar at x = 8 of each row
+    float xhm[100];          // u_bar at x = -1 of each row
+    float pxm[64];           // new p_x at x = -1 of each block row
+    unsigned short om[100];  // Omega: bits 0-7 at x = 0..7, bit 8 at x = 8, bit 9 at x = -1
+};
+
+template <typename T>
+__device__ inline void ld_row(const T* __restrict__ p, float* v) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    } else {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+        const T* h = reinterpret_cast<const T*>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(h + i);
+    }
+}
+
+template <typename T>
+__device__ inline void st_row(T* p, const float* v) {
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+        uint4 q;
+        T* h = reinterpret_cast<T*>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Store<T>::st(h + i, v[i]);
+        *reinterpret_cast<uint4*>(p) = q;
+    }
+}
+
+__device__ inline void sts_row(float* dst, const float* v) {
+    reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+__device__ inline void lds_row(const float* src, float* v) {
+    const float4 a = reinterpret_cast<const float4*>(src)[0];
+    const float4 b = reinterpret_cast<const float4*>(src)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+
+// Omega bits of x-row `row` of block n (x = 0..7) in the low byte.
+__device__ inline unsigned row_bits(const uint32_t* __restrict__ bits, int n, int row) {
+    return (__ldg(bits + (size_t)n * 16 + (row >> 2)) >> (8 * (row & 3))) & 0xffu;
+}
+
+// Loads a full neighbour row (x = 0..7) of block n into tile row `dst` with its Omega
+// byte; zeros (Omega-bar) when the block is not allocated.
+template <typename T>
+__device__ inline unsigned load_face_row(const SweepArgs<T>& a, int n, int src_row, float* dst) {
+    float v[8];
+    unsigned om = 0;
+    if (n >= 0) {
+        ld_row<T>(a.ub_in + (size_t)n * kBlockVoxels + 8 * src_row, v);
+        om = row_bits(a.bits, n, src_row);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+    }
+    sts_row(dst, v);
+    return om;
+}
+
+// One voxel of a neighbour block (u_bar value and Omega bit at offset l).
+template <typename T>
+__device__ inline float load_voxel(const SweepArgs<T>& a, int n, int l, unsigned* bit) {
+    if (n < 0) {
+        *bit = 0;
+        return 0.0f;
+    }
+    *bit = (__ldg(a.bits + (size_t)n * 16 + (l >> 5)) >> (l & 31)) & 1u;
+    return Store<T>::ld(a.ub_in + (size_t)n * kBlockVoxels + l);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads, 8) sweep_rows_kernel(SweepArgs<T> a) {
+    __shared__ RowTiles s;
+    const int r = threadIdx.x;
+    const int ly = r & 7, lz = r >> 3;
+    const int rr = r10(ly, lz);
+    const size_t ps = a.pstride;
+    for (int k = blockIdx.x; k < a.n_blocks; k += gridDim.x) {
+        const int b = a.order ? __ldg(a.order + k) : k;
+        const int32_t* nb = a.nbr + (size_t)b * kNeighbours;
+        const size_t base = (size_t)b * kBlockVoxels + 8 * r;
+
+        // ---------------------------------------------------------- staging
+        float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
+        ld_row<T>(a.ub_in + base, ub);
+        ld_row<T>(a.p_in + base, p0);
+        ld_row<T>(a.p_in + ps + base, p1);
+        ld_row<T>(a.p_in + 2 * ps + base, p2);
+        ld_row<T>(a.u + base, uo);
+        {
+            const float4* f4 = reinterpret_cast<const float4*>(a.f + base);
+            const float4* w4 = reinterpret_cast<const float4*>(a.w + base);
+            const float4 fa = __ldg(f4), fb = __ldg(f4 + 1), wa = __ldg(w4), wb = __ldg(w4 + 1);
+            fv[0] = fa.x, fv[1] = fa.y, fv[2] = fa.z, fv[3] = fa.w, fv[4] = fb.x, fv[5] = fb.y, fv[6] = fb.z, fv[7] = fb.w;
+            wv[0] = wa.x, wv[1] = wa.y, wv[2] = wa.z, wv[3] = wa.w, wv[4] = wb.x, wv[5] = wb.y, wv[6] = wb.z, wv[7] = wb.w;
+        }
+        unsigned om_r = row_bits(a.bits, b, r);
+        // x halos of the row: u_bar and Omega at x = 8 and x = -1, old p at x = -1
+        float hm0 = 0.0f, hm1 = 0.0f, hm2 = 0.0f;
+        {
+            unsigned bit;
+            const float xp = load_voxel<T>(a, __ldg(nb + 0), 8 * r, &bit);
+            om_r |= bit << 8;
+            const int n3 = __ldg(nb + 3);
+            const float xm = load_voxel<T>(a, n3, 8 * r + 7, &bit);
+            om_r |= bit << 9;
+            if (n3 >= 0) {
+                const size_t o3 = (size_t)n3 * kBlockVoxels + 8 * r + 7;
+                hm0 = Store<T>::ld(a.p_in + o3);
+                hm1 = Store<T>::ld(a.p_in + ps + o3);
+                hm2 = Store<T>::ld(a.p_in + 2 * ps + o3);
+            }
+            s.xhp[rr] = xp;
+            s.xhm[rr] = xm;
+        }
+        sts_row(s.ub[rr], ub);
+        s.om[rr] = (unsigned short)om_r;
+        // faces and edges
+        if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
+            const int d = r10(8, lz);
+            unsigned om = load_face_row<T>(a, __ldg(nb + 1), 8 * lz, s.ub[d]), bit;
+            s.xhm[d] = load_voxel<T>(a, __ldg(nb + 6), 8 * (8 * lz) + 7, &bit);
+            s.om[d] = (unsigned short)(om | (bit << 9));
+        }
+        if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
+            const int d = r10(-1, lz);
+            const int n4 = __ldg(nb + 4);
+            unsigned om = load_face_row<T>(a, n4, 7 + 8 * lz, s.ub[d]), bit;
+            s.xhp[d] = load_voxel<T>(a, __ldg(nb + 8), 8 * (7 + 8 * lz), &bit);
+            s.om[d] = (unsigned short)(om | (bit << 8));
+            float q[8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (n4 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n4 * kBlockVoxels + 8 * (7 + 8 * lz), q);
+                else
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+                sts_row(s.pfy[c][lz], q);
+            }
+        }
+        if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
+            const int d = r10(ly, 8);
+            unsigned om = load_face_row<T>(a, __ldg(nb + 2), ly, s.ub[d]), bit;
+            s.xhm[d] = load_voxel<T>(a, __ldg(nb + 7), 8 * ly + 7, &bit);
+            s.om[d] = (unsigned short)(om | (bit << 9));
+        }
+        if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
+            const int d = r10(ly, -1);
+            const int n5 = __ldg(nb + 5);
+            unsigned om = load_face_row<T>(a, n5, ly + 56, s.ub[d]), bit;
+            s.xhp[d] = load_voxel<T>(a, __ldg(nb + 10), 8 * (ly + 56), &bit);
+            s.om[d] = (unsigned short)(om | (bit << 8));
+            float q[8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (n5 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n5 * kBlockVoxels + 8 * (ly + 56), q);
+                else
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+                sts_row(s.pfz[c][ly], q);
+            }
+        }
+        if (ly == 0 && lz == 7)  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
+            s.om[r10(-1, 8)] = (unsigned short)load_face_row<T>(a, __ldg(nb + 9), 7, s.ub[r10(-1, 8)]);
+        if (ly == 7 && lz == 0)  // edge row (8, -1) <- block (-z,+y) row (0, 7)
+            s.om[r10(8, -1)] = (unsigned short)load_face_row<T>(a, __ldg(nb + 11), 56, s.ub[r10(8, -1)]);
+        __syncthreads();
+
+        // ------------------------------------------------------- dual steps
+        {
+            float uy[8], uz[8];
+            lds_row(s.ub[r10(ly + 1, lz)], uy);
+            lds_row(s.ub[r10(ly, lz + 1)], uz);
+            const unsigned om_y = s.om[r10(ly + 1, lz)], om_z = s.om[r10(ly, lz + 1)];
+            const float xp = s.xhp[rr];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const bool o = (om_r >> x) & 1u;
+                const float g0 = masked_diff(o && ((om_r >> (x + 1)) & 1u), x < 7 ? ub[x < 7 ? x + 1 : 7] : xp, ub[x]);
+                const float g1 = masked_diff(o && ((om_y >> x) & 1u), uy[x], ub[x]);
+                const float g2 = masked_diff(o && ((om_z >> x) & 1u), uz[x], ub[x]);
+                float out[3];
+                dual_update(p0[x], p1[x], p2[x], g0, g1, g2, a.sigma, out);
+                p0[x] = out[0], p1[x] = out[1], p2[x] = out[2];
+            }
+            // the -x face voxel (-1, ly, lz)
+            const bool o = (om_r >> 9) & 1u;
+            const float um = s.xhm[rr];
+            const int ry = r10(ly + 1, lz), rz = r10(ly, lz + 1);
+            const float g0 = masked_diff(o && (om_r & 1u), ub[0], um);
+            const float g1 = masked_diff(o && ((s.om[ry] >> 9) & 1u), s.xhm[ry], um);
+            const float g2 = masked_diff(o && ((s.om[rz] >> 9) & 1u), s.xhm[rz], um);
+            float out[3];
+            dual_update(hm0, hm1, hm2, g0, g1, g2, a.sigma, out);
+            s.pxm[r] = out[0];
+        }
+        {
+            // one voxel of the -y face, (fx, -1, fz), and one of the -z face, (fx, fy, -1)
+            const int fx = r & 7, fw = r >> 3;
+            {  // -y face: fw is z
+                const int d = r10(-1, fw), dz = r10(-1, fw + 1), dc = r10(0, fw);
+                const unsigned om = s.om[d];
+                const bool o = (om >> fx) & 1u;
+                const float v = s.ub[d][fx];
+                const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
+                const float g1 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
+                const float g2 = masked_diff(o && ((s.om[dz] >> fx) & 1u), s.ub[dz][fx], v);
+                float out[3];
+                dual_update(s.pfy[0][fw][fx], s.pfy[1][fw][fx], s.pfy[2][fw][fx], g0, g1, g2, a.sigma, out);
+                s.py[r9(-1, fw)][fx] = out[1];
+            }
+            {  // -z face: fw is y
+                const int d = r10(fw, -1), dy = r10(fw + 1, -1), dc = r10(fw, 0);
+                const unsigned om = s.om[d];
+                const bool o = (om >> fx) & 1u;
+                const float v = s.ub[d][fx];
+                const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
+                const float g1 = masked_diff(o && ((s.om[dy] >> fx) & 1u), s.ub[dy][fx], v);
+                const float g2 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
+                float out[3];
+                dual_update(s.pfz[0][fw][fx], s.pfz[1][fw][fx], s.pfz[2][fw][fx], g0, g1, g2, a.sigma, out);
+                s.pz[r9(fw, -1)][fx] = out[2];
+            }
+        }
+        sts_row(s.py[r9(ly, lz)], p1);
+        sts_row(s.pz[r9(ly, lz)], p2);
+        __syncthreads();
+
+        // ----------------------------------------------- primal + relaxation
+        {
+            float pym[8], pzm[8];
+            lds_row(s.py[r9(ly - 1, lz)], pym);
+            lds_row(s.pz[r9(ly, lz - 1)], pzm);
+            const unsigned om_ym = s.om[r10(ly - 1, lz)], om_zm = s.om[r10(ly, lz - 1)];
+            const unsigned om_yp = s.om[r10(ly + 1, lz)], om_zp = s.om[r10(ly, lz + 1)];
+            const float pxm = s.pxm[r];
+            float un[8], ubn[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const bool o = (om_r >> x) & 1u;
+                const bool exm = o && (x > 0 ? ((om_r >> (x - 1)) & 1u) : ((om_r >> 9) & 1u));
+                const float dv = div_terms(o && ((om_r >> (x + 1)) & 1u), p0[x], exm, x > 0 ? p0[x > 0 ? x - 1 : 0] : pxm,
+                                           o && ((om_yp >> x) & 1u), p1[x], o && ((om_ym >> x) & 1u), pym[x],
+                                           o && ((om_zp >> x) & 1u), p2[x], o && ((om_zm >> x) & 1u), pzm[x]);
+                primal_update(o, uo[x], o ? dv : 0.0f, fv[x], wv[x], a.tau, a.tau_lam, a.theta, &un[x], &ubn[x]);
+            }
+            st_row<T>(a.u + base, un);
+            st_row<T>(a.ub_out + base, ubn);
+            st_row<T>(a.p_out + base, p0);
+            st_row<T>(a.p_out + ps + base, p1);
+            st_row<T>(a.p_out + 2 * ps + base, p2);
+        }
+        __syncthreads();  // the tiles are rewritten for the next block
+    }
+}
+
+template <typename T>
+constexpr size_t sweep_pipe_smem() {
+    return ((sizeof(Tiles) + 15) / 16) * 16 + 2 * StageLayout<T>::kBytes + 3 * kNeighbours * sizeof(int);
 }
 
 template <typename T>
@@ -352,8 +881,22 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
     a.tau = (float)c->prm.tau;
     a.tau_lam = (float)(c->prm.tau * c->prm.lambda);
     a.theta = (float)c->prm.theta;
-    const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * 4);
-    sweep_kernel<T><<<grid, kSweepThreads, 0, s>>>(a);
+    a.order = c->sched.order ? c->order : nullptr;
+    if (c->sched.sweep_kernel == 0) {
+        const int per_sm = c->sched.ctas_per_sm > 0 ? c->sched.ctas_per_sm : 4;
+        const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * per_sm);
+        sweep_kernel<T><<<grid, kSweepThreads, 0, s>>>(a);
+    } else if (c->sched.sweep_kernel == 2) {
+        int per_sm = c->sched.ctas_per_sm * 4;  // 64-thread CTAs: four per 256 threads
+        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T>, kRowThreads, 0);
+        if (per_sm <= 0) per_sm = 8;
+        const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * per_sm);
+        sweep_rows_kernel<T><<<grid, kRowThreads, 0, s>>>(a);
+    } else {
+        const int per_sm = c->sched.ctas_per_sm > 0 ? c->sched.ctas_per_sm : 2;
+        const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * per_sm);
+        sweep_pipe_kernel<T><<<grid, kSweepThreads, sweep_pipe_smem<T>(), s>>>(a);
+    }
 }
 
 template <typename T>
@@ -367,8 +910,24 @@ void energy_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
 
 }  // namespace
 
+int configure_kernels(denser_ctx* c) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_pipe_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sweep_pipe_smem<float>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_pipe_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sweep_pipe_smem<__half>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_pipe_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sweep_pipe_smem<__nv_bfloat16>());
+    return cuda_check(c, e, "configure sweep kernels");
+}
+
 int launch_prepare_regularize(denser_ctx* c, int64_t nb, bool rebuild_nbr, cudaStream_t s) {
     if (nb <= 0) return DENSER_OK;
+    if (c->sched.order && c->order_valid_blocks != nb) {
+        int rc = launch_block_order(c, nb, s);
+        if (rc) return rc;
+    }
     omega_bits_kernel<<<grid_for(c->sm_count, nb * 32, 256, 8), 256, 0, s>>>(c->d.w, c->d.omega_bits, (int)nb);
     c->launches += 1;
     if (rebuild_nbr) {

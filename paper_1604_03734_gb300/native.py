@@ -28,7 +28,8 @@ DENSER_FP32, DENSER_FP16, DENSER_BF16 = 0, 1, 2
 EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_reset",
            "denser_last_error", "denser_sync", "denser_alloc_blocks", "denser_fuse_depth",
            "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual",
-           "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count")
+           "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
+           "denser_set_schedule", "denser_get_schedule")
 
 
 class denser_params(ctypes.Structure):
@@ -53,6 +54,11 @@ class denser_reg_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class denser_schedule(ctypes.Structure):
+    _fields_ = [("sweep_kernel", ctypes.c_int32), ("order", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class DenserError(RuntimeError):
@@ -90,6 +96,8 @@ def lib():
             "denser_load_state": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
             "denser_num_blocks": (_i64, [_vp, _vp]),
             "denser_launch_count": (_u64, [_vp]),
+            "denser_set_schedule": (_i32, [_vp, P(denser_schedule)]),
+            "denser_get_schedule": (_i32, [_vp, P(denser_schedule)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -248,6 +256,17 @@ def denser_num_blocks(ctx, stream=None) -> int:
 
 def denser_launch_count(ctx) -> int:
     return int(lib().denser_launch_count(ctx))
+
+
+def denser_set_schedule(ctx, sweep_kernel=1, order=1, ctas_per_sm=0):
+    sch = denser_schedule(int(sweep_kernel), int(order), int(ctas_per_sm), 0)
+    return _check(ctx, lib().denser_set_schedule(ctx, ctypes.byref(sch)))
+
+
+def denser_get_schedule(ctx) -> dict:
+    sch = denser_schedule()
+    _check(ctx, lib().denser_get_schedule(ctx, ctypes.byref(sch)))
+    return {"sweep_kernel": sch.sweep_kernel, "order": sch.order, "ctas_per_sm": sch.ctas_per_sm}
 
 
 # ------------------------------------------------------------ convenience

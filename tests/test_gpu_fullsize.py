@@ -1,0 +1,114 @@
+"""Full-size driving street (200 depth maps 1241x376, 200 iterations) in the context
+configuration bench.py times, checked against the oracle on what it can compute:
+
+  * allocation: the blocks of the first frames bit-exact (keys and indices), and every
+    key the oracle finds for later frames present;
+  * fusion: 48 sampled blocks fused by the oracle with every frame from the one that
+    allocated them on (w bit-exact, f within 1e-4);
+  * regularisation: from the GPU state after 200 iterations, one more GPU iteration
+    equals one oracle iteration on sampled blocks (the update of a block only reads
+    its 26-neighbourhood), and the FP64 gap is non-negative.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import denser_oracle as O
+from tests.oracle_helpers import grid_from_blocks
+from tests.pipelines import oracle_K
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1604_03734_gb300 import native as N  # noqa: E402
+from synth.scenes import street_scene  # noqa: E402
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def street():
+    s = street_scene(seed=0)
+    d = s.depth_maps()
+    cam = s.camera
+    K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    m = N.DenserMap(max_blocks=1 << 17, hash_slots=1 << 20)
+    dd = torch.from_numpy(d).cuda()
+    news = []   # blocks allocated after each frame
+    for k in range(len(d)):
+        N.denser_alloc_blocks(m.ctx, dd[k], K, s.poses[k])
+        N.denser_fuse_depth(m.ctx, dd[k], K, s.poses[k])
+        news.append(N.denser_num_blocks(m.ctx))
+    snap = m.snapshot()
+    yield s, d, m, snap, news
+    m.close()
+
+
+def test_full_allocation(street):
+    s, d, m, snap, news = street
+    K = oracle_K(s.camera)
+    g = O.SparseGrid(O.Params())
+    for k in range(3):
+        O.alloc_blocks(g, d[k], K, s.poses[k])
+        assert g.n_blocks == news[k]
+    np.testing.assert_array_equal(snap["coords"][:g.n_blocks], g.coords().astype(np.int32))
+    have = set(map(tuple, snap["coords"].tolist()))
+    for k in (57, 123, 199):
+        keys = O.frame_block_keys(d[k], K, s.poses[k], O.Params())
+        assert keys <= have, len(keys - have)
+    assert len(have) == len(snap["coords"]) > 10000
+
+
+def test_full_fusion_sampled_blocks(street):
+    s, d, m, snap, news = street
+    rng = np.random.default_rng(0)
+    sel = rng.choice(len(snap["coords"]), 48, replace=False)
+    g = grid_from_blocks([tuple(c) for c in snap["coords"][sel]])
+    K = oracle_K(s.camera)
+    # a block exists from the frame that allocated it on: fuse only later frames into it
+    born = np.searchsorted(np.array(news), sel, side="right")
+    for k in range(len(d)):
+        O.fuse_depth(g, d[k], K, s.poses[k], blocks=np.nonzero(born <= k)[0])
+    np.testing.assert_array_equal(snap["w"][sel], g.w.astype(np.float32))
+    assert np.max(np.abs(snap["f"][sel] - g.f)) <= TOL
+    assert g.w.sum() > 0
+
+
+def test_full_regularize_step_consistency(street):
+    s, d, m, snap, _ = street
+    st = N.denser_regularize(m.ctx, 200)
+    assert st.gap >= 0 and st.iters == 200
+    before = m.snapshot(dual=True)
+    N.denser_regularize(m.ctx, 1, 0.0, 1)
+    after = m.snapshot(dual=True)
+    coords = before["coords"]
+    index = {tuple(c): i for i, c in enumerate(coords.tolist())}
+    rng = np.random.default_rng(1)
+    sample = rng.choice(len(coords), 24, replace=False)
+    # sampled blocks first, then their allocated 26-neighbours
+    keys = [tuple(coords[i]) for i in sample]
+    seen = set(keys)
+    for c in list(keys):
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    q = (c[0], c[1] + dx, c[2] + dy, c[3] + dz)
+                    if q in index and q not in seen:
+                        seen.add(q)
+                        keys.append(q)
+    rows = [index[k] for k in keys]
+    g = grid_from_blocks(keys, before["f"][rows].astype(np.float64), before["w"][rows].astype(np.float64))
+    prob = O.PDProblem(g)
+    u1, ub1, p1 = O.pd_iterate(prob, before["u"][rows].reshape(-1).astype(np.float64),
+                               before["u_bar"][rows].reshape(-1).astype(np.float64),
+                               before["p"][:, rows].reshape(3, -1).astype(np.float64), 1, g.params)
+    n = len(sample)
+    nv = n * 512
+    assert np.max(np.abs(after["u"][sample].reshape(-1) - u1[:nv])) <= 2e-6
+    assert np.max(np.abs(after["u_bar"][sample].reshape(-1) - ub1[:nv])) <= 4e-6
+    assert np.max(np.abs(after["p"][:, sample].reshape(3, -1) - p1[:, :nv])) <= 2e-6
+    om = before["omega"].astype(bool)
+    assert np.all(after["u"][~om] == 0)
+    assert np.all(np.sqrt((after["p"] ** 2).sum(0)) <= 1 + 1e-6)

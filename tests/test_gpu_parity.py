@@ -285,3 +285,36 @@ def test_error_paths():
             N.denser_load_blocks(m.ctx, coords[:1])
         assert e.value.code == N.DENSER_ERR_INVALID_ARG
         assert N.denser_launch_count(m.ctx) > 0
+
+
+@pytest.mark.parametrize("sched", [(0, 0, 0), (0, 1, 2), (1, 0, 0), (1, 1, 1), (2, 0, 0), (2, 1, 0), (2, 1, 3)])
+def test_schedules_give_identical_iterates(tiny, sched):
+    """Every sweep schedule (kernel variant, visiting order, CTAs per SM) computes the
+    same Jacobi iterates bit for bit, and matches the oracle."""
+    s, d = tiny
+    g, _, _ = run_oracle(s, d, 40)
+    ref = None
+    with N.DenserMap() as m:
+        cam = s.camera
+        K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+        for k in range(len(d)):
+            N.denser_alloc_blocks(m.ctx, d[k], K, s.poses[k])
+            N.denser_fuse_depth(m.ctx, d[k], K, s.poses[k])
+        N.denser_set_schedule(m.ctx, 1, 1, 0)
+        N.denser_regularize(m.ctx, 40)
+        ref = m.snapshot(dual=True)
+        N.denser_set_schedule(m.ctx, *sched)
+        assert N.denser_get_schedule(m.ctx) == dict(zip(("sweep_kernel", "order", "ctas_per_sm"), sched))
+        N.denser_regularize(m.ctx, 40)
+        out = m.snapshot(dual=True)
+    for k in ("u", "u_bar", "p"):
+        np.testing.assert_array_equal(out[k], ref[k])
+    assert np.max(np.abs(out["u"] - g.u)) <= TOL and np.max(np.abs(out["p"] - g.p)) <= TOL
+
+
+def test_schedule_rejects_bad_fields():
+    with N.DenserMap() as m:
+        with pytest.raises(N.DenserError):
+            N.denser_set_schedule(m.ctx, 3, 0, 0)
+        with pytest.raises(N.DenserError):
+            N.denser_set_schedule(m.ctx, 1, 0, 9)
