@@ -54,6 +54,7 @@ extern "C" {
 #define DENSER_ERR_CUDA (-4)        /* a CUDA runtime call failed; see denser_last_error */
 #define DENSER_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
 #define DENSER_ERR_RANGE (-6)       /* a block coordinate outside +-2^18 or a bad segment */
+#define DENSER_ERR_TOO_LARGE (-7)   /* more blocks than denser_energy_noalloc can hold */
 
 #define DENSER_FP32 0
 #define DENSER_FP16 1
@@ -202,6 +203,30 @@ int64_t denser_num_blocks(denser_ctx* ctx, void* stream);
 
 /* Kernels this context has launched since it was created. */
 uint64_t denser_launch_count(const denser_ctx* ctx);
+
+/* Energies without allocation.  The paper has no counterpart to this call; it exists
+ * for callers that may not allocate device memory: a process whose device memory all
+ * belongs to its own allocator (a framework's caching allocator, or the fixed memory
+ * budget of an on-vehicle mapping process) must not call cudaMalloc behind it, and a
+ * latency-critical loop cannot take the device-wide synchronisation that cudaMalloc
+ * and cudaFree may cause.  It computes the same P(u) and D(p) as denser_energy, but
+ * from caller-owned buffers and with no context: coords int32 [n][4], f, w, u float32
+ * [n][512] and p float32 [3][n][512], all in device memory, in the layouts that
+ * denser_extract and denser_extract_dual write.  out (host or device memory) receives
+ * {P, D}; with a host `out` the call waits for the stream.
+ * Its only working memory is a fixed 2.2 MB array in device memory that every GPU which
+ * loads the library holds until the process exits.  That size caps the map at
+ * DENSER_NOALLOC_MAX_BLOCKS blocks: a larger n_blocks returns DENSER_ERR_TOO_LARGE.
+ * The first call on a device looks the array's address up for that device (a one-time
+ * set-up): make that first call outside any stream capture.  All calls on a device
+ * share the array, which keeps the contents of the last call; the call clears what it
+ * needs, but calls whose work overlaps on the GPU (different streams, or different
+ * host threads) race and must be serialised by the caller.  Repeated or out-of-range
+ * coordinates give NaN energies.  Returns DENSER_ERR_INVALID_ARG for host input
+ * pointers, NULL pointers or lambda <= 0. */
+#define DENSER_NOALLOC_MAX_BLOCKS 16384
+int denser_energy_noalloc(const int32_t* coords, const float* f, const float* w, const float* u,
+                          const float* p, int64_t n_blocks, double lambda, double* out, void* stream);
 
 #ifdef __cplusplus
 }

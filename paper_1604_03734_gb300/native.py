@@ -22,6 +22,8 @@ DENSER_ERR_POOL_FULL = -3
 DENSER_ERR_CUDA = -4
 DENSER_ERR_TIMEOUT = -5
 DENSER_ERR_RANGE = -6
+DENSER_ERR_TOO_LARGE = -7
+DENSER_NOALLOC_MAX_BLOCKS = 16384
 DENSER_FP32, DENSER_FP16, DENSER_BF16 = 0, 1, 2
 
 # every symbol include/denser.h declares
@@ -29,7 +31,7 @@ EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_r
            "denser_last_error", "denser_sync", "denser_alloc_blocks", "denser_fuse_depth",
            "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual",
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
-           "denser_set_schedule", "denser_get_schedule")
+           "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc")
 
 
 class denser_params(ctypes.Structure):
@@ -98,6 +100,7 @@ def lib():
             "denser_launch_count": (_u64, [_vp]),
             "denser_set_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_get_schedule": (_i32, [_vp, P(denser_schedule)]),
+            "denser_energy_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _dbl, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -267,6 +270,14 @@ def denser_get_schedule(ctx) -> dict:
     sch = denser_schedule()
     _check(ctx, lib().denser_get_schedule(ctx, ctypes.byref(sch)))
     return {"sweep_kernel": sch.sweep_kernel, "order": sch.order, "ctas_per_sm": sch.ctas_per_sm}
+
+
+def denser_energy_noalloc(coords, f, w, u, p, n_blocks, lam, out, stream=None) -> int:
+    """Energies {P, D} into ``out`` (2 float64, host or device) from caller-owned device
+    buffers, with no device allocation; returns the C status code (0 = OK)."""
+    return int(lib().denser_energy_noalloc(_ptr(coords, np.int32), _ptr(f, np.float32), _ptr(w, np.float32),
+                                           _ptr(u, np.float32), _ptr(p, np.float32), int(n_blocks), float(lam),
+                                           _ptr(out, np.float64), _stream(stream)))
 
 
 # ------------------------------------------------------------ convenience
