@@ -81,7 +81,7 @@ typedef struct {
 
 typedef struct {
     double fx, fy, cx, cy;    /* pixels; pixel (x, y) covers [x, x+1) x [y, y+1) */
-    int32_t width, height;
+    int32_t width, height;    /* each at most 2^20, width * height < 2^31 */
 } denser_intrinsics;
 
 typedef struct {

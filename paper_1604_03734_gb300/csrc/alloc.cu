@@ -28,10 +28,12 @@ struct AllocArgs {
     double bs;  // block size 8 s
     double R[9];
     double t[3];
-    double ifx, ify, ibs;  // 1/fx, 1/fy, 1/bs (float32 fast path only)
     int Ti[3];             // floor(t / bs)
     float tf[3];           // t / bs - Ti, in [0, 1)
     float hf;              // h as float32
+    float cx_hi, cx_lo, cy_hi, cy_lo;  // principal point as float32 hi + lo
+    float ifx, ify, ibs;   // 1/fx, 1/fy, 1/bs as float32
+    float Rf[9];           // R as float32
     int W, H, N, seg;
 };
 
@@ -92,39 +94,42 @@ __device__ unsigned long long sample_key(const AllocArgs& a, int x, int y, doubl
 
 // Float32 evaluation of sample n's key with a forward error bound.  The key of a
 // sample is floor(t/bs + z D), D = R (u/fx, v/fy, 1) / bs the pixel's ray step per
-// metre of depth in block units (computed once per pixel in float64, rounded to
-// float32), z = d + n h.  Returns 1 when every floor is certified (key or kEmptyKey
-// for z <= 0 in *key), 0 when the float64 path must decide.
-__device__ inline int sample_key_f32(const AllocArgs& a, const float* D, float d, int n, bool* range_err,
-                                     unsigned long long* key) {
+// metre of depth in block units, z = d + n h.  D is evaluated once per pixel in float32
+// and DA bounds the magnitude of its terms (its rounding error is below 2^-21 DA).
+// Returns 1 when every floor is certified (key, or kEmptyKey for z <= 0, in *key),
+// 0 when the float64 path must decide.
+__device__ inline int sample_key_f32(const AllocArgs& a, const float* D, const float* DA, float d, float nf,
+                                     bool* range_err, unsigned long long* key) {
     const float eps = 9.53674316e-7f;  // 2^-20
     const float nh = (float)a.N * a.hf;
-    const float z = fmaf((float)n, a.hf, d);
+    const float z = fmaf(nf, a.hf, d);
     const float ez = eps * (fabsf(d) + nh) + 1e-30f;
     if (z < -ez) {
         *key = kEmptyKey;
         return 1;
     }
     if (!(z > ez)) return 0;
-    float kf[3];
+    int kf[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const float q = fmaf(z, D[r], a.tf[r]);
-        const float e = eps * (fabsf(D[r]) * (z + nh) + fabsf(q) + 1.0f);
-        const float lo = floorf(q - e);
-        if (lo != floorf(q + e)) return 0;
+        if (!(fabsf(q) < 2097152.0f)) {  // |q| >= 2^21: the key is beyond 2^18 whatever Ti is
+            *range_err = true;
+            *key = kEmptyKey;
+            return 1;
+        }
+        const float e = eps * (DA[r] * (z + nh) + fabsf(q) + 1.0f);
+        const int lo = floor_small(q - e);
+        if (lo != floor_small(q + e)) return 0;
         kf[r] = lo;
     }
-    const float lim = (float)kCoordBias;
-    long long k0 = (long long)a.Ti[0] + (long long)kf[0], k1 = (long long)a.Ti[1] + (long long)kf[1],
-              k2 = (long long)a.Ti[2] + (long long)kf[2];
-    if (!(fabsf(kf[0]) < 4.0f * lim && fabsf(kf[1]) < 4.0f * lim && fabsf(kf[2]) < 4.0f * lim) ||
-        !key_in_range(a.seg, k0, k1, k2)) {
+    const int k0 = a.Ti[0] + kf[0], k1 = a.Ti[1] + kf[1], k2 = a.Ti[2] + kf[2];
+    if (!key_in_range(a.seg, k0, k1, k2)) {
         *range_err = true;
         *key = kEmptyKey;
         return 1;
     }
-    *key = pack_key(a.seg, (int32_t)k0, (int32_t)k1, (int32_t)k2);
+    *key = pack_key(a.seg, k0, k1, k2);
     return 1;
 }
 
@@ -138,18 +143,24 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
         float dv = pix < npix ? __ldg(depth + pix) : 0.0f;
         const bool valid = pix < npix && isfinite(dv) && dv > 0.0f;
         const int x = pix % a.W, y = pix / a.W;
-        float D[3] = {0.0f, 0.0f, 0.0f};
+        float D[3] = {0.0f, 0.0f, 0.0f}, DA[3] = {0.0f, 0.0f, 0.0f};
         if (valid) {
-            const double ua = ((double)x + 0.5 - a.cx) * a.ifx;
-            const double va = ((double)y + 0.5 - a.cy) * a.ify;
+            // u = (x + 0.5) - cx with cx as hi + lo: relative error below 2^-23
+            const float ua = (((float)x + 0.5f) - a.cx_hi) - a.cx_lo;
+            const float va = (((float)y + 0.5f) - a.cy_hi) - a.cy_lo;
+            const float ax = ua * a.ifx, ay = va * a.ify;
 #pragma unroll
-            for (int r = 0; r < 3; ++r) D[r] = (float)((a.R[3 * r] * ua + a.R[3 * r + 1] * va + a.R[3 * r + 2]) * a.ibs);
+            for (int r = 0; r < 3; ++r) {
+                D[r] = fmaf(a.Rf[3 * r], ax, fmaf(a.Rf[3 * r + 1], ay, a.Rf[3 * r + 2])) * a.ibs;
+                DA[r] = (fabsf(a.Rf[3 * r] * ax) + fabsf(a.Rf[3 * r + 1] * ay) + fabsf(a.Rf[3 * r + 2])) * a.ibs;
+            }
         }
         unsigned long long last = kEmptyKey;
-        for (int n = -a.N; n <= a.N; ++n) {
+        float nf = (float)(-a.N);
+        for (int n = -a.N; n <= a.N; ++n, nf += 1.0f) {
             unsigned long long key = kEmptyKey;
             if (valid) {
-                if (!sample_key_f32(a, D, dv, n, &range_err, &key))
+                if (!sample_key_f32(a, D, DA, dv, nf, &range_err, &key))
                     key = sample_key(a, x, y, (double)dv, n, &range_err);
                 if (key == last) key = kEmptyKey;  // consecutive samples in one block
                 else if (key != kEmptyKey) last = key;
@@ -355,7 +366,10 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
     }
     a.W = K->width, a.H = K->height;
     a.N = (int)ceil(c->prm.mu / a.h - 1e-9);
-    a.ifx = 1.0 / a.fx, a.ify = 1.0 / a.fy, a.ibs = 1.0 / a.bs;
+    a.ifx = (float)(1.0 / a.fx), a.ify = (float)(1.0 / a.fy), a.ibs = (float)(1.0 / a.bs);
+    a.cx_hi = (float)a.cx, a.cx_lo = (float)(a.cx - (double)a.cx_hi);
+    a.cy_hi = (float)a.cy, a.cy_lo = (float)(a.cy - (double)a.cy_hi);
+    for (int e = 0; e < 9; ++e) a.Rf[e] = (float)a.R[e];
     for (int r = 0; r < 3; ++r) {
         const double tb = a.t[r] / a.bs;
         const double ti = floor(tb);

@@ -109,7 +109,8 @@ int read_counters(denser_ctx* c, cudaStream_t s) {
 }
 
 bool valid_intrinsics(const denser_intrinsics* K) {
-    return K && K->width > 0 && K->height > 0 && (int64_t)K->width * K->height < (1ll << 31) &&
+    return K && K->width > 0 && K->height > 0 && K->width <= (1 << 20) && K->height <= (1 << 20) &&
+           (int64_t)K->width * K->height < (1ll << 31) &&
            isfinite(K->fx) && isfinite(K->fy) && isfinite(K->cx) && isfinite(K->cy) && K->fx > 0 && K->fy > 0;
 }
 

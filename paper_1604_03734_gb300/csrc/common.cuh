@@ -195,6 +195,14 @@ __host__ __device__ inline void neighbour_offset(int i, int* dx, int* dy, int* d
     *dz = t[i][2];
 }
 
+// floor(v) for |v| < 2^22 using only an FP32 add in round-down mode and an integer
+// subtract: v + 1.5*2^23 lands in [2^23, 2^24), where the float spacing is 1, so its
+// mantissa holds floor(v).  (Conversions from float to 64-bit integers and the
+// rounding instructions run on the narrow FP64 pipe of this GPU; this does not.)
+__device__ inline int floor_small(float v) {
+    return __float_as_int(__fadd_rd(v, 12582912.0f)) - 0x4B400000;
+}
+
 inline int grid_for(int sm_count, long long work, int threads, int per_sm) {
     long long g = (work + threads - 1) / threads;
     long long cap = (long long)sm_count * per_sm;

@@ -29,7 +29,7 @@ struct FuseArgs {
     double plane[4][3];  // unit normals of the four side planes (camera frame)
     double radius;       // bounding-sphere radius of a block's voxel centres, padded
     float M[9];          // s R^T: camera-frame step per local voxel index (float32)
-    float fxf, fyf, cxf, cyf, muf, sf;
+    float fxf, fyf, cxf, cyf, muf, sf, Wf, Hf;
     int W, H, seg;
 };
 
@@ -81,37 +81,48 @@ __global__ void cull_kernel(DeviceMap m, FuseArgs a) {
     const int dbits = m.counters[kDepthMaxBits];
     if (dbits == 0) return;  // no valid pixel: nothing can change
     const double far = (double)__int_as_float(dbits) + a.mu;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        const int4 k = reinterpret_cast<const int4*>(m.coords)[b];
-        if (k.x != a.seg) continue;
-        // centre of the block's voxel centres: voxel index 8 b + 3.5 -> (8 b + 4) s
-        double c[3];
-        to_camera(a, (8.0 * k.y + 4.0) * a.s, (8.0 * k.z + 4.0) * a.s, (8.0 * k.w + 4.0) * a.s, c);
-        const double r = a.radius;
-        if (c[2] + r < 0.0) continue;    // every voxel behind the camera
-        if (c[2] - r > far) continue;    // every voxel beyond any depth + mu
-        bool out = false;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            out |= a.plane[q][0] * c[0] + a.plane[q][1] * c[1] + a.plane[q][2] * c[2] < -r;
-        if (out) continue;
-        double c0[3];
-        to_camera(a, __dmul_rn(__dadd_rn((double)(8 * k.y), 0.5), a.s), __dmul_rn(__dadd_rn((double)(8 * k.z), 0.5), a.s),
-                  __dmul_rn(__dadd_rn((double)(8 * k.w), 0.5), a.s), c0);
+    const int lane = threadIdx.x & 31;
+    // warp-uniform loop bound: every lane reaches the ballot
+    for (int base = blockIdx.x * blockDim.x; base < nb; base += gridDim.x * blockDim.x) {
+        const int b = base + (int)threadIdx.x;
+        bool keep = false;
         VisBlock vb;
-        vb.b = b;
-        double amax = 0.0;
+        if (b < nb) {
+            const int4 k = reinterpret_cast<const int4*>(m.coords)[b];
+            if (k.x == a.seg) {
+                // centre of the block's voxel centres: voxel index 8 b + 3.5 -> (8 b + 4) s
+                double c[3];
+                to_camera(a, (8.0 * k.y + 4.0) * a.s, (8.0 * k.z + 4.0) * a.s, (8.0 * k.w + 4.0) * a.s, c);
+                const double r = a.radius;
+                keep = c[2] + r >= 0.0 && c[2] - r <= far;  // not all behind, not all beyond d + mu
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            vb.hi[e] = (float)c0[e];
-            vb.lo[e] = (float)(c0[e] - (double)vb.hi[e]);
-            amax = fmax(amax, fabs(c0[e]));
+                for (int q = 0; q < 4; ++q)
+                    keep &= a.plane[q][0] * c[0] + a.plane[q][1] * c[1] + a.plane[q][2] * c[2] >= -r;
+                if (keep) {
+                    double c0[3];
+                    to_camera(a, __dmul_rn(__dadd_rn((double)(8 * k.y), 0.5), a.s),
+                              __dmul_rn(__dadd_rn((double)(8 * k.z), 0.5), a.s),
+                              __dmul_rn(__dadd_rn((double)(8 * k.w), 0.5), a.s), c0);
+                    vb.b = b;
+                    double amax = 0.0;
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        vb.hi[e] = (float)c0[e];
+                        vb.lo[e] = (float)(c0[e] - (double)vb.hi[e]);
+                        amax = fmax(amax, fabs(c0[e]));
+                    }
+                    // x = (hi + M l) + lo in float32: two roundings of |x| <= amax + 14 s, plus the
+                    // rounding of M (|M| <= s) times |l| <= 7; 2^-21 leaves a factor >= 4 of margin.
+                    vb.delta = (float)(ldexp(amax + 1.0 + 30.0 * a.s, -21));
+                }
+            }
         }
-        // x = (hi + M l) + lo in float32: two roundings of |x| <= amax + 14 s, plus the
-        // rounding of M (|M| <= s) times |l| <= 7; 2^-21 leaves a factor >= 4 of margin.
-        vb.delta = (float)(ldexp(amax + 1.0 + 30.0 * a.s, -21));
-        const int pos = atomicAdd(m.counters + kNumVisible, 1);
-        reinterpret_cast<VisBlock*>(m.visible)[pos] = vb;
+        // one atomic per warp for the work-list slots
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        int first = 0;
+        if (lane == 0 && ball) first = atomicAdd(m.counters + kNumVisible, __popc(ball));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (keep) reinterpret_cast<VisBlock*>(m.visible)[first + __popc(ball & ((1u << lane) - 1))] = vb;
     }
 }
 
@@ -133,11 +144,11 @@ __device__ bool fuse_voxel_f64(const float* __restrict__ depth, const FuseArgs& 
 }
 
 // floor() of a float32 projection value v with error bound e, certified when
-// floor(v - e) == floor(v + e); returns false when undecided.
-__device__ inline bool certified_floor(float v, float e, float* out) {
-    const float lo = floorf(v - e), hi = floorf(v + e);
+// floor(v - e) == floor(v + e); returns false when undecided.  |v| must be below 2^21.
+__device__ inline bool certified_floor(float v, float e, int* out) {
+    const int lo = floor_small(v - e);
     *out = lo;
-    return lo == hi;
+    return lo == floor_small(v + e);
 }
 
 __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ depth, DeviceMap m, FuseArgs a) {
@@ -147,6 +158,7 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
     const int lx0 = l0 & 7, ly = (l0 >> 3) & 7, lz = l0 >> 6;
     const float eps = 4.76837158e-7f;  // 2^-21
     const VisBlock* __restrict__ vis = reinterpret_cast<const VisBlock*>(m.visible);
+    const float lyf = (float)ly, lzf = (float)lz, lx0f = (float)lx0;
     for (int kb = blockIdx.x; kb < nv; kb += gridDim.x) {
         const VisBlock vb = vis[kb];
         const int b = vb.b;
@@ -158,11 +170,11 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
         bool any = false;
         const float dl = vb.delta;
         // local offsets along y and z are shared by the thread's four voxels
-        const float myz[3] = {fmaf(a.M[1], (float)ly, a.M[2] * (float)lz), fmaf(a.M[4], (float)ly, a.M[5] * (float)lz),
-                              fmaf(a.M[7], (float)ly, a.M[8] * (float)lz)};
+        const float myz[3] = {fmaf(a.M[1], lyf, a.M[2] * lzf), fmaf(a.M[4], lyf, a.M[5] * lzf),
+                              fmaf(a.M[7], lyf, a.M[8] * lzf)};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float lx = (float)(lx0 + q);
+            const float lx = lx0f + (float)q;
             const float mx = fmaf(a.M[0], lx, myz[0]);
             const float my = fmaf(a.M[3], lx, myz[1]);
             const float mz = fmaf(a.M[6], lx, myz[2]);
@@ -182,12 +194,14 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
                 const float g = 2.0f * dl / (z - dl);
                 const float ex = a.fxf * g * (1.0f + fabsf(rx)) + eps * (a.fxf * fabsf(rx) + fabsf(px) + fabsf(a.cxf)) + 1e-6f;
                 const float ey = a.fyf * g * (1.0f + fabsf(ry)) + eps * (a.fyf * fabsf(ry) + fabsf(py) + fabsf(a.cyf)) + 1e-6f;
-                float pxi, pyi;
-                if (certified_floor(px, ex, &pxi) && certified_floor(py, ey, &pyi)) {
-                    if (!(pxi >= 0.0f && pxi < (float)a.W && pyi >= 0.0f && pyi < (float)a.H)) {
-                        decided = 1;
-                    } else {
-                        const float d = __ldg(depth + (size_t)pyi * a.W + (size_t)pxi);
+                int pxi, pyi;
+                if (px + ex < 0.0f || px - ex >= a.Wf || py + ey < 0.0f || py - ey >= a.Hf) {
+                    decided = 1;  // the real projection is certainly outside the image
+                } else if (ex < 1048576.0f && ey < 1048576.0f && certified_floor(px, ex, &pxi) &&
+                           certified_floor(py, ey, &pyi)) {
+                    // certified and within (-e, W + e): the pixel lies in the image
+                    {
+                        const float d = __ldg(depth + pyi * a.W + pxi);
                         if (!(isfinite(d) && d > 0.0f)) {
                             decided = 1;
                         } else {
@@ -251,6 +265,7 @@ int launch_fuse(denser_ctx* c, const float* depth, const denser_intrinsics* K, c
     for (int e = 0; e < 9; ++e) a.M[e] = (float)(a.Ri[e] * a.s);
     a.fxf = (float)a.fx, a.fyf = (float)a.fy, a.cxf = (float)a.cx, a.cyf = (float)a.cy;
     a.muf = (float)a.mu, a.sf = (float)a.s;
+    a.Wf = (float)a.W, a.Hf = (float)a.H;
     cudaMemsetAsync(c->d.counters + kNumVisible, 0, 2 * sizeof(int32_t), s);
     const int npix = a.W * a.H;
     depth_max_kernel<<<grid_for(c->sm_count, (npix + 3) / 4, 256, 2), 256, 0, s>>>(depth, npix, c->d.counters);

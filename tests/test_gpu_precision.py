@@ -1,0 +1,55 @@
+"""Reduced-precision storage of u, u_bar and p (FP16 / BF16, FP32 stencil arithmetic,
+FP64 energies) against the FP64 oracle.
+
+Bars on u after 50 and 200 iterations of the tiny workload (normalised TSDF
+units): 5e-3 for FP16.  BF16 keeps 8 mantissa bits, so one rounding of a value in
+[0.5, 1) already costs up to 2e-3 and the iterate drifts by a few of its spacings
+(3.9e-3): it is held to 2e-2 and does not meet 5e-3.  Allocation, block indices, w and f are unaffected by the storage type
+(they stay FP32 / exact) and are checked bit for bit against the FP32 context.
+The measured errors are printed so that the precision table in the design notes
+can be refreshed from a run (pytest -s).
+"""
+
+import numpy as np
+import pytest
+
+from synth.scenes import tiny_scene
+from tests.pipelines import run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1604_03734_gb300 import native as N  # noqa: E402
+
+BAR = {0: 1e-4, 1: 5e-3, 2: 2e-2}   # by storage precision: FP32, FP16, BF16
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = tiny_scene(seed=0)
+    return s, s.depth_maps()
+
+
+@pytest.mark.parametrize("iters", [50, 200])
+@pytest.mark.parametrize("precision", [N.DENSER_FP16, N.DENSER_BF16])
+def test_reduced_precision_parity(tiny, precision, iters):
+    s, d = tiny
+    g, _, _ = run_oracle(s, d, iters)
+    m, _, st = run_gpu(s, d, iters, precision=precision)
+    snap = m.snapshot(dual=True)
+    m.close()
+    m32, _, st32 = run_gpu(s, d, iters)
+    s32 = m32.snapshot(dual=True)
+    m32.close()
+    for k in ("coords", "w", "f", "omega"):
+        np.testing.assert_array_equal(snap[k], s32[k])
+    err_u = float(np.max(np.abs(snap["u"] - g.u)))
+    err_p = float(np.max(np.abs(snap["p"] - g.p)))
+    mean_u = float(np.mean(np.abs(snap["u"] - g.u)[g.w > 0]))
+    name = {N.DENSER_FP16: "fp16", N.DENSER_BF16: "bf16"}[precision]
+    print(f"\n{name} {iters} iters: max|u-u*| {err_u:.2e} mean {mean_u:.2e} max|p-p*| {err_p:.2e} "
+          f"rel gap {st.rel_gap:.3e} (fp32 {st32.rel_gap:.3e})")
+    assert err_u <= BAR[precision], err_u
+    assert abs(st.primal - st32.primal) <= 1e-2 * abs(st32.primal)
