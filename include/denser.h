@@ -91,7 +91,8 @@ typedef struct {
     double dual;              /* D(p) after the last iteration */
     double gap;               /* primal - dual */
     double rel_gap;           /* gap / |primal| */
-    double sweep_ms;          /* device time of the primal-dual sweeps (CUDA events) */
+    double sweep_ms;          /* device time of the iteration loop (CUDA events): the sweeps, plus the
+                                 gap evaluations when they run inside the graph-captured loop */
     double total_ms;          /* device time of the whole call */
     int32_t sweep_launches;   /* sweep kernel launches timed in sweep_ms */
     int32_t gap_evals;        /* gap evaluations done inside the loop */
@@ -106,12 +107,20 @@ typedef struct {
  *                 2: rows (one thread per 8-voxel x-row, vector loads; the default)
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)
- *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default) */
+ *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default)
+ *   use_graph     1: the iteration loop of denser_regularize runs as one CUDA graph: a
+ *                 WHILE conditional node whose body is gap_every sweeps (10 when no gap
+ *                 test is asked for) plus the FP64 gap evaluation, and whose condition is
+ *                 set on the device (no host round trip per gap test).  The graph is
+ *                 recorded once and reused while the map, schedule and loop shape stay
+ *                 the same.  Needs an even gap_every; otherwise, and for the iterations
+ *                 left over after the last full body pass, sweeps are launched one by one.
+ *                 0: one launch per sweep and a host round trip per gap test. */
 typedef struct {
     int32_t sweep_kernel;
     int32_t order;
     int32_t ctas_per_sm;
-    int32_t reserved;
+    int32_t use_graph;
 } denser_schedule;
 
 /* Fills *p with the defaults above (hash 2^20 slots, 65536 blocks, FP32). */

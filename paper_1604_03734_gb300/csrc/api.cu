@@ -171,11 +171,15 @@ void free_all(denser_ctx* c) {
     void* ptrs[] = {c->d.hash_keys, c->d.hash_vals, c->d.coords, c->d.f, c->d.w, c->d.u, c->d.ub[0], c->d.ub[1],
                     c->d.p[0], c->d.p[1], c->d.omega_bits, c->d.nbr, c->d.counters, c->d.new_keys,
                     c->d.new_slots, c->d.visible, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch,
-                    c->order, c->order_keys, c->order_vals};
+                    c->order, c->order_keys, c->order_vals, c->ctl_i, c->ctl_d};
+    release_graph_loop(c);
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_counters) cudaFreeHost(c->h_counters);
     if (c->h_energy) cudaFreeHost(c->h_energy);
+    if (c->h_ctl_i) cudaFreeHost(c->h_ctl_i);
+    if (c->h_ctl_d) cudaFreeHost(c->h_ctl_d);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
 }
 
 }  // namespace
@@ -225,9 +229,12 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->sched.sweep_kernel = 2;
     c->sched.order = 1;
     c->sched.ctas_per_sm = 0;
-    c->sched.reserved = 0;
+    c->sched.use_graph = 1;
     c->order = nullptr, c->order_keys = nullptr, c->order_vals = nullptr;
     c->order_valid_blocks = -1;
+    c->capture_stream = nullptr;
+    c->ctl_i = nullptr, c->ctl_d = nullptr, c->h_ctl_i = nullptr, c->h_ctl_d = nullptr;
+    c->loop.valid = false;
     c->elem_size = p.precision == DENSER_FP32 ? 4 : 2;
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -259,7 +266,9 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
                 {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2) * 8},
                 {(void**)&c->order, mb * 4},
                 {(void**)&c->order_keys, mb * 8},
-                {(void**)&c->order_vals, mb * 4}};
+                {(void**)&c->order_vals, mb * 4},
+                {(void**)&c->ctl_i, 4 * sizeof(int32_t)},
+                {(void**)&c->ctl_d, 4 * sizeof(double)}};
     for (auto& r : reqs) {
         if (cudaMalloc(r.ptr, r.bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -269,7 +278,10 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
         }
     }
     if (cudaMallocHost((void**)&c->h_counters, kNumCounters * 4) != cudaSuccess ||
-        cudaMallocHost((void**)&c->h_energy, 2 * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost((void**)&c->h_energy, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_ctl_i, 4 * sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_ctl_d, 4 * sizeof(double)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         free_all(c);
         delete c;
@@ -387,7 +399,42 @@ int denser_regularize(denser_ctx* c, int32_t max_iters, double gap_tol, int32_t 
         int launches = 0, gap_evals = 0, converged = 0, it = 0;
         double P = NAN, D = NAN;
         bool have_energy = false;
-        while (it < max_iters) {
+        // graph-captured body passes of k iterations (k even keeps the ping-pong parity)
+        const int k = check_gap ? c->prm.gap_every : 10;
+        if (c->sched.use_graph && nb > 0 && k % 2 == 0 && max_iters >= k) {
+            c->h_ctl_i[0] = 0, c->h_ctl_i[1] = max_iters, c->h_ctl_i[2] = 0, c->h_ctl_i[3] = 0;
+            c->h_ctl_d[0] = gap_tol, c->h_ctl_d[1] = c->h_ctl_d[2] = c->h_ctl_d[3] = 0.0;
+            rc = cuda_check(c, cudaMemcpyAsync(c->ctl_i, c->h_ctl_i, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+                            "loop control");
+            if (!rc)
+                rc = cuda_check(c, cudaMemcpyAsync(c->ctl_d, c->h_ctl_d, 4 * sizeof(double), cudaMemcpyHostToDevice, s),
+                                "loop control");
+            if (!rc) rc = cuda_check(c, cudaEventRecord(a0, s), "event");
+            if (!rc) rc = launch_graph_loop(c, nb, k, check_gap, s);
+            if (!rc) rc = cuda_check(c, cudaEventRecord(a1, s), "event");
+            if (rc) return rc;
+            if (check_gap || out) {
+                rc = cuda_check(c, cudaMemcpyAsync(c->h_ctl_i, c->ctl_i, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                                "loop control");
+                if (!rc)
+                    rc = cuda_check(c, cudaMemcpyAsync(c->h_ctl_d, c->ctl_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, s),
+                                    "loop control");
+                if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+                if (rc) return rc;
+                it = c->h_ctl_i[0];
+                converged = c->h_ctl_i[2];
+                gap_evals = c->h_ctl_i[3];
+                if (gap_evals > 0) P = c->h_ctl_d[1], D = c->h_ctl_d[2], have_energy = true;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a0, a1);
+                sweep_ms += ms;
+            } else {
+                it = (max_iters / k) * k;  // without gap checks the pass count is fixed
+            }
+            launches += it;
+            c->launches += (unsigned long long)(it / k) * (k + (check_gap ? 2 : 0) + 1);
+        }
+        while (it < max_iters && !converged) {
             int batch = max_iters - it;
             if (check_gap) batch = std::min(batch, c->prm.gap_every - (it % c->prm.gap_every));
             cudaEventRecord(a0, s);
@@ -549,10 +596,9 @@ int denser_load_state(denser_ctx* c, const float* u, const float* u_bar, const f
 int denser_set_schedule(denser_ctx* c, const denser_schedule* sch) {
     if (!c || !sch) return DENSER_ERR_INVALID_ARG;
     if (sch->sweep_kernel < 0 || sch->sweep_kernel > 2 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
-        sch->ctas_per_sm > 8)
+        sch->ctas_per_sm > 8 || sch->use_graph < 0 || sch->use_graph > 1)
         return set_error(c, DENSER_ERR_INVALID_ARG, "set_schedule: field out of range");
     c->sched = *sch;
-    c->sched.reserved = 0;
     c->order_valid_blocks = -1;
     return DENSER_OK;
 }

@@ -142,6 +142,20 @@ struct denser_ctx {
     unsigned long long* order_keys;  // [max_blocks] scratch of the order sort
     uint32_t* order_vals;      // [max_blocks]
     int64_t order_valid_blocks;  // blocks covered by `order` (-1: rebuild)
+    // graph-captured iteration loop (schedule.use_graph)
+    cudaStream_t capture_stream;   // private stream used only to record graphs
+    int32_t* ctl_i;                // device [4]: iterations done, max iterations, converged, gap evaluations
+    double* ctl_d;                 // device [4]: gap tolerance, P, D, unused
+    int32_t* h_ctl_i;              // pinned copies
+    double* h_ctl_d;
+    struct LoopGraph {
+        bool valid;
+        int64_t nb;
+        denser_schedule sched;
+        int cur, k, with_gap;
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+    } loop;
     std::string msg;
 };
 
@@ -164,6 +178,8 @@ int launch_sort_pairs(denser_ctx* c, unsigned long long* keys, uint32_t* vals, c
                       cudaStream_t s);
 int launch_block_order(denser_ctx* c, int64_t n_blocks, cudaStream_t s);
 int configure_kernels(denser_ctx* c);
+int launch_graph_loop(denser_ctx* c, int64_t n_blocks, int k, bool with_gap, cudaStream_t s);
+void release_graph_loop(denser_ctx* c);
 
 int set_error(denser_ctx* c, int code, const std::string& m);
 int cuda_check(denser_ctx* c, cudaError_t e, const char* what);

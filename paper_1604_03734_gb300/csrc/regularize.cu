@@ -17,6 +17,7 @@
 //   energy       FP64 primal P(u) and dual D(p) partial sums per CTA (fixed grid, fixed
 //                order: deterministic), then one CTA sums the partials.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -909,6 +910,94 @@ void energy_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Tail of one body pass of the graph-captured loop: counts the k iterations just run,
+// records the energies when they were evaluated, and sets the WHILE condition: run the
+// body again while k more iterations fit and the relative gap is above the tolerance.
+__global__ void loop_decide_kernel(const double* energy, int32_t* ci, double* cd, cudaGraphConditionalHandle h, int k,
+                                   int with_gap) {
+    const int done = ci[0] + k;
+    ci[0] = done;
+    bool more = done + k <= ci[1];
+    if (with_gap) {
+        const double P = energy[0], D = energy[1];
+        cd[1] = P, cd[2] = D;
+        ci[3] += 1;
+        const bool conv = (P - D) <= cd[0] * fabs(P);
+        ci[2] = conv;
+        more = more && !conv;
+    }
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+void release_graph_loop(denser_ctx* c) {
+    if (c->loop.valid) {
+        cudaGraphExecDestroy(c->loop.exec);
+        cudaGraphDestroy(c->loop.graph);
+    }
+    c->loop.valid = false;
+}
+
+// Runs k-iteration body passes (k even, so the ping-pong buffers end where they began)
+// inside one WHILE conditional node until fewer than k iterations remain or the gap
+// test passes.  ctl_i / ctl_d must hold {0, max, 0, 0} / {tol, ...} on the stream.
+int launch_graph_loop(denser_ctx* c, int64_t nb, int k, bool with_gap, cudaStream_t s) {
+    const bool same = c->loop.valid && c->loop.nb == nb && c->loop.cur == c->cur && c->loop.k == k &&
+                      c->loop.with_gap == (int)with_gap && memcmp(&c->loop.sched, &c->sched, sizeof(c->sched)) == 0;
+    if (!same) {
+        release_graph_loop(c);
+        cudaGraph_t g;
+        int rc = cuda_check(c, cudaGraphCreate(&g, 0), "cudaGraphCreate");
+        if (rc) return rc;
+        cudaGraphConditionalHandle h;
+        rc = cuda_check(c, cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault), "conditional handle");
+        // the parameter union has no usable default constructor: zeroed raw storage
+        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+        memset(raw, 0, sizeof(raw));
+        cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+        np->type = cudaGraphNodeTypeConditional;
+        np->conditional.handle = h;
+        np->conditional.type = cudaGraphCondTypeWhile;
+        np->conditional.size = 1;
+        cudaGraphNode_t node;
+        if (!rc) rc = cuda_check(c, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, np), "conditional node");
+        if (rc) {
+            cudaGraphDestroy(g);
+            return rc;
+        }
+        cudaGraph_t body = np->conditional.phGraph_out[0];
+        cudaStream_t cs = c->capture_stream;
+        rc = cuda_check(c, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                        "begin capture");
+        const unsigned long long launches0 = c->launches;
+        for (int i = 0; i < k && !rc; ++i) rc = launch_sweep(c, nb, cs);
+        if (!rc && with_gap) rc = launch_energy(c, nb, cs);
+        if (!rc) {
+            loop_decide_kernel<<<1, 1, 0, cs>>>(c->d.partials + 2 * kEnergyGrid, c->ctl_i, c->ctl_d, h, k, (int)with_gap);
+            rc = cuda_check(c, cudaGetLastError(), "decide kernel");
+        }
+        cudaGraph_t captured;
+        const cudaError_t e = cudaStreamEndCapture(cs, &captured);
+        c->launches = launches0;  // recording launches nothing
+        if (!rc) rc = cuda_check(c, e, "end capture");
+        cudaGraphExec_t exec;
+        if (!rc) rc = cuda_check(c, cudaGraphInstantiate(&exec, g, 0), "graph instantiate");
+        if (rc) {
+            cudaGraphDestroy(g);
+            return rc;
+        }
+        c->loop.valid = true;
+        c->loop.nb = nb;
+        c->loop.sched = c->sched;
+        c->loop.cur = c->cur;
+        c->loop.k = k;
+        c->loop.with_gap = (int)with_gap;
+        c->loop.graph = g;
+        c->loop.exec = exec;
+    }
+    // the launch counter counts kernels run: known only after the loop ends (see caller)
+    return cuda_check(c, cudaGraphLaunch(c->loop.exec, s), "graph launch");
+}
 
 int configure_kernels(denser_ctx* c) {
     cudaError_t e = cudaFuncSetAttribute(sweep_pipe_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -60,7 +60,7 @@ class denser_reg_stats(ctypes.Structure):
 
 class denser_schedule(ctypes.Structure):
     _fields_ = [("sweep_kernel", ctypes.c_int32), ("order", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32)]
 
 
 class DenserError(RuntimeError):
@@ -261,15 +261,16 @@ def denser_launch_count(ctx) -> int:
     return int(lib().denser_launch_count(ctx))
 
 
-def denser_set_schedule(ctx, sweep_kernel=1, order=1, ctas_per_sm=0):
-    sch = denser_schedule(int(sweep_kernel), int(order), int(ctas_per_sm), 0)
+def denser_set_schedule(ctx, sweep_kernel=2, order=1, ctas_per_sm=0, use_graph=1):
+    sch = denser_schedule(int(sweep_kernel), int(order), int(ctas_per_sm), int(use_graph))
     return _check(ctx, lib().denser_set_schedule(ctx, ctypes.byref(sch)))
 
 
 def denser_get_schedule(ctx) -> dict:
     sch = denser_schedule()
     _check(ctx, lib().denser_get_schedule(ctx, ctypes.byref(sch)))
-    return {"sweep_kernel": sch.sweep_kernel, "order": sch.order, "ctas_per_sm": sch.ctas_per_sm}
+    return {"sweep_kernel": sch.sweep_kernel, "order": sch.order, "ctas_per_sm": sch.ctas_per_sm,
+            "use_graph": sch.use_graph}
 
 
 def denser_energy_noalloc(coords, f, w, u, p, n_blocks, lam, out, stream=None) -> int:

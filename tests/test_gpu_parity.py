@@ -287,7 +287,8 @@ def test_error_paths():
         assert N.denser_launch_count(m.ctx) > 0
 
 
-@pytest.mark.parametrize("sched", [(0, 0, 0), (0, 1, 2), (1, 0, 0), (1, 1, 1), (2, 0, 0), (2, 1, 0), (2, 1, 3)])
+@pytest.mark.parametrize("sched", [(0, 0, 0, 0), (0, 1, 2, 1), (1, 0, 0, 0), (1, 1, 1, 1), (2, 0, 0, 1),
+                                   (2, 1, 0, 0), (2, 1, 3, 1)])
 def test_schedules_give_identical_iterates(tiny, sched):
     """Every sweep schedule (kernel variant, visiting order, CTAs per SM) computes the
     same Jacobi iterates bit for bit, and matches the oracle."""
@@ -300,11 +301,11 @@ def test_schedules_give_identical_iterates(tiny, sched):
         for k in range(len(d)):
             N.denser_alloc_blocks(m.ctx, d[k], K, s.poses[k])
             N.denser_fuse_depth(m.ctx, d[k], K, s.poses[k])
-        N.denser_set_schedule(m.ctx, 1, 1, 0)
+        N.denser_set_schedule(m.ctx, 1, 1, 0, 0)
         N.denser_regularize(m.ctx, 40)
         ref = m.snapshot(dual=True)
         N.denser_set_schedule(m.ctx, *sched)
-        assert N.denser_get_schedule(m.ctx) == dict(zip(("sweep_kernel", "order", "ctas_per_sm"), sched))
+        assert N.denser_get_schedule(m.ctx) == dict(zip(("sweep_kernel", "order", "ctas_per_sm", "use_graph"), sched))
         N.denser_regularize(m.ctx, 40)
         out = m.snapshot(dual=True)
     for k in ("u", "u_bar", "p"):
@@ -318,3 +319,5 @@ def test_schedule_rejects_bad_fields():
             N.denser_set_schedule(m.ctx, 3, 0, 0)
         with pytest.raises(N.DenserError):
             N.denser_set_schedule(m.ctx, 1, 0, 9)
+        with pytest.raises(N.DenserError):
+            N.denser_set_schedule(m.ctx, 1, 0, 0, 2)
