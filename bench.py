@@ -32,6 +32,38 @@ BYTES_PER_VOXEL_ITER = {0: 48, 1: 28, 2: 28}  # FP32 / FP16 / BF16 storage of u,
 WORKLOAD = "driving street 100 m: 200 depth maps 1241x376, f=718 px, 0.1 m voxels, 8^3 blocks, mu 0.3 m, 200 PD iters"
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_rows_street100_traffic.json")
+SWEEP_SOURCE = os.path.join(ROOT, "paper_1604_03734_gb300", "csrc", "regularize.cu")
+
+
+def sweep_fingerprint() -> str:
+    """sha256 of the row-sweep kernel's source and of the stencil arithmetic it calls."""
+    import hashlib
+    src = open(SWEEP_SOURCE).read()
+    parts = []
+    for start, end in (("// Arithmetic shared by every sweep variant", "// Dual step at tile position"),
+                       ("// --------------------------------------------------------------- row sweep",
+                        "template <typename T>\nconstexpr size_t sweep_pipe_smem")):
+        i, j = src.find(start), src.find(end)
+        parts.append(src[i:j] if 0 <= i < j else "")
+    return hashlib.sha256("".join(parts).encode()).hexdigest()
+
+
+def measured_traffic(kernel: str, precision: int, nvox: int):
+    """DRAM bytes per launch from the committed ncu capture of the same kernel and workload,
+    or None when the capture is missing, of another workload, or the kernel changed since."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            j = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if kernel != "sweep_rows_kernel" or precision != 0 or j.get("source_fingerprint") != sweep_fingerprint():
+        return None
+    if int(j.get("voxels", -1)) != nvox:
+        return None
+    return float(j["dram_read_bytes"]) + float(j["dram_write_bytes"])
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -277,6 +309,7 @@ def main():
     sweep_avg_ms = sweep_ms / max(sweep_launches, 1)
     bpv = BYTES_PER_VOXEL_ITER[args.precision]
     achieved = bpv * nvox / (sweep_avg_ms / 1e3) / 1e9
+    kernel_name = ["sweep_kernel", "sweep_pipe_kernel", "sweep_rows_kernel"][N.denser_get_schedule(ctx)["sweep_kernel"]]
 
     if rank != 0:
         if world > 1:
@@ -304,7 +337,8 @@ def main():
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),
                    "pd_share_of_step": sweep_ms / args.steps / step_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": ["sweep_kernel", "sweep_pipe_kernel", "sweep_rows_kernel"][N.denser_get_schedule(ctx)["sweep_kernel"]],
+                     "frac": achieved / hbm, "traffic": measured_traffic(kernel_name, args.precision, nvox),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": kernel_name,
                      "peak_kind": peak_kind, "bytes_per_voxel": bpv,
                      "schedule": N.denser_get_schedule(ctx)},
         "e2e": {"value": updates * world / (e2e_ms / 1e3), "unit": "voxel-updates/s",
