@@ -1,0 +1,95 @@
+"""CPU FP64 oracle of the warm-start network -- TEST INFRASTRUCTURE ONLY.
+
+The network maps one fused block with its one-voxel halo (10^3 voxels, channels
+f and a normalised weight) to a starting point for the primal-dual iteration of
+Section III-C on the block's 8^3 voxels (channels u, p_x, p_y, p_z): four 3^3
+convolutions with zero ("same") padding over the 10^3 grid, ReLU after the first
+three, the centre 8^3 of the last one as the output.  The paper has no such
+network; it only fixes what the output is used for (u, p of Section III-C).
+
+Only tests/ and bench.py's reference leg may import this module.  It shares no
+code with the CUDA path.  Layout here: x [n, C, 10, 10, 10] (z, y, x order) and
+W [Cout, Cin, 3, 3, 3] (dz, dy, dx), cross-correlation as in every deep-learning
+framework:  y[co, z, y, x] = b[co] + sum W[co, ci, dz, dy, dx] x[ci, z+dz-1, y+dy-1, x+dx-1].
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+CHANNELS = (2, 16, 16, 16, 4)
+GRID = 10
+
+
+def conv3d_same(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Zero-padded 3^3 cross-correlation, summed tap by tap."""
+    n, ci, D, H, Wd = x.shape
+    xp = np.zeros((n, ci, D + 2, H + 2, Wd + 2))
+    xp[:, :, 1:-1, 1:-1, 1:-1] = x
+    y = np.zeros((n, W.shape[0], D, H, Wd)) + b[None, :, None, None, None]
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                patch = xp[:, :, dz:dz + D, dy:dy + H, dx:dx + Wd]
+                y += np.einsum("oc,nczyx->nozyx", W[:, :, dz, dy, dx], patch)
+    return y
+
+
+def conv3d_same_backward(x, W, dy):
+    """Gradients of conv3d_same with respect to x, W and b, given dL/dy."""
+    n, ci, D, H, Wd = x.shape
+    xp = np.zeros((n, ci, D + 2, H + 2, Wd + 2))
+    xp[:, :, 1:-1, 1:-1, 1:-1] = x
+    dxp = np.zeros_like(xp)
+    dW = np.zeros_like(W)
+    for dz in range(3):
+        for dy_ in range(3):
+            for dx in range(3):
+                patch = xp[:, :, dz:dz + D, dy_:dy_ + H, dx:dx + Wd]
+                dW[:, :, dz, dy_, dx] = np.einsum("nozyx,nczyx->oc", dy, patch)
+                dxp[:, :, dz:dz + D, dy_:dy_ + H, dx:dx + Wd] += np.einsum("oc,nozyx->nczyx", W[:, :, dz, dy_, dx], dy)
+    db = dy.sum(axis=(0, 2, 3, 4))
+    return dxp[:, :, 1:-1, 1:-1, 1:-1], dW, db
+
+
+def init_params(seed: int = 0):
+    """He-style initial weights, zero biases; layer l maps CHANNELS[l] -> CHANNELS[l+1]."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for cin, cout in zip(CHANNELS[:-1], CHANNELS[1:]):
+        W = rng.standard_normal((cout, cin, 3, 3, 3)) * np.sqrt(2.0 / (27 * cin))
+        params.append((W, np.zeros(cout)))
+    return params
+
+
+def forward(params, x):
+    """Returns (output [n, 4, 8, 8, 8], activations for backward)."""
+    acts = [x]
+    h = x
+    for li, (W, b) in enumerate(params):
+        z = conv3d_same(h, W, b)
+        h = np.maximum(z, 0.0) if li < len(params) - 1 else z
+        acts.append(h)
+    return h[:, :, 1:-1, 1:-1, 1:-1], acts
+
+
+def loss(out, target, mask):
+    """Mean over samples of the masked squared error: sum mask (out - target)^2 / n."""
+    d = (out - target) * mask
+    return float(np.sum(d * d) / out.shape[0]), 2.0 * d * mask / out.shape[0]
+
+
+def backward(params, acts, dout):
+    """Gradients [(dW, db)] of the network given dL/d(output) on the centre 8^3."""
+    n = dout.shape[0]
+    dh = np.zeros((n, CHANNELS[-1], GRID, GRID, GRID))
+    dh[:, :, 1:-1, 1:-1, 1:-1] = dout
+    grads = [None] * len(params)
+    for li in range(len(params) - 1, -1, -1):
+        W, b = params[li]
+        if li < len(params) - 1:
+            dh = dh * (acts[li + 1] > 0)        # through the ReLU
+        dx, dW, db = conv3d_same_backward(acts[li], W, dh)
+        grads[li] = (dW, db)
+        dh = dx
+    return grads
