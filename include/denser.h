@@ -213,6 +213,64 @@ int64_t denser_num_blocks(denser_ctx* ctx, void* stream);
 /* Kernels this context has launched since it was created. */
 uint64_t denser_launch_count(const denser_ctx* ctx);
 
+/* ------------------------------------------------------------------ warm start
+ * A small 3D convolutional network gives the primal-dual iteration a starting point
+ * (the paper starts from zero, Section III-C step 1; the network is not part of it).
+ * Inputs are a block and its one-voxel halo, 10^3 voxels; outputs the block's 8^3
+ * (u, p_x, p_y, p_z).  Four 3^3 convolutions with zero padding over the 10^3 grid,
+ * ReLU after the first three.  Tensors, all in device memory:
+ *   activations  BF16 [n][1000][16], voxel x + 10 y + 100 z of the 10^3 grid, channel last
+ *                (the input uses channels 0 = f, 1 = w / (w + 8); the output channels 0..3)
+ *   weights      BF16 [27][16 out][16 in], tap dx + 3 dy + 9 dz for offset (dx-1, dy-1, dz-1)
+ *   biases       FP32 [16]
+ * Products run on tensor cores (BF16 inputs, FP32 accumulation).  `blocks` lists block
+ * indices (device int32 [n]); NULL means blocks 0..n-1. */
+
+/* Network inputs of the listed blocks: x BF16 [n][1000][16]. */
+int denser_net_gather(denser_ctx* ctx, const int32_t* blocks, int64_t n, void* x, void* stream);
+
+/* Training targets from the context's current state: target FP32 [n][4][512] (u, p_x,
+ * p_y, p_z) and mask FP32 [n][4][512] (u: the voxel is in Omega; p_a: the Eq. 3 edge
+ * along axis a exists). */
+int denser_net_targets(denser_ctx* ctx, const int32_t* blocks, int64_t n, float* target, float* mask,
+                       void* stream);
+
+/* Writes a warm start into the state from network outputs out FP32 [n][1000][16]:
+ * u = clamp(out_0, -1, 1) on Omega and 0 elsewhere, u_bar = u, p_a = out_{1+a} on the
+ * Eq. 3 edges and 0 elsewhere, then p projected onto the unit ball.  Follow it with
+ * denser_regularize(start = 1). */
+int denser_net_apply(denser_ctx* ctx, const int32_t* blocks, int64_t n, const float* out, void* stream);
+
+/* One layer: y = conv(x, w) + bias, then ReLU when relu != 0.  x BF16 [n][1000][16];
+ * bias FP32 [16] or NULL; outputs y_bf16 BF16 and/or y_f32 FP32 [n][1000][16] (either
+ * may be NULL).  The data gradient of a layer is the same call on its output gradient
+ * with the mirrored, transposed weights of denser_pack_weights and no bias or ReLU. */
+int denser_conv3(const void* x, const void* w, const float* bias, int32_t relu, void* y_bf16, float* y_f32,
+                 int64_t n, void* stream);
+
+/* Weight and bias gradients of a layer, accumulated (+=) into dw FP32 [27][16][16] and
+ * db FP32 [16]: dw[tap][co][ci] += sum_n sum_v dz[v][co] h[v + offset(tap)][ci], db[co] +=
+ * sum dz[v][co]; h is the layer input and dz the gradient at its pre-activation, BF16. */
+int denser_conv3_wgrad(const void* h, const void* dz, float* dw, float* db, int64_t n, void* stream);
+
+/* dz = dh where h > 0, else 0 (BF16, `count` elements): the gradient through a ReLU. */
+int denser_relu_backward(const void* dh, const void* h, void* dz, int64_t count, void* stream);
+
+/* Masked squared error of outputs out FP32 [n][1000][16] (channels 0..3 on the centre
+ * 8^3) against target/mask FP32 [n][4][512]: *loss += sum mask (out - target)^2 / n
+ * (device FP64), dout BF16 [n][1000][16] = its gradient (zero off the centre). */
+int denser_net_loss(const float* out, const float* target, const float* mask, void* dout, double* loss,
+                    int64_t n, void* stream);
+
+/* Adam update of FP32 parameters w with gradient grad and moments m, v (count elements),
+ * bias-corrected for step `step` (>= 1). */
+int denser_adam(float* w, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                float beta2, float eps, int32_t step, void* stream);
+
+/* BF16 copies of FP32 weights [27][16][16]: wf in the forward layout and wb with taps
+ * mirrored and in/out channels swapped (the data-gradient convolution). */
+int denser_pack_weights(const float* w32, void* wf, void* wb, void* stream);
+
 /* Energies without allocation.  The paper has no counterpart to this call; it exists
  * for callers that may not allocate device memory: a process whose device memory all
  * belongs to its own allocator (a framework's caching allocator, or the fixed memory

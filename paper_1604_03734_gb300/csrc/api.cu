@@ -593,6 +593,56 @@ int denser_load_state(denser_ctx* c, const float* u, const float* u_bar, const f
     });
 }
 
+// ------------------------------------------------------------- warm start
+namespace {
+int net_blocks_check(denser_ctx* c, const int32_t* blocks, int64_t n, int64_t nb) {
+    if (n < 0 || n > nb || (n > 0 && blocks && !is_device_ptr(blocks)))
+        return set_error(c, DENSER_ERR_INVALID_ARG, "net: n out of range or block list not in device memory");
+    return DENSER_OK;
+}
+}  // namespace
+
+int denser_net_gather(denser_ctx* c, const int32_t* blocks, int64_t n, void* x, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        if ((rc = net_blocks_check(c, blocks, n, c->h_counters[kNumBlocks]))) return rc;
+        if (n == 0) return DENSER_OK;
+        if (!x || !is_device_ptr(x)) return set_error(c, DENSER_ERR_INVALID_ARG, "net_gather: x must be device memory");
+        return launch_net_gather(c, blocks, (int)n, x, s);
+    });
+}
+
+int denser_net_targets(denser_ctx* c, const int32_t* blocks, int64_t n, float* target, float* mask, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if ((rc = net_blocks_check(c, blocks, n, nb))) return rc;
+        if (n == 0) return DENSER_OK;
+        if (!target || !mask || !is_device_ptr(target) || !is_device_ptr(mask))
+            return set_error(c, DENSER_ERR_INVALID_ARG, "net_targets: outputs must be device memory");
+        if ((rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s))) return rc;
+        return launch_net_targets(c, blocks, (int)n, target, mask, s);
+    });
+}
+
+int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const float* out, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if ((rc = net_blocks_check(c, blocks, n, nb))) return rc;
+        if (n == 0) return DENSER_OK;
+        if (!out || !is_device_ptr(out)) return set_error(c, DENSER_ERR_INVALID_ARG, "net_apply: out must be device memory");
+        if ((rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s))) return rc;
+        return launch_net_apply(c, blocks, (int)n, out, s);
+    });
+}
+
 int denser_set_schedule(denser_ctx* c, const denser_schedule* sch) {
     if (!c || !sch) return DENSER_ERR_INVALID_ARG;
     if (sch->sweep_kernel < 0 || sch->sweep_kernel > 2 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||

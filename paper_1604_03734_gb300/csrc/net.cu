@@ -1,0 +1,484 @@
+// Warm-start network: a 4-layer 3^3 convolutional network that maps a fused block and
+// its one-voxel halo (10^3 voxels; f and a normalised weight) to a starting point (u,
+// p_x, p_y, p_z) of the primal-dual iteration on the block's 8^3 voxels.  The paper has
+// no such network; these kernels train and run it.
+//
+// Every layer is computed as a 16 -> 16 channel 3^3 convolution with zero padding over
+// the 10^3 grid (the first layer's 2 input channels and the last layer's 4 output
+// channels are zero-padded, and their extra weights stay zero because their gradients
+// are zero).  Activations are BF16, channel-last: act[sample][voxel][16], voxel
+// v = x + 10 y + 100 z.  Weights are BF16 [27 taps][16 out][16 in], tap = dx + 3 dy +
+// 9 dz for the offset (dx - 1, dy - 1, dz - 1).  Products run on the tensor cores as
+// implicit GEMMs with mma.sync m16n8k16 (BF16 in, FP32 accumulate):
+//   forward / data gradient: M = 16 voxels, N = 8 channels, K = 16 channels of one tap;
+//   weight gradient:         M = 16 out channels, N = 8 in channels, K = 16 voxels.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace denser {
+namespace {
+
+constexpr int kC = 16;           // channels of every layer as computed
+constexpr int kG = 10;           // grid side: block + halo
+constexpr int kGV = 1000;        // voxels per sample
+constexpr int kP = 12;           // padded tile side
+constexpr int kTiles = 63;       // 16-voxel row tiles covering 1000 voxels (1008)
+constexpr int kNetThreads = 128;
+constexpr size_t kTileBytes = (size_t)kP * kP * kP * kC * 2;   // 55296
+constexpr size_t kWBytes = (size_t)27 * kC * kC * 2;            // 13824
+constexpr size_t kConvSmem = kTileBytes + kWBytes;
+
+__device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline void ldsm_x4(unsigned addr, unsigned* r) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ inline void ldsm_x4_t(unsigned addr, unsigned* r) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ inline void mma_bf16(float* d, const unsigned* a, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Padded-tile byte offset of grid voxel (x, y, z) shifted by tap offsets (0..2 each).
+__device__ inline int tile_off(int x, int y, int z) { return ((z * kP + y) * kP + x) * (kC * 2); }
+
+// Copies one sample [1000][16] bf16 into the padded tile interior (border stays zero).
+__device__ inline void load_tile(char* tile, const __nv_bfloat16* src) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    for (int i = threadIdx.x; i < kGV * 2; i += blockDim.x) {
+        const int v = i >> 1, half = i & 1;
+        const int x = v % kG, y = (v / kG) % kG, z = v / (kG * kG);
+        *reinterpret_cast<uint4*>(tile + tile_off(x + 1, y + 1, z + 1) + half * 16) = __ldg(s + i);
+    }
+}
+
+// y[v][co] = sum_taps sum_ci W[tap][co][ci] x[v + offset(tap)][ci] (+ bias, ReLU).
+__global__ void __launch_bounds__(kNetThreads) conv3_kernel(const __nv_bfloat16* __restrict__ x,
+                                                             const __nv_bfloat16* __restrict__ w,
+                                                             const float* __restrict__ bias, int relu,
+                                                             __nv_bfloat16* __restrict__ y_bf16,
+                                                             float* __restrict__ y_f32, int n) {
+    extern __shared__ __align__(16) char smem[];
+    char* tile = smem;
+    char* ws = smem + kTileBytes;
+    for (int i = threadIdx.x; i < (int)(kTileBytes / 16); i += blockDim.x)
+        reinterpret_cast<uint4*>(tile)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < (int)(kWBytes / 16); i += blockDim.x)
+        reinterpret_cast<uint4*>(ws)[i] = __ldg(reinterpret_cast<const uint4*>(w) + i);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, c = lane & 3;
+    float bv[2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        for (int e = 0; e < 2; ++e) bv[j][e] = bias ? bias[8 * j + 2 * c + e] : 0.0f;
+    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+        __syncthreads();
+        load_tile(tile, x + (size_t)s * kGV * kC);
+        __syncthreads();
+        for (int t = warp; t < kTiles; t += kNetThreads / 32) {
+            // this lane's A row: voxel of the tile (clamped inside the grid for the padding rows)
+            const int vr = min(t * 16 + (lane & 15), kGV - 1);
+            const int xr = vr % kG, yr = (vr / kG) % kG, zr = vr / (kG * kG);
+            const unsigned arow = smem_u32(tile) + tile_off(xr, yr, zr) + (lane >> 4) * 16;
+            float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+#pragma unroll 1
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+                unsigned a[4];
+                ldsm_x4(arow + tile_off(dx, dy, dz), a);
+                const unsigned* wt = reinterpret_cast<const unsigned*>(ws + tap * kC * kC * 2);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    // B[k = ci][n = co]: W[tap][8 j + g][2 c .. 2 c + 1] and [.. + 8]
+                    const unsigned b0 = wt[((8 * j + g) * kC + 2 * c) >> 1];
+                    const unsigned b1 = wt[((8 * j + g) * kC + 2 * c + 8) >> 1];
+                    mma_bf16(acc[j], a, b0, b1);
+                }
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int v = t * 16 + g + 8 * half;
+                if (v >= kGV) continue;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    float o0 = acc[j][2 * half] + bv[j][0], o1 = acc[j][2 * half + 1] + bv[j][1];
+                    if (relu) o0 = fmaxf(o0, 0.0f), o1 = fmaxf(o1, 0.0f);
+                    const size_t off = ((size_t)s * kGV + v) * kC + 8 * j + 2 * c;
+                    if (y_bf16) *reinterpret_cast<__nv_bfloat162*>(y_bf16 + off) = __floats2bfloat162_rn(o0, o1);
+                    if (y_f32) *reinterpret_cast<float2*>(y_f32 + off) = make_float2(o0, o1);
+                }
+            }
+        }
+    }
+}
+
+// dW[tap][co][ci] += sum_samples sum_v dz[v][co] h[v + offset(tap)][ci] (zero padding);
+// db[co] += sum dz[v][co].  Each warp owns taps warp, warp + 4, ... and accumulates them
+// over all of the CTA's samples before one atomic flush.
+__global__ void __launch_bounds__(kNetThreads) wgrad_kernel(const __nv_bfloat16* __restrict__ h,
+                                                             const __nv_bfloat16* __restrict__ dz, float* dw,
+                                                             float* db, int n) {
+    extern __shared__ __align__(16) char smem[];
+    char* tile = smem;                       // padded h
+    char* dzs = smem + kTileBytes;           // dz rows [1008][16], rows >= 1000 zero
+    __shared__ float dbs[kC];
+    for (int i = threadIdx.x; i < (int)(kTileBytes / 16); i += blockDim.x)
+        reinterpret_cast<uint4*>(tile)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < kTiles * 16 * 2; i += blockDim.x)
+        reinterpret_cast<uint4*>(dzs)[i] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x < kC) dbs[threadIdx.x] = 0.0f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[7][2][4];
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+        for (int j = 0; j < 2; ++j)
+            for (int e = 0; e < 4; ++e) acc[q][j][e] = 0.0f;
+    float bsum = 0.0f;  // thread t < 128 sums channel t % 16 over rows t / 16 + 8 i
+    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+        __syncthreads();
+        load_tile(tile, h + (size_t)s * kGV * kC);
+        const uint4* src = reinterpret_cast<const uint4*>(dz + (size_t)s * kGV * kC);
+        for (int i = threadIdx.x; i < kGV * 2; i += blockDim.x) reinterpret_cast<uint4*>(dzs)[i] = __ldg(src + i);
+        __syncthreads();
+        {
+            const __nv_bfloat16* d = reinterpret_cast<const __nv_bfloat16*>(dzs);
+            for (int v = threadIdx.x >> 4; v < kGV; v += kNetThreads / 16)
+                bsum += __bfloat162float(d[v * kC + (threadIdx.x & 15)]);
+        }
+        for (int ks = 0; ks < kTiles; ++ks) {
+            // A = dz^T (16 co x 16 voxels): rows of dz are voxels; .trans gives the co-major fragment
+            const int mtx = lane >> 3, r = lane & 7;
+            unsigned a[4];
+            {
+                const int v = ks * 16 + r + ((mtx >> 1) & 1) * 8;   // matrices: (v0-7,co0-7) (v0-7,co8-15) (v8-15,co0-7) (v8-15,co8-15)
+                const int co = (mtx & 1) * 8;
+                ldsm_x4_t(smem_u32(dzs) + v * kC * 2 + co * 2, a);
+            }
+            const int vb = min(ks * 16 + r + (mtx & 1) * 8, kGV - 1);   // B rows: voxels, clamped (dz is zero there)
+            const int xb = vb % kG, yb = (vb / kG) % kG, zb = vb / (kG * kG);
+            const unsigned brow = smem_u32(tile) + tile_off(xb, yb, zb) + (mtx >> 1) * 16;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                const int tap = warp + 4 * q;
+                if (tap < 27) {
+                    const int dx = tap % 3, dy = (tap / 3) % 3, dzz = tap / 9;
+                    unsigned b[4];  // (v0-7, ci0-7) (v8-15, ci0-7) (v0-7, ci8-15) (v8-15, ci8-15)
+                    ldsm_x4_t(brow + tile_off(dx, dy, dzz), b);
+                    mma_bf16(acc[q][0], a, b[0], b[1]);
+                    mma_bf16(acc[q][1], a, b[2], b[3]);
+                }
+            }
+        }
+    }
+    // flush: fragment (row co = g (+8), cols ci = 8 j + 2 c (+1))
+    const int g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const int tap = warp + 4 * q;
+        if (tap >= 27) continue;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            for (int e = 0; e < 4; ++e) {
+                const int co = g + 8 * (e >> 1), ci = 8 * j + 2 * c + (e & 1);
+                atomicAdd(dw + (tap * kC + co) * kC + ci, acc[q][j][e]);
+            }
+    }
+    atomicAdd(&dbs[threadIdx.x & 15], bsum);
+    __syncthreads();
+    if (threadIdx.x < kC) atomicAdd(db + threadIdx.x, dbs[threadIdx.x]);
+}
+
+__global__ void relu_backward_kernel(const __nv_bfloat16* __restrict__ dh, const __nv_bfloat16* __restrict__ h,
+                                     __nv_bfloat16* __restrict__ dz, long long count) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+        dz[i] = __bfloat162float(h[i]) > 0.0f ? dh[i] : __float2bfloat16(0.0f);
+}
+
+// Masked squared error on the centre 8^3 of channels 0..3; dout (bf16, zero elsewhere)
+// = 2 (out - target) mask / n; the loss sum goes to *loss (FP64).
+__global__ void loss_kernel(const float* __restrict__ out, const float* __restrict__ target,
+                            const float* __restrict__ mask, __nv_bfloat16* __restrict__ dout, double* loss, int n) {
+    double acc = 0.0;
+    const long long total = (long long)n * kGV;
+    const float inv_n = 1.0f / (float)n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(i / kGV), v = (int)(i % kGV);
+        const int x = v % kG, y = (v / kG) % kG, z = v / (kG * kG);
+        const bool centre = x >= 1 && x <= 8 && y >= 1 && y <= 8 && z >= 1 && z <= 8;
+        float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (centre) {
+            const int l = (x - 1) + 8 * (y - 1) + 64 * (z - 1);
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                const size_t ti = ((size_t)s * 4 + ch) * 512 + l;
+                const float d = (out[i * kC + ch] - target[ti]) * mask[ti];
+                acc += (double)d * d;
+                g[ch] = 2.0f * d * mask[ti] * inv_n;
+            }
+        }
+        __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(dout + i * kC);
+        dst[0] = __floats2bfloat162_rn(g[0], g[1]);
+        dst[1] = __floats2bfloat162_rn(g[2], g[3]);
+#pragma unroll
+        for (int q = 2; q < kC / 2; ++q) dst[q] = __floats2bfloat162_rn(0.0f, 0.0f);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / n);
+}
+
+__global__ void adam_kernel(float* w, const float* grad, float* m, float* v, int count, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const float gr = grad[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gr;
+        const float vi = b2 * v[i] + (1.0f - b2) * gr * gr;
+        m[i] = mi, v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 copies of FP32 weights [27][16 out][16 in]: the forward layout, and the layout of
+// the data-gradient convolution (taps mirrored, in/out swapped).
+__global__ void pack_weights_kernel(const float* w32, __nv_bfloat16* wf, __nv_bfloat16* wb) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 27 * kC * kC; i += gridDim.x * blockDim.x) {
+        const int tap = i / (kC * kC), co = (i / kC) % kC, ci = i % kC;
+        const __nv_bfloat16 v = __float2bfloat16(w32[i]);
+        wf[i] = v;
+        wb[((26 - tap) * kC + ci) * kC + co] = v;
+    }
+}
+
+// ---------------------------------------------------------- map <-> samples
+// Network inputs of listed blocks: f and w / (w + 8) on the 10^3 grid of the block and its
+// one-voxel halo (all 26 neighbours, found through the hash table), zero elsewhere.
+__global__ void gather_kernel(DeviceMap m, const int32_t* __restrict__ blocks, int n, __nv_bfloat16* x) {
+    __shared__ int nb27[27];
+    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+        const int b = blocks ? blocks[s] : s;
+        __syncthreads();
+        if (threadIdx.x < 27) {
+            const int4 k = reinterpret_cast<const int4*>(m.coords)[b];
+            const int dx = threadIdx.x % 3 - 1, dy = (threadIdx.x / 3) % 3 - 1, dz = threadIdx.x / 9 - 1;
+            int idx = -1;
+            if (key_in_range(k.x, (long long)k.y + dx, (long long)k.z + dy, (long long)k.w + dz))
+                idx = hash_lookup(m, pack_key(k.x, k.y + dx, k.z + dy, k.w + dz));
+            nb27[threadIdx.x] = idx;
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v < kGV; v += blockDim.x) {
+            const int gx = v % kG - 1, gy = (v / kG) % kG - 1, gz = v / (kG * kG) - 1;  // -1..8
+            const int ox = gx < 0 ? -1 : (gx > 7 ? 1 : 0), oy = gy < 0 ? -1 : (gy > 7 ? 1 : 0),
+                      oz = gz < 0 ? -1 : (gz > 7 ? 1 : 0);
+            const int nbi = nb27[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
+            float fv = 0.0f, wn = 0.0f;
+            if (nbi >= 0) {
+                const int l = (gx - 8 * ox) + 8 * (gy - 8 * oy) + 64 * (gz - 8 * oz);
+                const float wv = m.w[(size_t)nbi * kBlockVoxels + l];
+                fv = wv > 0.0f ? m.f[(size_t)nbi * kBlockVoxels + l] : 0.0f;
+                wn = wv / (wv + 8.0f);
+            }
+            __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(x + ((size_t)s * kGV + v) * kC);
+            dst[0] = __floats2bfloat162_rn(fv, wn);
+#pragma unroll
+            for (int q = 1; q < kC / 2; ++q) dst[q] = __floats2bfloat162_rn(0.0f, 0.0f);
+        }
+    }
+}
+
+__device__ inline bool omega_of(const DeviceMap& m, int b, int l) {
+    return (m.omega_bits[(size_t)b * 16 + (l >> 5)] >> (l & 31)) & 1u;
+}
+
+// Edge mask of Eq. 3 at voxel l of block b along axis a: l and its +a neighbour in Omega.
+__device__ inline bool edge_of(const DeviceMap& m, int b, int l, int a) {
+    if (!omega_of(m, b, l)) return false;
+    const int lc = a == 0 ? (l & 7) : (a == 1 ? ((l >> 3) & 7) : (l >> 6));
+    const int step = a == 0 ? 1 : (a == 1 ? 8 : 64);
+    if (lc < 7) return omega_of(m, b, l + step);
+    const int nb = m.nbr[(size_t)b * kNeighbours + a];
+    return nb >= 0 && omega_of(m, nb, l - 7 * step);
+}
+
+template <typename T>
+__global__ void targets_kernel(DeviceMap m, const T* u, const T* p, size_t pstride, const int32_t* __restrict__ blocks,
+                               int n, float* target, float* mask) {
+    const long long total = (long long)n * kBlockVoxels;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(i / kBlockVoxels), l = (int)(i % kBlockVoxels);
+        const int b = blocks ? blocks[s] : s;
+        const size_t v = (size_t)b * kBlockVoxels + l;
+        const bool o = omega_of(m, b, l);
+        target[((size_t)s * 4 + 0) * 512 + l] = Store<T>::ld(u + v);
+        mask[((size_t)s * 4 + 0) * 512 + l] = o ? 1.0f : 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            target[((size_t)s * 4 + 1 + a) * 512 + l] = Store<T>::ld(p + a * pstride + v);
+            mask[((size_t)s * 4 + 1 + a) * 512 + l] = edge_of(m, b, l, a) ? 1.0f : 0.0f;
+        }
+    }
+}
+
+// Writes a warm start into the state: u on Omega (clamped to [-1, 1]), u_bar = u, and p
+// on the edges of Eq. 3, projected onto the unit ball; zero elsewhere.
+template <typename T>
+__global__ void apply_kernel(DeviceMap m, T* u, T* ub, T* p, size_t pstride, const int32_t* __restrict__ blocks, int n,
+                             const float* __restrict__ out) {
+    const long long total = (long long)n * kBlockVoxels;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(i / kBlockVoxels), l = (int)(i % kBlockVoxels);
+        const int b = blocks ? blocks[s] : s;
+        const int gx = (l & 7) + 1, gy = ((l >> 3) & 7) + 1, gz = (l >> 6) + 1;
+        const float* o = out + ((size_t)s * kGV + gx + kG * gy + kG * kG * gz) * kC;
+        const bool om = omega_of(m, b, l);
+        const float u0 = om ? fminf(1.0f, fmaxf(-1.0f, o[0])) : 0.0f;
+        float q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[a] = edge_of(m, b, l, a) ? o[1 + a] : 0.0f;
+        const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        const float sc = n2 > 1.0f ? rsqrtf(n2) : 1.0f;
+        const size_t v = (size_t)b * kBlockVoxels + l;
+        Store<T>::st(u + v, u0);
+        Store<T>::st(ub + v, u0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Store<T>::st(p + a * pstride + v, q[a] * sc);
+    }
+}
+
+}  // namespace
+
+int configure_net_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(conv3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kTileBytes + (size_t)kTiles * 16 * kC * 2));
+    return e == cudaSuccess ? DENSER_OK : DENSER_ERR_CUDA;
+}
+
+int launch_net_targets(denser_ctx* c, const int32_t* blocks, int n, float* target, float* mask, cudaStream_t s) {
+    const size_t ps = (size_t)c->d.max_blocks * kBlockVoxels;
+    const int g = grid_for(c->sm_count, (long long)n * kBlockVoxels, 256, 8);
+    switch (c->prm.precision) {
+        case DENSER_FP16:
+            targets_kernel<__half><<<g, 256, 0, s>>>(c->d, (const __half*)c->d.u, (const __half*)c->d.p[c->cur], ps,
+                                                     blocks, n, target, mask);
+            break;
+        case DENSER_BF16:
+            targets_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(c->d, (const __nv_bfloat16*)c->d.u,
+                                                            (const __nv_bfloat16*)c->d.p[c->cur], ps, blocks, n, target,
+                                                            mask);
+            break;
+        default:
+            targets_kernel<float><<<g, 256, 0, s>>>(c->d, (const float*)c->d.u, (const float*)c->d.p[c->cur], ps,
+                                                    blocks, n, target, mask);
+    }
+    c->launches += 1;
+    return cuda_check(c, cudaGetLastError(), "targets kernel");
+}
+
+int launch_net_apply(denser_ctx* c, const int32_t* blocks, int n, const float* out, cudaStream_t s) {
+    const size_t ps = (size_t)c->d.max_blocks * kBlockVoxels;
+    const int g = grid_for(c->sm_count, (long long)n * kBlockVoxels, 256, 8);
+    const int cur = c->cur;
+    switch (c->prm.precision) {
+        case DENSER_FP16:
+            apply_kernel<__half><<<g, 256, 0, s>>>(c->d, (__half*)c->d.u, (__half*)c->d.ub[cur], (__half*)c->d.p[cur], ps,
+                                                   blocks, n, out);
+            break;
+        case DENSER_BF16:
+            apply_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(c->d, (__nv_bfloat16*)c->d.u, (__nv_bfloat16*)c->d.ub[cur],
+                                                          (__nv_bfloat16*)c->d.p[cur], ps, blocks, n, out);
+            break;
+        default:
+            apply_kernel<float><<<g, 256, 0, s>>>(c->d, (float*)c->d.u, (float*)c->d.ub[cur], (float*)c->d.p[cur], ps,
+                                                  blocks, n, out);
+    }
+    c->launches += 1;
+    return cuda_check(c, cudaGetLastError(), "apply kernel");
+}
+
+int launch_net_gather(denser_ctx* c, const int32_t* blocks, int n, void* x, cudaStream_t s) {
+    gather_kernel<<<std::min(n, c->sm_count * 8), 256, 0, s>>>(c->d, blocks, n, (__nv_bfloat16*)x);
+    c->launches += 1;
+    return cuda_check(c, cudaGetLastError(), "gather kernel");
+}
+
+}  // namespace denser
+
+// ------------------------------------------------------------- context-free calls
+using namespace denser;
+
+static int net_grid(int n, int per_sm) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    return std::max(1, std::min(n, sms * per_sm));
+}
+
+static int net_status() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DENSER_OK : DENSER_ERR_CUDA;
+}
+
+extern "C" int denser_conv3(const void* x, const void* w, const float* bias, int32_t relu, void* y_bf16, float* y_f32,
+                            int64_t n, void* stream) {
+    if (!x || !w || n < 0 || (!y_bf16 && !y_f32)) return DENSER_ERR_INVALID_ARG;
+    if (n == 0) return DENSER_OK;
+    if (configure_net_kernels() != DENSER_OK) return DENSER_ERR_CUDA;
+    conv3_kernel<<<net_grid((int)n, 3), kNetThreads, kConvSmem, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)x, (const __nv_bfloat16*)w, bias, relu, (__nv_bfloat16*)y_bf16, y_f32, (int)n);
+    return net_status();
+}
+
+extern "C" int denser_conv3_wgrad(const void* h, const void* dz, float* dw, float* db, int64_t n, void* stream) {
+    if (!h || !dz || !dw || !db || n < 0) return DENSER_ERR_INVALID_ARG;
+    if (n == 0) return DENSER_OK;
+    if (configure_net_kernels() != DENSER_OK) return DENSER_ERR_CUDA;
+    wgrad_kernel<<<net_grid((int)n, 2), kNetThreads, kTileBytes + (size_t)kTiles * 16 * kC * 2, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)h, (const __nv_bfloat16*)dz, dw, db, (int)n);
+    return net_status();
+}
+
+extern "C" int denser_relu_backward(const void* dh, const void* h, void* dz, int64_t count, void* stream) {
+    if (!dh || !h || !dz || count < 0) return DENSER_ERR_INVALID_ARG;
+    if (count == 0) return DENSER_OK;
+    relu_backward_kernel<<<net_grid((int)std::min<int64_t>(count / 256 + 1, 1 << 20), 16), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)dh, (const __nv_bfloat16*)h, (__nv_bfloat16*)dz, count);
+    return net_status();
+}
+
+extern "C" int denser_net_loss(const float* out, const float* target, const float* mask, void* dout, double* loss,
+                               int64_t n, void* stream) {
+    if (!out || !target || !mask || !dout || !loss || n <= 0) return DENSER_ERR_INVALID_ARG;
+    loss_kernel<<<net_grid((int)std::min<int64_t>(n * kGV / 256 + 1, 1 << 20), 8), 256, 0, (cudaStream_t)stream>>>(
+        out, target, mask, (__nv_bfloat16*)dout, loss, (int)n);
+    return net_status();
+}
+
+extern "C" int denser_adam(float* w, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                           float beta2, float eps, int32_t step, void* stream) {
+    if (!w || !grad || !m || !v || count < 0 || step < 1) return DENSER_ERR_INVALID_ARG;
+    const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+    adam_kernel<<<net_grid((int)(count / 256 + 1), 4), 256, 0, (cudaStream_t)stream>>>(w, grad, m, v, (int)count, lr, beta1,
+                                                                                       beta2, eps, c1, c2);
+    return net_status();
+}
+
+extern "C" int denser_pack_weights(const float* w32, void* wf, void* wb, void* stream) {
+    if (!w32 || !wf || !wb) return DENSER_ERR_INVALID_ARG;
+    pack_weights_kernel<<<16, 256, 0, (cudaStream_t)stream>>>(w32, (__nv_bfloat16*)wf, (__nv_bfloat16*)wb);
+    return net_status();
+}

@@ -31,7 +31,9 @@ EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_r
            "denser_last_error", "denser_sync", "denser_alloc_blocks", "denser_fuse_depth",
            "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual",
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
-           "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc")
+           "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc",
+           "denser_net_gather", "denser_net_targets", "denser_net_apply", "denser_conv3", "denser_conv3_wgrad",
+           "denser_relu_backward", "denser_net_loss", "denser_adam", "denser_pack_weights")
 
 
 class denser_params(ctypes.Structure):
@@ -101,6 +103,16 @@ def lib():
             "denser_set_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_get_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_energy_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _dbl, _vp, _vp]),
+            "denser_net_gather": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+            "denser_net_targets": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+            "denser_net_apply": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+            "denser_conv3": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp]),
+            "denser_conv3_wgrad": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
+            "denser_relu_backward": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+            "denser_net_loss": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+            "denser_adam": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, _i32, _vp]),
+            "denser_pack_weights": (_i32, [_vp, _vp, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -279,6 +291,62 @@ def denser_energy_noalloc(coords, f, w, u, p, n_blocks, lam, out, stream=None) -
     return int(lib().denser_energy_noalloc(_ptr(coords, np.int32), _ptr(f, np.float32), _ptr(w, np.float32),
                                            _ptr(u, np.float32), _ptr(p, np.float32), int(n_blocks), float(lam),
                                            _ptr(out, np.float64), _stream(stream)))
+
+
+def _tptr(t):
+    """Address of a contiguous torch tensor of any dtype (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def denser_net_gather(ctx, blocks, n, x, stream=None):
+    return _check(ctx, lib().denser_net_gather(ctx, _tptr(blocks), int(n), _tptr(x), _stream(stream)))
+
+
+def denser_net_targets(ctx, blocks, n, target, mask, stream=None):
+    return _check(ctx, lib().denser_net_targets(ctx, _tptr(blocks), int(n), _tptr(target), _tptr(mask),
+                                                _stream(stream)))
+
+
+def denser_net_apply(ctx, blocks, n, out, stream=None):
+    return _check(ctx, lib().denser_net_apply(ctx, _tptr(blocks), int(n), _tptr(out), _stream(stream)))
+
+
+def _ok(rc, what):
+    if rc != DENSER_OK:
+        raise DenserError(rc, what)
+
+
+def denser_conv3(x, w, bias, relu, y_bf16, y_f32, n, stream=None):
+    _ok(lib().denser_conv3(_tptr(x), _tptr(w), _tptr(bias), int(relu), _tptr(y_bf16), _tptr(y_f32), int(n),
+                           _stream(stream)), "denser_conv3")
+
+
+def denser_conv3_wgrad(h, dz, dw, db, n, stream=None):
+    _ok(lib().denser_conv3_wgrad(_tptr(h), _tptr(dz), _tptr(dw), _tptr(db), int(n), _stream(stream)),
+        "denser_conv3_wgrad")
+
+
+def denser_relu_backward(dh, h, dz, count, stream=None):
+    _ok(lib().denser_relu_backward(_tptr(dh), _tptr(h), _tptr(dz), int(count), _stream(stream)),
+        "denser_relu_backward")
+
+
+def denser_net_loss(out, target, mask, dout, loss, n, stream=None):
+    _ok(lib().denser_net_loss(_tptr(out), _tptr(target), _tptr(mask), _tptr(dout), _tptr(loss), int(n),
+                              _stream(stream)), "denser_net_loss")
+
+
+def denser_adam(w, grad, m, v, count, lr, beta1, beta2, eps, step, stream=None):
+    _ok(lib().denser_adam(_tptr(w), _tptr(grad), _tptr(m), _tptr(v), int(count), float(lr), float(beta1),
+                          float(beta2), float(eps), int(step), _stream(stream)), "denser_adam")
+
+
+def denser_pack_weights(w32, wf, wb, stream=None):
+    _ok(lib().denser_pack_weights(_tptr(w32), _tptr(wf), _tptr(wb), _stream(stream)), "denser_pack_weights")
 
 
 # ------------------------------------------------------------ convenience

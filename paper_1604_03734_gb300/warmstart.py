@@ -1,0 +1,223 @@
+"""Learned warm start for the primal-dual solver: network, training and use.
+
+A 4-layer 3^3 convolutional network (2 -> 16 -> 16 -> 16 -> 4 channels) reads a fused
+block with its one-voxel halo (f and w / (w + 8) on 10^3 voxels) and predicts the
+block's converged (u, p_x, p_y, p_z).  Those predictions, masked to Omega and to the
+edges of Eq. 3 and projected onto |p| <= 1, replace the zero start of Section III-C;
+the plain primal-dual iteration then runs from there, so it stays the judge of the
+result (same fixed point, same gap test).
+
+Every product and update runs in the library's kernels (tensor-core BF16 convolutions
+with FP32 accumulation, Adam in FP32); torch only holds the buffers.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import native as N
+
+C = 16          # channels as computed (inputs and outputs zero-padded to 16)
+GV = 1000       # voxels of the 10^3 grid
+CHANNELS = (2, 16, 16, 16, 4)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class WarmStartNet:
+    """Parameters and training state of the network, on one CUDA device."""
+
+    def __init__(self, seed: int = 0, device=None):
+        torch = _torch()
+        self.device = torch.device(device or "cuda")
+        rng = np.random.default_rng(seed)
+        self.w32, self.b32 = [], []
+        for cin, cout in zip(CHANNELS[:-1], CHANNELS[1:]):
+            w = np.zeros((27, C, C), np.float32)
+            w[:, :cout, :cin] = rng.standard_normal((27, cout, cin)) * math.sqrt(2.0 / (27 * cin))
+            self.w32.append(torch.tensor(w, device=self.device))
+            self.b32.append(torch.zeros(C, device=self.device))
+        self.step = 0
+        self.m = [torch.zeros(27 * C * C + C, device=self.device) for _ in self.w32]
+        self.v = [torch.zeros(27 * C * C + C, device=self.device) for _ in self.w32]
+        self.params = [torch.cat([w.reshape(-1), b]) for w, b in zip(self.w32, self.b32)]
+        self._views()
+        self.pack()
+
+    def _views(self):
+        self.w32 = [p[:27 * C * C].view(27, C, C) for p in self.params]
+        self.b32 = [p[27 * C * C:] for p in self.params]
+
+    def pack(self):
+        torch = _torch()
+        self.wf = [torch.empty(27, C, C, dtype=torch.bfloat16, device=self.device) for _ in self.params]
+        self.wb = [torch.empty(27, C, C, dtype=torch.bfloat16, device=self.device) for _ in self.params]
+        for w, f, b in zip(self.w32, self.wf, self.wb):
+            N.denser_pack_weights(w, f, b)
+
+    # ------------------------------------------------------------ passes
+    def forward(self, x):
+        """x BF16 [n, 1000, 16] -> (out FP32 [n, 1000, 16], activations for backward)."""
+        torch = _torch()
+        n = x.shape[0]
+        acts = [x]
+        h = x
+        out = torch.empty(n, GV, C, device=self.device)
+        for li in range(4):
+            last = li == 3
+            y = None if last else torch.empty(n, GV, C, dtype=torch.bfloat16, device=self.device)
+            N.denser_conv3(h, self.wf[li], self.b32[li], 0 if last else 1, y, out if last else None, n)
+            if not last:
+                acts.append(y)
+                h = y
+        return out, acts
+
+    def backward(self, acts, dout):
+        """Gradients (flat FP32 per layer, same layout as params) given dL/dout (BF16)."""
+        torch = _torch()
+        n = dout.shape[0]
+        grads = [torch.zeros_like(p) for p in self.params]
+        dz = dout
+        for li in range(3, -1, -1):
+            g = grads[li]
+            N.denser_conv3_wgrad(acts[li], dz, g[:27 * C * C], g[27 * C * C:], n)
+            if li > 0:
+                dh = torch.empty(n, GV, C, dtype=torch.bfloat16, device=self.device)
+                N.denser_conv3(dz, self.wb[li], None, 0, dh, None, n)
+                dz = torch.empty_like(dh)
+                N.denser_relu_backward(dh, acts[li], dz, dh.numel())
+        return grads
+
+    def loss_and_grad(self, out, target, mask):
+        torch = _torch()
+        n = out.shape[0]
+        dout = torch.empty(n, GV, C, dtype=torch.bfloat16, device=self.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        N.denser_net_loss(out, target, mask, dout, loss, n)
+        return loss, dout
+
+    def train_step(self, x, target, mask, lr=1e-3):
+        out, acts = self.forward(x)
+        loss, dout = self.loss_and_grad(out, target, mask)
+        grads = self.backward(acts, dout)
+        self.step += 1
+        for p, g, m, v in zip(self.params, grads, self.m, self.v):
+            N.denser_adam(p, g, m, v, p.numel(), lr, 0.9, 0.999, 1e-8, self.step)
+        for w, f, b in zip(self.w32, self.wf, self.wb):
+            N.denser_pack_weights(w, f, b)
+        return loss
+
+    # -------------------------------------------------------- save / load
+    def state_dict(self):
+        return {f"layer{i}": p.detach().cpu().numpy() for i, p in enumerate(self.params)}
+
+    def load_state_dict(self, sd):
+        torch = _torch()
+        for i in range(4):
+            self.params[i].copy_(torch.as_tensor(sd[f"layer{i}"], device=self.device))
+        self._views()
+        self.pack()
+
+    # ----------------------------------------------------------- use
+    def warm_start(self, ctx, chunk: int = 4096, stream=None):
+        """Writes the network's prediction into every block of the map; follow with
+        denser_regularize(..., start=1)."""
+        torch = _torch()
+        nb = N.denser_num_blocks(ctx, stream)
+        for first in range(0, nb, chunk):
+            n = min(chunk, nb - first)
+            blocks = torch.arange(first, first + n, dtype=torch.int32, device=self.device)
+            x = torch.empty(n, GV, C, dtype=torch.bfloat16, device=self.device)
+            N.denser_net_gather(ctx, blocks, n, x, stream)
+            out, _ = self.forward(x)
+            N.denser_net_apply(ctx, blocks, n, out, stream)
+
+
+# ------------------------------------------------------------ training data
+def scene_variant(seed: int, variant: int):
+    """A tiny-workload scene with randomised wall distance, cube position, pose jitter
+    and frame count (drawn from the seed and the variant number)."""
+    from synth.scenes import tiny_scene
+    rng = np.random.default_rng([seed, variant, 3])
+    return tiny_scene(seed=seed * 1000 + variant, n_frames=int(rng.integers(2, 6)),
+                      yaw_jitter=float(rng.uniform(0.0, 0.12)), wall_z=float(rng.uniform(9.0, 16.0)),
+                      cube_at=(float(rng.uniform(-4.0, 3.0)), float(rng.uniform(5.0, 8.5))))
+
+
+def solved_map(scenes, iters: int, gap_tol: float = 0.0, **params):
+    """One map holding every scene as its own segment (at most 127), fused and solved."""
+    m = N.DenserMap(max_blocks=max(4096, 700 * len(scenes)), gap_every=10, **params)
+    for seg, s in enumerate(scenes):
+        cam = s.camera
+        K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+        for k, d in enumerate(s.depth_maps()):
+            N.denser_alloc_blocks(m.ctx, d, K, s.poses[k], seg)
+            N.denser_fuse_depth(m.ctx, d, K, s.poses[k], seg)
+    if iters > 0:
+        N.denser_regularize(m.ctx, iters, gap_tol, 0)
+    return m
+
+
+def make_training_set(seeds, variants_per_seed: int, iters: int = 1500, gap_tol: float = 1e-6, per_map: int = 64):
+    """(x BF16 [n, 1000, 16], target FP32 [n, 4, 512], mask FP32 [n, 4, 512]) from the
+    plain solver on scene variants of the given seeds."""
+    torch = _torch()
+    xs, ts, ms = [], [], []
+    jobs = [(s, v) for s in seeds for v in range(variants_per_seed)]
+    for i in range(0, len(jobs), per_map):
+        scenes = [scene_variant(s, v) for s, v in jobs[i:i + per_map]]
+        m = solved_map(scenes, iters, gap_tol)
+        nb = N.denser_num_blocks(m.ctx)
+        blocks = torch.arange(nb, dtype=torch.int32, device="cuda")
+        x = torch.empty(nb, GV, C, dtype=torch.bfloat16, device="cuda")
+        t = torch.empty(nb, 4, 512, device="cuda")
+        mk = torch.empty(nb, 4, 512, device="cuda")
+        N.denser_net_gather(m.ctx, blocks, nb, x)
+        N.denser_net_targets(m.ctx, blocks, nb, t, mk)
+        xs.append(x), ts.append(t), ms.append(mk)
+        m.close()
+    return torch.cat(xs), torch.cat(ts), torch.cat(ms)
+
+
+def train(net: WarmStartNet, data, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, log=None):
+    torch = _torch()
+    x, t, mk = data
+    n = x.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    history = []
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).to(x.device)
+        tot = torch.zeros(1, dtype=torch.float64, device=x.device)
+        for i in range(0, n - batch + 1, batch):
+            idx = perm[i:i + batch]
+            tot += net.train_step(x[idx].contiguous(), t[idx].contiguous(), mk[idx].contiguous(), lr) * batch
+        history.append(float(tot.item()) / max(1, (n // batch) * batch))
+        if log:
+            log(f"epoch {ep}: loss {history[-1]:.5f}")
+    return history
+
+
+def time_to_gap(scene, net: WarmStartNet | None, gap_tol: float = 1e-4, max_iters: int = 20000):
+    """Device time (ms, CUDA events) and iterations to reach gap_tol from a cold start or
+    from the network's warm start (inference included)."""
+    torch = _torch()
+    m = solved_map([scene], 0)
+    N.denser_regularize(m.ctx, 10, 0.0, 0)  # records the graph loop shape, builds tables
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    if net is not None:
+        net.warm_start(m.ctx)
+        st = N.denser_regularize(m.ctx, max_iters, gap_tol, 1)
+    else:
+        st = N.denser_regularize(m.ctx, max_iters, gap_tol, 0)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m.close()
+    return ms, st.iters, st.rel_gap, st.converged

@@ -1,0 +1,175 @@
+"""Warm-start network kernels against the FP64 oracle (oracle/net_oracle.py).
+
+Per layer, on BF16-representable inputs (so that only the FP32 accumulation differs
+from the oracle): forward convolution, data gradient and weight/bias gradient to a
+relative 1e-5 of the largest entry; the loss to 1e-6.  The whole network (BF16
+activations between layers) against the FP64 network: outputs and every layer's
+gradients within 5e-2 relative (the rounding of activations to 8 mantissa bits).
+Training with the library's Adam lowers the loss.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import net_oracle as NO
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1604_03734_gb300 import native as N  # noqa: E402
+from paper_1604_03734_gb300 import warmstart as WS  # noqa: E402
+
+N.lib()
+
+
+def bf16_round(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def to_ours(x):
+    """[n, C, 10, 10, 10] -> [n, 1000, 16] (channels zero-padded to 16)."""
+    n, c = x.shape[:2]
+    out = np.zeros((n, 1000, 16))
+    out[:, :, :c] = x.transpose(0, 2, 3, 4, 1).reshape(n, 1000, c)
+    return out
+
+
+def from_ours(y, c):
+    n = y.shape[0]
+    return y[:, :, :c].reshape(n, 10, 10, 10, c).transpose(0, 4, 1, 2, 3)
+
+
+def w_ours(W):
+    """[co, ci, 3, 3, 3] -> [27, 16, 16] (tap = dx + 3 dy + 9 dz)."""
+    co, ci = W.shape[:2]
+    out = np.zeros((27, 16, 16))
+    out[:, :co, :ci] = W.transpose(2, 3, 4, 0, 1).reshape(27, co, ci)
+    return out
+
+
+def dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda").to(dtype).contiguous()
+
+
+@pytest.fixture(scope="module")
+def layer_case():
+    rng = np.random.default_rng(0)
+    n = 3
+    x = bf16_round(rng.standard_normal((n, 16, 10, 10, 10)))
+    W = bf16_round(rng.standard_normal((16, 16, 3, 3, 3)) * 0.1)
+    b = rng.standard_normal(16).astype(np.float32).astype(np.float64)
+    return n, x, W, b
+
+
+def test_conv3_forward_layer(layer_case):
+    n, x, W, b = layer_case
+    y = torch.empty(n, 1000, 16, device="cuda")
+    yb = torch.empty(n, 1000, 16, dtype=torch.bfloat16, device="cuda")
+    N.denser_conv3(dev(to_ours(x), torch.bfloat16), dev(w_ours(W), torch.bfloat16), dev(b), 0, yb, y, n)
+    ref = NO.conv3d_same(x, W, b)
+    got = from_ours(y.cpu().numpy().astype(np.float64), 16)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+    # ReLU and the BF16 copy
+    N.denser_conv3(dev(to_ours(x), torch.bfloat16), dev(w_ours(W), torch.bfloat16), dev(b), 1, yb, y, n)
+    got = from_ours(y.cpu().numpy().astype(np.float64), 16)
+    assert np.max(np.abs(got - np.maximum(ref, 0))) <= 1e-5 * np.max(np.abs(ref))
+    np.testing.assert_array_equal(yb.float().cpu().numpy(), y.to(torch.bfloat16).float().cpu().numpy())
+
+
+def test_conv3_gradients_layer(layer_case):
+    n, x, W, b = layer_case
+    rng = np.random.default_rng(1)
+    dz = bf16_round(rng.standard_normal((n, 16, 10, 10, 10)))
+    dx_ref, dW_ref, db_ref = NO.conv3d_same_backward(x, W, dz)
+    w32 = dev(w_ours(W))
+    wf = torch.empty(27, 16, 16, dtype=torch.bfloat16, device="cuda")
+    wb = torch.empty_like(wf)
+    N.denser_pack_weights(w32, wf, wb)
+    np.testing.assert_array_equal(wf.float().cpu().numpy(), w_ours(W).astype(np.float32))
+    dx = torch.empty(n, 1000, 16, device="cuda")
+    N.denser_conv3(dev(to_ours(dz), torch.bfloat16), wb, None, 0, None, dx, n)
+    got = from_ours(dx.cpu().numpy().astype(np.float64), 16)
+    assert np.max(np.abs(got - dx_ref)) <= 1e-5 * np.max(np.abs(dx_ref))
+    dw = torch.zeros(27, 16, 16, device="cuda")
+    db = torch.zeros(16, device="cuda")
+    N.denser_conv3_wgrad(dev(to_ours(x), torch.bfloat16), dev(to_ours(dz), torch.bfloat16), dw, db, n)
+    assert np.max(np.abs(dw.cpu().numpy() - w_ours(dW_ref))) <= 1e-5 * np.max(np.abs(dW_ref))
+    assert np.max(np.abs(db.cpu().numpy() - db_ref)) <= 1e-5 * np.max(np.abs(db_ref))
+    # gradients accumulate
+    N.denser_conv3_wgrad(dev(to_ours(x), torch.bfloat16), dev(to_ours(dz), torch.bfloat16), dw, db, n)
+    assert np.max(np.abs(dw.cpu().numpy() - 2 * w_ours(dW_ref))) <= 2e-5 * np.max(np.abs(dW_ref))
+
+
+def test_relu_backward_and_loss():
+    rng = np.random.default_rng(2)
+    n = 2
+    h = dev(bf16_round(rng.standard_normal((n, 1000, 16))), torch.bfloat16)
+    dh = dev(bf16_round(rng.standard_normal((n, 1000, 16))), torch.bfloat16)
+    dz = torch.empty_like(dh)
+    N.denser_relu_backward(dh, h, dz, dh.numel())
+    np.testing.assert_array_equal(dz.float().cpu().numpy(), np.where(h.float().cpu().numpy() > 0,
+                                                                       dh.float().cpu().numpy(), 0))
+    out = rng.standard_normal((n, 1000, 16)).astype(np.float32)
+    tgt = rng.standard_normal((n, 4, 512)).astype(np.float32)
+    mk = (rng.random((n, 4, 512)) < 0.6).astype(np.float32)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dout = torch.empty(n, 1000, 16, dtype=torch.bfloat16, device="cuda")
+    N.denser_net_loss(dev(out), dev(tgt), dev(mk), dout, loss, n)
+    o = from_ours(out.astype(np.float64), 4)[:, :, 1:-1, 1:-1, 1:-1]
+    t = tgt.astype(np.float64).reshape(n, 4, 8, 8, 8)
+    L, dref = NO.loss(o, t, mk.astype(np.float64).reshape(n, 4, 8, 8, 8))
+    assert abs(loss.item() - L) <= 1e-6 * L
+    full = np.zeros((n, 4, 10, 10, 10))
+    full[:, :, 1:-1, 1:-1, 1:-1] = dref
+    got = from_ours(dout.float().cpu().numpy().astype(np.float64), 4)
+    assert np.max(np.abs(got - full)) <= 1e-2 * np.max(np.abs(full))
+
+
+def test_network_against_fp64_oracle():
+    rng = np.random.default_rng(3)
+    n = 4
+    params = NO.init_params(5)
+    x = np.zeros((n, 2, 10, 10, 10))
+    x[:, 0] = rng.uniform(-1, 1, (n, 10, 10, 10))
+    x[:, 1] = rng.uniform(0, 0.8, (n, 10, 10, 10))
+    x = bf16_round(x)
+    tgt = rng.standard_normal((n, 4, 8, 8, 8)) * 0.5
+    mk = (rng.random((n, 4, 8, 8, 8)) < 0.7).astype(float)
+    out_ref, acts = NO.forward(params, x)
+    _, dout = NO.loss(out_ref, tgt, mk)
+    grads_ref = NO.backward(params, acts, dout)
+
+    net = WS.WarmStartNet(seed=0)
+    sd = {}
+    for i, (W, b) in enumerate(params):
+        sd[f"layer{i}"] = np.concatenate([w_ours(W).astype(np.float32).reshape(-1),
+                                          np.pad(b, (0, 16 - b.size)).astype(np.float32)])
+    net.load_state_dict(sd)
+    out, gacts = net.forward(dev(to_ours(x), torch.bfloat16))
+    got = from_ours(out.cpu().numpy().astype(np.float64), 4)[:, :, 1:-1, 1:-1, 1:-1]
+    assert np.max(np.abs(got - out_ref)) <= 5e-2 * np.max(np.abs(out_ref))
+    t_ours = dev(tgt.reshape(n, 4, 512))
+    m_ours = dev(mk.reshape(n, 4, 512))
+    loss, dout_g = net.loss_and_grad(out, t_ours, m_ours)
+    grads = net.backward(gacts, dout_g)
+    for li in range(4):
+        dW_ref, db_ref = grads_ref[li]
+        g = grads[li].cpu().numpy()
+        dW = g[:27 * 256].reshape(27, 16, 16)
+        rel = np.linalg.norm(dW - w_ours(dW_ref)) / np.linalg.norm(dW_ref)
+        assert rel <= 5e-2, (li, rel)
+        co = db_ref.size
+        assert np.linalg.norm(g[27 * 256:][:co] - db_ref) <= 5e-2 * np.linalg.norm(db_ref) + 1e-9
+        # padded channels carry no gradient, so their weights stay zero
+        assert np.all(dW[:, co:, :] == 0) and np.all(g[27 * 256:][co:] == 0)
+
+
+def test_training_lowers_loss():
+    data = WS.make_training_set(seeds=[100], variants_per_seed=6, iters=400)
+    x, t, m = data
+    assert x.shape[0] > 1500
+    net = WS.WarmStartNet(seed=1)
+    hist = WS.train(net, data, epochs=4, batch=128, lr=2e-3)
+    assert hist[-1] < 0.6 * hist[0], hist
