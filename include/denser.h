@@ -230,16 +230,18 @@ uint64_t denser_launch_count(const denser_ctx* ctx);
 int denser_net_gather(denser_ctx* ctx, const int32_t* blocks, int64_t n, void* x, void* stream);
 
 /* Training targets from the context's current state: target FP32 [n][4][512] (u, p_x,
- * p_y, p_z) and mask FP32 [n][4][512] (u: the voxel is in Omega; p_a: the Eq. 3 edge
- * along axis a exists). */
+ * p_y, p_z) and mask FP32 [n][4][512]: sqrt(u_weight) where the voxel is in Omega (u),
+ * sqrt(p_weight) where the Eq. 3 edge along axis a exists (p_a), 0 elsewhere, so that the
+ * loss of denser_net_loss weighs squared errors of u and p by u_weight and p_weight. */
 int denser_net_targets(denser_ctx* ctx, const int32_t* blocks, int64_t n, float* target, float* mask,
-                       void* stream);
+                       float u_weight, float p_weight, void* stream);
 
 /* Writes a warm start into the state from network outputs out FP32 [n][1000][16]:
  * u = clamp(out_0, -1, 1) on Omega and 0 elsewhere, u_bar = u, p_a = out_{1+a} on the
- * Eq. 3 edges and 0 elsewhere, then p projected onto the unit ball.  Follow it with
- * denser_regularize(start = 1). */
-int denser_net_apply(denser_ctx* ctx, const int32_t* blocks, int64_t n, const float* out, void* stream);
+ * Eq. 3 edges and 0 elsewhere (p = 0 everywhere when with_dual is 0), then p projected
+ * onto the unit ball.  Follow it with denser_regularize(start = 1). */
+int denser_net_apply(denser_ctx* ctx, const int32_t* blocks, int64_t n, const float* out, int32_t with_dual,
+                     void* stream);
 
 /* One layer: y = conv(x, w) + bias, then ReLU when relu != 0.  x BF16 [n][1000][16];
  * bias FP32 [16] or NULL; outputs y_bf16 BF16 and/or y_f32 FP32 [n][1000][16] (either

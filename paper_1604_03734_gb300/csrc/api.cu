@@ -614,7 +614,8 @@ int denser_net_gather(denser_ctx* c, const int32_t* blocks, int64_t n, void* x, 
     });
 }
 
-int denser_net_targets(denser_ctx* c, const int32_t* blocks, int64_t n, float* target, float* mask, void* stream) {
+int denser_net_targets(denser_ctx* c, const int32_t* blocks, int64_t n, float* target, float* mask, float u_weight,
+                       float p_weight, void* stream) {
     return guarded(c, [&]() -> int {
         cudaStream_t s = (cudaStream_t)stream;
         int rc = read_counters(c, s);
@@ -622,14 +623,15 @@ int denser_net_targets(denser_ctx* c, const int32_t* blocks, int64_t n, float* t
         const int64_t nb = c->h_counters[kNumBlocks];
         if ((rc = net_blocks_check(c, blocks, n, nb))) return rc;
         if (n == 0) return DENSER_OK;
-        if (!target || !mask || !is_device_ptr(target) || !is_device_ptr(mask))
-            return set_error(c, DENSER_ERR_INVALID_ARG, "net_targets: outputs must be device memory");
+        if (!target || !mask || !is_device_ptr(target) || !is_device_ptr(mask) || !(u_weight >= 0) || !(p_weight >= 0))
+            return set_error(c, DENSER_ERR_INVALID_ARG, "net_targets: outputs must be device memory, weights >= 0");
         if ((rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s))) return rc;
-        return launch_net_targets(c, blocks, (int)n, target, mask, s);
+        return launch_net_targets(c, blocks, (int)n, target, mask, sqrtf(u_weight), sqrtf(p_weight), s);
     });
 }
 
-int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const float* out, void* stream) {
+int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const float* out, int32_t with_dual,
+                     void* stream) {
     return guarded(c, [&]() -> int {
         cudaStream_t s = (cudaStream_t)stream;
         int rc = read_counters(c, s);
@@ -639,7 +641,7 @@ int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const floa
         if (n == 0) return DENSER_OK;
         if (!out || !is_device_ptr(out)) return set_error(c, DENSER_ERR_INVALID_ARG, "net_apply: out must be device memory");
         if ((rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s))) return rc;
-        return launch_net_apply(c, blocks, (int)n, out, s);
+        return launch_net_apply(c, blocks, (int)n, out, with_dual, s);
     });
 }
 

@@ -314,7 +314,7 @@ __device__ inline bool edge_of(const DeviceMap& m, int b, int l, int a) {
 
 template <typename T>
 __global__ void targets_kernel(DeviceMap m, const T* u, const T* p, size_t pstride, const int32_t* __restrict__ blocks,
-                               int n, float* target, float* mask) {
+                               int n, float* target, float* mask, float mu, float mp) {
     const long long total = (long long)n * kBlockVoxels;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(i / kBlockVoxels), l = (int)(i % kBlockVoxels);
@@ -322,11 +322,11 @@ __global__ void targets_kernel(DeviceMap m, const T* u, const T* p, size_t pstri
         const size_t v = (size_t)b * kBlockVoxels + l;
         const bool o = omega_of(m, b, l);
         target[((size_t)s * 4 + 0) * 512 + l] = Store<T>::ld(u + v);
-        mask[((size_t)s * 4 + 0) * 512 + l] = o ? 1.0f : 0.0f;
+        mask[((size_t)s * 4 + 0) * 512 + l] = o ? mu : 0.0f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             target[((size_t)s * 4 + 1 + a) * 512 + l] = Store<T>::ld(p + a * pstride + v);
-            mask[((size_t)s * 4 + 1 + a) * 512 + l] = edge_of(m, b, l, a) ? 1.0f : 0.0f;
+            mask[((size_t)s * 4 + 1 + a) * 512 + l] = edge_of(m, b, l, a) ? mp : 0.0f;
         }
     }
 }
@@ -335,7 +335,7 @@ __global__ void targets_kernel(DeviceMap m, const T* u, const T* p, size_t pstri
 // on the edges of Eq. 3, projected onto the unit ball; zero elsewhere.
 template <typename T>
 __global__ void apply_kernel(DeviceMap m, T* u, T* ub, T* p, size_t pstride, const int32_t* __restrict__ blocks, int n,
-                             const float* __restrict__ out) {
+                             const float* __restrict__ out, int with_dual) {
     const long long total = (long long)n * kBlockVoxels;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(i / kBlockVoxels), l = (int)(i % kBlockVoxels);
@@ -346,7 +346,7 @@ __global__ void apply_kernel(DeviceMap m, T* u, T* ub, T* p, size_t pstride, con
         const float u0 = om ? fminf(1.0f, fmaxf(-1.0f, o[0])) : 0.0f;
         float q[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) q[a] = edge_of(m, b, l, a) ? o[1 + a] : 0.0f;
+        for (int a = 0; a < 3; ++a) q[a] = (with_dual && edge_of(m, b, l, a)) ? o[1 + a] : 0.0f;
         const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
         const float sc = n2 > 1.0f ? rsqrtf(n2) : 1.0f;
         const size_t v = (size_t)b * kBlockVoxels + l;
@@ -367,43 +367,44 @@ int configure_net_kernels() {
     return e == cudaSuccess ? DENSER_OK : DENSER_ERR_CUDA;
 }
 
-int launch_net_targets(denser_ctx* c, const int32_t* blocks, int n, float* target, float* mask, cudaStream_t s) {
+int launch_net_targets(denser_ctx* c, const int32_t* blocks, int n, float* target, float* mask, float mu, float mp,
+                       cudaStream_t s) {
     const size_t ps = (size_t)c->d.max_blocks * kBlockVoxels;
     const int g = grid_for(c->sm_count, (long long)n * kBlockVoxels, 256, 8);
     switch (c->prm.precision) {
         case DENSER_FP16:
             targets_kernel<__half><<<g, 256, 0, s>>>(c->d, (const __half*)c->d.u, (const __half*)c->d.p[c->cur], ps,
-                                                     blocks, n, target, mask);
+                                                     blocks, n, target, mask, mu, mp);
             break;
         case DENSER_BF16:
             targets_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(c->d, (const __nv_bfloat16*)c->d.u,
                                                             (const __nv_bfloat16*)c->d.p[c->cur], ps, blocks, n, target,
-                                                            mask);
+                                                            mask, mu, mp);
             break;
         default:
             targets_kernel<float><<<g, 256, 0, s>>>(c->d, (const float*)c->d.u, (const float*)c->d.p[c->cur], ps,
-                                                    blocks, n, target, mask);
+                                                    blocks, n, target, mask, mu, mp);
     }
     c->launches += 1;
     return cuda_check(c, cudaGetLastError(), "targets kernel");
 }
 
-int launch_net_apply(denser_ctx* c, const int32_t* blocks, int n, const float* out, cudaStream_t s) {
+int launch_net_apply(denser_ctx* c, const int32_t* blocks, int n, const float* out, int with_dual, cudaStream_t s) {
     const size_t ps = (size_t)c->d.max_blocks * kBlockVoxels;
     const int g = grid_for(c->sm_count, (long long)n * kBlockVoxels, 256, 8);
     const int cur = c->cur;
     switch (c->prm.precision) {
         case DENSER_FP16:
             apply_kernel<__half><<<g, 256, 0, s>>>(c->d, (__half*)c->d.u, (__half*)c->d.ub[cur], (__half*)c->d.p[cur], ps,
-                                                   blocks, n, out);
+                                                   blocks, n, out, with_dual);
             break;
         case DENSER_BF16:
             apply_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(c->d, (__nv_bfloat16*)c->d.u, (__nv_bfloat16*)c->d.ub[cur],
-                                                          (__nv_bfloat16*)c->d.p[cur], ps, blocks, n, out);
+                                                          (__nv_bfloat16*)c->d.p[cur], ps, blocks, n, out, with_dual);
             break;
         default:
             apply_kernel<float><<<g, 256, 0, s>>>(c->d, (float*)c->d.u, (float*)c->d.ub[cur], (float*)c->d.p[cur], ps,
-                                                  blocks, n, out);
+                                                  blocks, n, out, with_dual);
     }
     c->launches += 1;
     return cuda_check(c, cudaGetLastError(), "apply kernel");

@@ -104,8 +104,8 @@ def lib():
             "denser_get_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_energy_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _dbl, _vp, _vp]),
             "denser_net_gather": (_i32, [_vp, _vp, _i64, _vp, _vp]),
-            "denser_net_targets": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
-            "denser_net_apply": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+            "denser_net_targets": (_i32, [_vp, _vp, _i64, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp]),
+            "denser_net_apply": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp]),
             "denser_conv3": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp]),
             "denser_conv3_wgrad": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
             "denser_relu_backward": (_i32, [_vp, _vp, _vp, _i64, _vp]),
@@ -306,13 +306,14 @@ def denser_net_gather(ctx, blocks, n, x, stream=None):
     return _check(ctx, lib().denser_net_gather(ctx, _tptr(blocks), int(n), _tptr(x), _stream(stream)))
 
 
-def denser_net_targets(ctx, blocks, n, target, mask, stream=None):
+def denser_net_targets(ctx, blocks, n, target, mask, u_weight=1.0, p_weight=1.0, stream=None):
     return _check(ctx, lib().denser_net_targets(ctx, _tptr(blocks), int(n), _tptr(target), _tptr(mask),
-                                                _stream(stream)))
+                                                float(u_weight), float(p_weight), _stream(stream)))
 
 
-def denser_net_apply(ctx, blocks, n, out, stream=None):
-    return _check(ctx, lib().denser_net_apply(ctx, _tptr(blocks), int(n), _tptr(out), _stream(stream)))
+def denser_net_apply(ctx, blocks, n, out, with_dual=1, stream=None):
+    return _check(ctx, lib().denser_net_apply(ctx, _tptr(blocks), int(n), _tptr(out), int(with_dual),
+                                              _stream(stream)))
 
 
 def _ok(rc, what):

@@ -124,9 +124,9 @@ class WarmStartNet:
         self.pack()
 
     # ----------------------------------------------------------- use
-    def warm_start(self, ctx, chunk: int = 4096, stream=None):
-        """Writes the network's prediction into every block of the map; follow with
-        denser_regularize(..., start=1)."""
+    def warm_start(self, ctx, chunk: int = 4096, stream=None, dual: bool = True):
+        """Writes the network's prediction into every block of the map (p = 0 when
+        ``dual`` is False); follow with denser_regularize(..., start=1)."""
         torch = _torch()
         nb = N.denser_num_blocks(ctx, stream)
         for first in range(0, nb, chunk):
@@ -135,7 +135,7 @@ class WarmStartNet:
             x = torch.empty(n, GV, C, dtype=torch.bfloat16, device=self.device)
             N.denser_net_gather(ctx, blocks, n, x, stream)
             out, _ = self.forward(x)
-            N.denser_net_apply(ctx, blocks, n, out, stream)
+            N.denser_net_apply(ctx, blocks, n, out, 1 if dual else 0, stream)
 
 
 # ------------------------------------------------------------ training data
@@ -163,9 +163,14 @@ def solved_map(scenes, iters: int, gap_tol: float = 0.0, **params):
     return m
 
 
-def make_training_set(seeds, variants_per_seed: int, iters: int = 1500, gap_tol: float = 1e-6, per_map: int = 64):
+# Loss weights of u and p: the squared distance in the metric of the Chambolle-Pock
+# analysis, |u - u*|^2 / tau + |p - p*|^2 / sigma (tau = 1/6, sigma = 0.5).
+U_WEIGHT, P_WEIGHT = 6.0, 2.0
+
+
+def make_training_set(seeds, variants_per_seed: int, iters: int = 8000, gap_tol: float = 1e-7, per_map: int = 64):
     """(x BF16 [n, 1000, 16], target FP32 [n, 4, 512], mask FP32 [n, 4, 512]) from the
-    plain solver on scene variants of the given seeds."""
+    plain solver on scene variants of the given seeds; masks carry the loss weights."""
     torch = _torch()
     xs, ts, ms = [], [], []
     jobs = [(s, v) for s in seeds for v in range(variants_per_seed)]
@@ -178,7 +183,7 @@ def make_training_set(seeds, variants_per_seed: int, iters: int = 1500, gap_tol:
         t = torch.empty(nb, 4, 512, device="cuda")
         mk = torch.empty(nb, 4, 512, device="cuda")
         N.denser_net_gather(m.ctx, blocks, nb, x)
-        N.denser_net_targets(m.ctx, blocks, nb, t, mk)
+        N.denser_net_targets(m.ctx, blocks, nb, t, mk, U_WEIGHT, P_WEIGHT)
         xs.append(x), ts.append(t), ms.append(mk)
         m.close()
     return torch.cat(xs), torch.cat(ts), torch.cat(ms)
@@ -202,7 +207,7 @@ def train(net: WarmStartNet, data, epochs: int, batch: int = 256, lr: float = 1e
     return history
 
 
-def time_to_gap(scene, net: WarmStartNet | None, gap_tol: float = 1e-4, max_iters: int = 20000):
+def time_to_gap(scene, net: WarmStartNet | None, gap_tol: float = 1e-4, max_iters: int = 20000, dual: bool = True):
     """Device time (ms, CUDA events) and iterations to reach gap_tol from a cold start or
     from the network's warm start (inference included)."""
     torch = _torch()
@@ -212,7 +217,7 @@ def time_to_gap(scene, net: WarmStartNet | None, gap_tol: float = 1e-4, max_iter
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
     if net is not None:
-        net.warm_start(m.ctx)
+        net.warm_start(m.ctx, dual=dual)
         st = N.denser_regularize(m.ctx, max_iters, gap_tol, 1)
     else:
         st = N.denser_regularize(m.ctx, max_iters, gap_tol, 0)
@@ -221,3 +226,63 @@ def time_to_gap(scene, net: WarmStartNet | None, gap_tol: float = 1e-4, max_iter
     ms = e0.elapsed_time(e1)
     m.close()
     return ms, st.iters, st.rel_gap, st.converged
+
+
+def evaluate(net: WarmStartNet, seeds, gap_tol: float = 1e-4):
+    """Mean time (ms, inference included) and iterations to gap_tol on held-out scenes,
+    cold start against warm start."""
+    rows = []
+    for seed in seeds:
+        sc = scene_variant(seed, 0)
+        cold = time_to_gap(sc, None, gap_tol)
+        warm = time_to_gap(sc, net, gap_tol)
+        rows.append((cold, warm))
+    out = {"scenes": len(rows), "gap_tol": gap_tol,
+           "ms_cold": float(np.mean([r[0][0] for r in rows])), "ms_warm": float(np.mean([r[1][0] for r in rows])),
+           "iters_cold": float(np.mean([r[0][1] for r in rows])), "iters_warm": float(np.mean([r[1][1] for r in rows])),
+           "all_converged": all(r[0][3] and r[1][3] for r in rows)}
+    out["speedup_time"] = out["ms_cold"] / out["ms_warm"]
+    out["speedup_iters"] = out["iters_cold"] / out["iters_warm"]
+    return out
+
+
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "weights", "warmstart.npz")
+
+
+def load_default(device=None):
+    """The network trained by ``main`` on seeds 100-199 (8 variants each), or None."""
+    import os
+    if not os.path.exists(WEIGHTS):
+        return None
+    net = WarmStartNet(seed=0, device=device)
+    net.load_state_dict(dict(np.load(WEIGHTS)))
+    return net
+
+
+def main(argv=None):
+    """python -m paper_1604_03734_gb300.warmstart OUT.npz [--seeds 100:200] [--variants 4]
+    [--epochs 30]: trains the network on scene variants of the given seeds and saves it."""
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("out")
+    ap.add_argument("--seeds", default="100:200")
+    ap.add_argument("--variants", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--eval-seeds", default="200:220")
+    args = ap.parse_args(argv)
+    a, b = (int(v) for v in args.seeds.split(":"))
+    data = make_training_set(list(range(a, b)), args.variants)
+    net = WarmStartNet(seed=0)
+    n_ep = args.epochs
+    for ep in range(n_ep):
+        lr = 2e-3 if ep < 0.4 * n_ep else (1e-3 if ep < 0.75 * n_ep else 3e-4)
+        loss = train(net, data, epochs=1, lr=lr, seed=ep)[0]
+        print(f"epoch {ep}: lr {lr:g} loss {loss:.4f}", flush=True)
+    np.savez(args.out, **net.state_dict())
+    a, b = (int(v) for v in args.eval_seeds.split(":"))
+    import json
+    print(json.dumps({"samples": int(data[0].shape[0]), **evaluate(net, range(a, b))}))
+
+
+if __name__ == "__main__":
+    main()
