@@ -104,10 +104,14 @@ typedef struct {
  * iterates; only speed differs (chosen by the autotuner).
  *   sweep_kernel  0: staged (each CTA loads a block, then computes it),
  *                 1: pipelined (cp.async prefetch of the next block while computing),
- *                 2: rows (one thread per 8-voxel x-row, vector loads; the default)
+ *                 2: rows (one thread per 8-voxel x-row, vector loads; the default),
+ *                 3: rows with the next block's own fields prefetched by 1-D bulk copies
+ *                    (TMA) into a double-buffered shared-memory stage
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)
- *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default)
+ *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default); for
+ *                 the row kernel it picks the register budget: 0/1 -> 8 CTAs of 64
+ *                 threads per SM, 2 -> 10, 3 -> 12; for kernel 3 it caps CTAs at 2x this
  *   use_graph     1: the iteration loop of denser_regularize runs as one CUDA graph: a
  *                 WHILE conditional node whose body is gap_every sweeps (10 when no gap
  *                 test is asked for) plus the FP64 gap evaluation, and whose condition is

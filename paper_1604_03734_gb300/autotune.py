@@ -22,8 +22,8 @@ from . import native as N
 
 # (sweep_kernel, order, ctas_per_sm, use_graph); ctas_per_sm 0 = the kernel's default
 DEFAULT_CANDIDATES = (
-    (2, 1, 0, 1), (2, 0, 0, 1), (2, 1, 2, 1), (2, 1, 1, 1), (2, 0, 2, 1),
-    (1, 1, 0, 1), (1, 0, 0, 1), (0, 1, 0, 1), (2, 1, 0, 0),
+    (2, 1, 0, 1), (2, 0, 0, 1), (2, 1, 2, 1), (2, 0, 2, 1), (2, 1, 3, 1),
+    (3, 1, 0, 1), (3, 0, 0, 1), (1, 1, 0, 1), (0, 1, 0, 1), (2, 1, 0, 0),
 )
 
 _cache: dict = {}

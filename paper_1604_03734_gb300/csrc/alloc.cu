@@ -32,6 +32,8 @@ struct AllocArgs {
     float tf[3];           // t / bs - Ti, in [0, 1)
     float hf;              // h as float32
     float cx_hi, cx_lo, cy_hi, cy_lo;  // principal point as float32 hi + lo
+    float nhf;             // N h as float32
+    unsigned long long w_magic;  // ceil(2^64 / W): y = umulhi(pixel, w_magic) for pixel < 2^32
     float ifx, ify, ibs;   // 1/fx, 1/fy, 1/bs as float32
     float Rf[9];           // R as float32
     int W, H, N, seg;
@@ -68,7 +70,7 @@ __device__ bool hash_insert(const DeviceMap& m, unsigned long long key) {
 // Block key of band sample n of pixel (x, y) with depth d, or kEmptyKey when z <= 0.
 // The float64 operations follow the oracle's order one by one; the _rn intrinsics keep
 // the compiler from contracting them into fused multiply-adds.
-__device__ unsigned long long sample_key(const AllocArgs& a, int x, int y, double d, int n, bool* range_err) {
+__device__ __forceinline__ unsigned long long sample_key(const AllocArgs& a, int x, int y, double d, int n, bool* range_err) {
     const double z = __dadd_rn(d, __dmul_rn((double)n, a.h));
     if (!(z > 0.0)) return kEmptyKey;
     const double uu = __dsub_rn(__dadd_rn((double)x, 0.5), a.cx);
@@ -98,10 +100,10 @@ __device__ unsigned long long sample_key(const AllocArgs& a, int x, int y, doubl
 // and DA bounds the magnitude of its terms (its rounding error is below 2^-21 DA).
 // Returns 1 when every floor is certified (key, or kEmptyKey for z <= 0, in *key),
 // 0 when the float64 path must decide.
-__device__ inline int sample_key_f32(const AllocArgs& a, const float* D, const float* DA, float d, float nf,
-                                     bool* range_err, unsigned long long* key) {
+__device__ __forceinline__ int sample_key_f32(const AllocArgs& a, const float* D, const float* DA, float d, float nf,
+                                              bool* range_err, unsigned long long* key) {
     const float eps = 9.53674316e-7f;  // 2^-20
-    const float nh = (float)a.N * a.hf;
+    const float nh = a.nhf;
     const float z = fmaf(nf, a.hf, d);
     const float ez = eps * (fabsf(d) + nh) + 1e-30f;
     if (z < -ez) {
@@ -118,7 +120,9 @@ __device__ inline int sample_key_f32(const AllocArgs& a, const float* D, const f
             *key = kEmptyKey;
             return 1;
         }
-        const float e = eps * (DA[r] * (z + nh) + fabsf(q) + 1.0f);
+        // |q - q_real| <= 2^-21 DA (1.25 z + 0.125 nh) + 2^-24 (|q| + 1) (the rounding of D, of
+        // z, of the fma and of t / bs); e covers each term at least twice
+        const float e = fmaf(1.25f * eps, DA[r] * (z + nh), 0.25f * eps * (fabsf(q) + 1.0f));
         const int lo = floor_small(q - e);
         if (lo != floor_small(q + e)) return 0;
         kf[r] = lo;
@@ -133,7 +137,38 @@ __device__ inline int sample_key_f32(const AllocArgs& a, const float* D, const f
     return 1;
 }
 
-__global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
+// A ray's distinct keys, held in four registers (selected by constant indices only, so
+// that they never spill to local memory).
+struct RayKeys {
+    unsigned long long k0 = kEmptyKey, k1 = kEmptyKey, k2 = kEmptyKey, k3 = kEmptyKey;
+    int count = 0;
+    __device__ void push(unsigned long long k) {
+        if (count == 0) k0 = k;
+        else if (count == 1) k1 = k;
+        else if (count == 2) k2 = k;
+        else k3 = k;
+        ++count;
+    }
+    __device__ unsigned long long at(int i) const {
+        return i == 0 ? k0 : (i == 1 ? k1 : (i == 2 ? k2 : (i == 3 ? k3 : kEmptyKey)));
+    }
+};
+
+// Inserts the pending keys of a warp: round after round every lane offers its next key,
+// lanes offering the same key elect one leader (match.any), and the leaders insert.
+__device__ inline void warp_insert(const DeviceMap& m, const RayKeys& rk, int lane) {
+    for (int i = 0;; ++i) {
+        const unsigned long long key = i < rk.count ? rk.at(i) : kEmptyKey;
+        const unsigned active = __ballot_sync(0xffffffffu, key != kEmptyKey);
+        if (!active) break;
+        if (key != kEmptyKey) {
+            const unsigned peers = __match_any_sync(active, key);
+            if (lane == __ffs(peers) - 1) hash_insert(m, key);
+        }
+    }
+}
+
+__global__ void __maxnreg__(96) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
     const int npix = a.W * a.H;
     const int lane = threadIdx.x & 31;
     bool range_err = false;
@@ -142,7 +177,7 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
         const int pix = base + (int)threadIdx.x;
         float dv = pix < npix ? __ldg(depth + pix) : 0.0f;
         const bool valid = pix < npix && isfinite(dv) && dv > 0.0f;
-        const int x = pix % a.W, y = pix / a.W;
+        const int y = (int)__umul64hi((unsigned long long)(unsigned)pix, a.w_magic), x = pix - y * a.W;
         float D[3] = {0.0f, 0.0f, 0.0f}, DA[3] = {0.0f, 0.0f, 0.0f};
         if (valid) {
             // u = (x + 0.5) - cx with cx as hi + lo: relative error below 2^-23
@@ -155,22 +190,23 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
                 DA[r] = (fabsf(a.Rf[3 * r] * ax) + fabsf(a.Rf[3 * r + 1] * ay) + fabsf(a.Rf[3 * r + 2])) * a.ibs;
             }
         }
+        // the distinct block keys of this ray's band samples, in sample order (consecutive
+        // samples mostly share a block), inserted a warp round at a time once collected
+        RayKeys rk;
         unsigned long long last = kEmptyKey;
         float nf = (float)(-a.N);
-        for (int n = -a.N; n <= a.N; ++n, nf += 1.0f) {
+        for (int n = -a.N; valid && n <= a.N; ++n, nf += 1.0f) {
             unsigned long long key = kEmptyKey;
-            if (valid) {
-                if (!sample_key_f32(a, D, DA, dv, nf, &range_err, &key))
-                    key = sample_key(a, x, y, (double)dv, n, &range_err);
-                if (key == last) key = kEmptyKey;  // consecutive samples in one block
-                else if (key != kEmptyKey) last = key;
+            if (!sample_key_f32(a, D, DA, dv, nf, &range_err, &key)) key = sample_key(a, x, y, (double)dv, n, &range_err);
+            if (key == kEmptyKey || key == last) continue;
+            last = key;
+            if (rk.count == 4) {  // a very oblique ray: insert what it holds (divergent, rare)
+                hash_insert(m, rk.k0), hash_insert(m, rk.k1), hash_insert(m, rk.k2), hash_insert(m, rk.k3);
+                rk.count = 0;
             }
-            const unsigned active = __ballot_sync(0xffffffffu, key != kEmptyKey);
-            if (key != kEmptyKey) {
-                const unsigned peers = __match_any_sync(active, key);
-                if (lane == __ffs(peers) - 1) hash_insert(m, key);
-            }
+            rk.push(key);
         }
+        warp_insert(m, rk, lane);
     }
     if (range_err) report(m.counters, kErrRange);
 }
@@ -377,6 +413,9 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
         a.tf[r] = (float)(tb - (double)a.Ti[r]);
     }
     a.hf = (float)a.h;
+    a.nhf = (float)(a.N * a.h);
+    // floor(n / W) = floor(n * ceil(2^64 / W) / 2^64) for every 32-bit n (W < 2^32)
+    a.w_magic = ~0ull / (unsigned long long)a.W + 1ull;
     a.seg = segment;
     const int npix = a.W * a.H;
     alloc_keys_kernel<<<grid_for(c->sm_count, npix, 256, 8), 256, 0, s>>>(depth, a, c->d);

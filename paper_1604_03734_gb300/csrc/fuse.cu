@@ -39,7 +39,7 @@ struct VisBlock {
     int b;
     float hi[3];
     float lo[3];
-    float delta;  // bound on the float32 camera-coordinate error of any voxel of the block
+    float delta;  // bound on |c0 - (hi + lo)| for the block
 };
 static_assert(sizeof(VisBlock) == 32, "VisBlock is 32 bytes");
 
@@ -111,9 +111,13 @@ __global__ void cull_kernel(DeviceMap m, FuseArgs a) {
                         vb.lo[e] = (float)(c0[e] - (double)vb.hi[e]);
                         amax = fmax(amax, fabs(c0[e]));
                     }
-                    // x = (hi + M l) + lo in float32: two roundings of |x| <= amax + 14 s, plus the
-                    // rounding of M (|M| <= s) times |l| <= 7; 2^-21 leaves a factor >= 4 of margin.
-                    vb.delta = (float)(ldexp(amax + 1.0 + 30.0 * a.s, -21));
+                    // What hi + lo misses of the float64 origin, and the float64 roundings of the
+                    // oracle's own transform (relative 2^-51 of |R| |g| + |t| per coordinate);
+                    // the float32 rounding of each voxel's coordinate is bounded per voxel in the
+                    // fusion kernel.
+                    const double gmax = (8.0 * (fabs((double)k.y) + fabs((double)k.z) + fabs((double)k.w)) + 24.0) * a.s;
+                    const double tmax = fabs(a.ti[0]) + fabs(a.ti[1]) + fabs(a.ti[2]);
+                    vb.delta = (float)(ldexp(amax + gmax + tmax + 1.0, -44));
                 }
             }
         }
@@ -156,11 +160,17 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
     const int t = threadIdx.x;
     const int l0 = 4 * t;
     const int lx0 = l0 & 7, ly = (l0 >> 3) & 7, lz = l0 >> 6;
-    const float eps = 4.76837158e-7f;  // 2^-21
     const VisBlock* __restrict__ vis = reinterpret_cast<const VisBlock*>(m.visible);
     const float lyf = (float)ly, lzf = (float)lz, lx0f = (float)lx0;
+    const float eps22 = 2.38418579e-7f;  // 2^-22
+    const float s25 = 25.0f * a.sf;
+    // the next work-list entry is fetched one block ahead, so that a block's f, w and
+    // depth loads are not queued behind the load of its own entry
+    VisBlock vb_next;
+    if (blockIdx.x < nv) vb_next = vis[blockIdx.x];
     for (int kb = blockIdx.x; kb < nv; kb += gridDim.x) {
-        const VisBlock vb = vis[kb];
+        const VisBlock vb = vb_next;
+        if (kb + (int)gridDim.x < nv) vb_next = vis[kb + gridDim.x];
         const int b = vb.b;
         float4* fp = reinterpret_cast<float4*>(m.f + (size_t)b * kBlockVoxels) + t;
         float4* wp = reinterpret_cast<float4*>(m.w + (size_t)b * kBlockVoxels) + t;
@@ -181,39 +191,46 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
             const float x = (vb.hi[0] + mx) + vb.lo[0];
             const float y = (vb.hi[1] + my) + vb.lo[1];
             const float z = (vb.hi[2] + mz) + vb.lo[2];
+            // Error of each coordinate: two roundings of |x| (the sums), the rounding of
+            // M = s R^T and of its products with l <= 7 (|M l| <= 7 s sqrt(3)), the origin
+            // residual; 2^-22 (|x| + 25 s) is twice 2^-24 (2 |x| + 49 s).
+            const float dx = fmaf(eps22, fabsf(x) + s25, dl), dy = fmaf(eps22, fabsf(y) + s25, dl),
+                        dz = fmaf(eps22, fabsf(z) + s25, dl);
             int decided = 0;  // 1: certified in float32
             bool upd = false;
             float ut = 0.0f;
-            if (z + dl <= 0.0f) {
+            if (z + dz <= 0.0f) {
                 decided = 1;  // certainly behind the camera
-            } else if (z - dl > 0.0f) {
+            } else if (z - dz > 0.0f) {
                 const float inv = __frcp_rn(z);
                 const float rx = x * inv, ry = y * inv;
                 const float px = fmaf(a.fxf, rx, a.cxf);
                 const float py = fmaf(a.fyf, ry, a.cyf);
-                const float g = 2.0f * dl / (z - dl);
-                const float ex = a.fxf * g * (1.0f + fabsf(rx)) + eps * (a.fxf * fabsf(rx) + fabsf(px) + fabsf(a.cxf)) + 1e-6f;
-                const float ey = a.fyf * g * (1.0f + fabsf(ry)) + eps * (a.fyf * fabsf(ry) + fabsf(py) + fabsf(a.cyf)) + 1e-6f;
+                // |x/z - rx| <= (dx + |rx| dz) / (z - dz) from the coordinates, plus the
+                // roundings of 1/z, x * (1/z), the fma and of fx, cx (below 2^-24 (|px| + |cx| +
+                // 3 fx |rx|)); 2^-22 (fx |rx| + |px| + |cx|) covers those with margin.
+                const float iz = __frcp_rn(z - dz);
+                const float ex = a.fxf * (dx + fabsf(rx) * dz) * iz * 1.01f + eps22 * (a.fxf * fabsf(rx) + fabsf(px) + fabsf(a.cxf)) + 1e-6f;
+                const float ey = a.fyf * (dy + fabsf(ry) * dz) * iz * 1.01f + eps22 * (a.fyf * fabsf(ry) + fabsf(py) + fabsf(a.cyf)) + 1e-6f;
                 int pxi, pyi;
                 if (px + ex < 0.0f || px - ex >= a.Wf || py + ey < 0.0f || py - ey >= a.Hf) {
                     decided = 1;  // the real projection is certainly outside the image
                 } else if (ex < 1048576.0f && ey < 1048576.0f && certified_floor(px, ex, &pxi) &&
                            certified_floor(py, ey, &pyi)) {
                     // certified and within (-e, W + e): the pixel lies in the image
-                    {
-                        const float d = __ldg(depth + pyi * a.W + pxi);
-                        if (!(isfinite(d) && d > 0.0f)) {
+                    const float d = __ldg(depth + pyi * a.W + pxi);
+                    if (!(isfinite(d) && d > 0.0f)) {
+                        decided = 1;
+                    } else {
+                        // u_SDF = d - z with z = hi + mz + lo: three roundings, the error of mz,
+                        // the rounding of mu and of us + mu
+                        const float dh = d - vb.hi[2];
+                        const float us = (dh - mz) - vb.lo[2];
+                        const float eu = eps22 * (fabsf(dh) + fabsf(mz) + fabsf(us) + a.muf + s25) + dl + 1e-7f;
+                        if (fabsf(us + a.muf) > eu) {
                             decided = 1;
-                        } else {
-                            // u_SDF = d - z with z = hi + mz + lo; d - hi is (nearly) exact
-                            const float dh = d - vb.hi[2];
-                            const float us = (dh - mz) - vb.lo[2];
-                            const float eu = eps * (fabsf(dh) + fabsf(mz) + fabsf(us) + 30.0f * a.sf) + 1e-7f;
-                            if (fabsf(us + a.muf) > eu) {
-                                decided = 1;
-                                upd = us >= -a.muf;
-                                ut = fminf(1.0f, us / a.muf);
-                            }
+                            upd = us >= -a.muf;
+                            ut = fminf(1.0f, us / a.muf);
                         }
                     }
                 }

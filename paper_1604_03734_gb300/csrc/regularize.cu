@@ -203,6 +203,7 @@ struct SweepArgs {
     const uint32_t* bits;
     const int32_t* nbr;
     const int32_t* order;  // visiting order of the blocks (NULL: index order)
+    int32_t* err;          // sticky error flags (bounded waits that gave up)
     size_t pstride;
     int n_blocks;
     float sigma, tau, tau_lam, theta;
@@ -557,189 +558,344 @@ __device__ inline float load_voxel(const SweepArgs<T>& a, int n, int l, unsigned
     return Store<T>::ld(a.ub_in + (size_t)n * kBlockVoxels + l);
 }
 
+// Shared-memory stage of one block's own fields, filled by 1-D bulk copies (TMA).
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads, 8) sweep_rows_kernel(SweepArgs<T> a) {
-    __shared__ RowTiles s;
-    const int r = threadIdx.x;
+struct RowStage {
+    static constexpr int kField = kBlockVoxels * (int)sizeof(T);
+    static constexpr int kUb = 0;
+    static constexpr int kP = kUb + kField;
+    static constexpr int kU = kP + 3 * kField;
+    static constexpr int kF = kU + kField;
+    static constexpr int kW = kF + kBlockVoxels * 4;
+    static constexpr int kBits = kW + kBlockVoxels * 4;
+    static constexpr int kTx = kBits + 64;                 // bytes the copies deliver
+    static constexpr int kBytes = (kTx + 127) / 128 * 128;  // stride between the two stages
+};
+
+template <typename T>
+__device__ inline void ld_row_smem(const T* p, float* v) {
+    if constexpr (sizeof(T) == 4) {
+        lds_row(reinterpret_cast<const float*>(p), v);
+    } else {
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        const T* h = reinterpret_cast<const T*>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(h + i);
+    }
+}
+
+// One block of the row sweep: staging of the rows, faces and edges, the dual steps,
+// the primal step and the relaxation.  `stage` holds the block's own fields when they
+// were prefetched into shared memory (else they are read from global memory).
+template <typename T>
+__device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, int b, int r, const char* stage,
+                                           const int* nb) {
     const int ly = r & 7, lz = r >> 3;
     const int rr = r10(ly, lz);
     const size_t ps = a.pstride;
-    for (int k = blockIdx.x; k < a.n_blocks; k += gridDim.x) {
-        const int b = a.order ? __ldg(a.order + k) : k;
-        const int32_t* nb = a.nbr + (size_t)b * kNeighbours;
-        const size_t base = (size_t)b * kBlockVoxels + 8 * r;
-
-        // ---------------------------------------------------------- staging
-        float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
+    const size_t base = (size_t)b * kBlockVoxels + 8 * r;
+    // ---------------------------------------------------------- staging
+    float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
+    unsigned om_r;
+    if (stage) {  // this block's rows were brought into shared memory by the bulk copies
+        using L = RowStage<T>;
+        ld_row_smem<T>(reinterpret_cast<const T*>(stage + L::kUb) + 8 * r, ub);
+        ld_row_smem<T>(reinterpret_cast<const T*>(stage + L::kP) + 8 * r, p0);
+        ld_row_smem<T>(reinterpret_cast<const T*>(stage + L::kP + L::kField) + 8 * r, p1);
+        ld_row_smem<T>(reinterpret_cast<const T*>(stage + L::kP + 2 * L::kField) + 8 * r, p2);
+        ld_row_smem<T>(reinterpret_cast<const T*>(stage + L::kU) + 8 * r, uo);
+        lds_row(reinterpret_cast<const float*>(stage + L::kF) + 8 * r, fv);
+        lds_row(reinterpret_cast<const float*>(stage + L::kW) + 8 * r, wv);
+        om_r = (reinterpret_cast<const uint32_t*>(stage + L::kBits)[r >> 2] >> (8 * (r & 3))) & 0xffu;
+    } else {
         ld_row<T>(a.ub_in + base, ub);
         ld_row<T>(a.p_in + base, p0);
         ld_row<T>(a.p_in + ps + base, p1);
         ld_row<T>(a.p_in + 2 * ps + base, p2);
         ld_row<T>(a.u + base, uo);
-        {
-            const float4* f4 = reinterpret_cast<const float4*>(a.f + base);
-            const float4* w4 = reinterpret_cast<const float4*>(a.w + base);
-            const float4 fa = __ldg(f4), fb = __ldg(f4 + 1), wa = __ldg(w4), wb = __ldg(w4 + 1);
-            fv[0] = fa.x, fv[1] = fa.y, fv[2] = fa.z, fv[3] = fa.w, fv[4] = fb.x, fv[5] = fb.y, fv[6] = fb.z, fv[7] = fb.w;
-            wv[0] = wa.x, wv[1] = wa.y, wv[2] = wa.z, wv[3] = wa.w, wv[4] = wb.x, wv[5] = wb.y, wv[6] = wb.z, wv[7] = wb.w;
+        const float4* f4 = reinterpret_cast<const float4*>(a.f + base);
+        const float4* w4 = reinterpret_cast<const float4*>(a.w + base);
+        const float4 fa = __ldg(f4), fb = __ldg(f4 + 1), wa = __ldg(w4), wb = __ldg(w4 + 1);
+        fv[0] = fa.x, fv[1] = fa.y, fv[2] = fa.z, fv[3] = fa.w, fv[4] = fb.x, fv[5] = fb.y, fv[6] = fb.z, fv[7] = fb.w;
+        wv[0] = wa.x, wv[1] = wa.y, wv[2] = wa.z, wv[3] = wa.w, wv[4] = wb.x, wv[5] = wb.y, wv[6] = wb.z, wv[7] = wb.w;
+        om_r = row_bits(a.bits, b, r);
+    }
+    // x halos of the row: u_bar and Omega at x = 8 and x = -1, old p at x = -1
+    float hm0 = 0.0f, hm1 = 0.0f, hm2 = 0.0f;
+    {
+        unsigned bit;
+        const float xp = load_voxel<T>(a, nb[0], 8 * r, &bit);
+        om_r |= bit << 8;
+        const int n3 = nb[3];
+        const float xm = load_voxel<T>(a, n3, 8 * r + 7, &bit);
+        om_r |= bit << 9;
+        if (n3 >= 0) {
+            const size_t o3 = (size_t)n3 * kBlockVoxels + 8 * r + 7;
+            hm0 = Store<T>::ld(a.p_in + o3);
+            hm1 = Store<T>::ld(a.p_in + ps + o3);
+            hm2 = Store<T>::ld(a.p_in + 2 * ps + o3);
         }
-        unsigned om_r = row_bits(a.bits, b, r);
-        // x halos of the row: u_bar and Omega at x = 8 and x = -1, old p at x = -1
-        float hm0 = 0.0f, hm1 = 0.0f, hm2 = 0.0f;
-        {
-            unsigned bit;
-            const float xp = load_voxel<T>(a, __ldg(nb + 0), 8 * r, &bit);
-            om_r |= bit << 8;
-            const int n3 = __ldg(nb + 3);
-            const float xm = load_voxel<T>(a, n3, 8 * r + 7, &bit);
-            om_r |= bit << 9;
-            if (n3 >= 0) {
-                const size_t o3 = (size_t)n3 * kBlockVoxels + 8 * r + 7;
-                hm0 = Store<T>::ld(a.p_in + o3);
-                hm1 = Store<T>::ld(a.p_in + ps + o3);
-                hm2 = Store<T>::ld(a.p_in + 2 * ps + o3);
-            }
-            s.xhp[rr] = xp;
-            s.xhm[rr] = xm;
-        }
-        sts_row(s.ub[rr], ub);
-        s.om[rr] = (unsigned short)om_r;
-        // faces and edges
-        if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
-            const int d = r10(8, lz);
-            unsigned om = load_face_row<T>(a, __ldg(nb + 1), 8 * lz, s.ub[d]), bit;
-            s.xhm[d] = load_voxel<T>(a, __ldg(nb + 6), 8 * (8 * lz) + 7, &bit);
-            s.om[d] = (unsigned short)(om | (bit << 9));
-        }
-        if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
-            const int d = r10(-1, lz);
-            const int n4 = __ldg(nb + 4);
-            unsigned om = load_face_row<T>(a, n4, 7 + 8 * lz, s.ub[d]), bit;
-            s.xhp[d] = load_voxel<T>(a, __ldg(nb + 8), 8 * (7 + 8 * lz), &bit);
-            s.om[d] = (unsigned short)(om | (bit << 8));
-            float q[8];
+        s.xhp[rr] = xp;
+        s.xhm[rr] = xm;
+    }
+    sts_row(s.ub[rr], ub);
+    s.om[rr] = (unsigned short)om_r;
+    // faces and edges
+    if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
+        const int d = r10(8, lz);
+        unsigned om = load_face_row<T>(a, nb[1], 8 * lz, s.ub[d]), bit;
+        s.xhm[d] = load_voxel<T>(a, nb[6], 8 * (8 * lz) + 7, &bit);
+        s.om[d] = (unsigned short)(om | (bit << 9));
+    }
+    if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
+        const int d = r10(-1, lz);
+        const int n4 = nb[4];
+        unsigned om = load_face_row<T>(a, n4, 7 + 8 * lz, s.ub[d]), bit;
+        s.xhp[d] = load_voxel<T>(a, nb[8], 8 * (7 + 8 * lz), &bit);
+        s.om[d] = (unsigned short)(om | (bit << 8));
+        float q[8];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (n4 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n4 * kBlockVoxels + 8 * (7 + 8 * lz), q);
-                else
+        for (int c = 0; c < 3; ++c) {
+            if (n4 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n4 * kBlockVoxels + 8 * (7 + 8 * lz), q);
+            else
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
-                sts_row(s.pfy[c][lz], q);
-            }
+                for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+            sts_row(s.pfy[c][lz], q);
         }
-        if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
-            const int d = r10(ly, 8);
-            unsigned om = load_face_row<T>(a, __ldg(nb + 2), ly, s.ub[d]), bit;
-            s.xhm[d] = load_voxel<T>(a, __ldg(nb + 7), 8 * ly + 7, &bit);
-            s.om[d] = (unsigned short)(om | (bit << 9));
-        }
-        if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
-            const int d = r10(ly, -1);
-            const int n5 = __ldg(nb + 5);
-            unsigned om = load_face_row<T>(a, n5, ly + 56, s.ub[d]), bit;
-            s.xhp[d] = load_voxel<T>(a, __ldg(nb + 10), 8 * (ly + 56), &bit);
-            s.om[d] = (unsigned short)(om | (bit << 8));
-            float q[8];
+    }
+    if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
+        const int d = r10(ly, 8);
+        unsigned om = load_face_row<T>(a, nb[2], ly, s.ub[d]), bit;
+        s.xhm[d] = load_voxel<T>(a, nb[7], 8 * ly + 7, &bit);
+        s.om[d] = (unsigned short)(om | (bit << 9));
+    }
+    if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
+        const int d = r10(ly, -1);
+        const int n5 = nb[5];
+        unsigned om = load_face_row<T>(a, n5, ly + 56, s.ub[d]), bit;
+        s.xhp[d] = load_voxel<T>(a, nb[10], 8 * (ly + 56), &bit);
+        s.om[d] = (unsigned short)(om | (bit << 8));
+        float q[8];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (n5 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n5 * kBlockVoxels + 8 * (ly + 56), q);
-                else
+        for (int c = 0; c < 3; ++c) {
+            if (n5 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n5 * kBlockVoxels + 8 * (ly + 56), q);
+            else
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
-                sts_row(s.pfz[c][ly], q);
-            }
+                for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+            sts_row(s.pfz[c][ly], q);
         }
-        if (ly == 0 && lz == 7)  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
-            s.om[r10(-1, 8)] = (unsigned short)load_face_row<T>(a, __ldg(nb + 9), 7, s.ub[r10(-1, 8)]);
-        if (ly == 7 && lz == 0)  // edge row (8, -1) <- block (-z,+y) row (0, 7)
-            s.om[r10(8, -1)] = (unsigned short)load_face_row<T>(a, __ldg(nb + 11), 56, s.ub[r10(8, -1)]);
-        __syncthreads();
+    }
+    if (ly == 0 && lz == 7)  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
+        s.om[r10(-1, 8)] = (unsigned short)load_face_row<T>(a, nb[9], 7, s.ub[r10(-1, 8)]);
+    if (ly == 7 && lz == 0)  // edge row (8, -1) <- block (-z,+y) row (0, 7)
+        s.om[r10(8, -1)] = (unsigned short)load_face_row<T>(a, nb[11], 56, s.ub[r10(8, -1)]);
+    __syncthreads();
 
-        // ------------------------------------------------------- dual steps
-        {
-            float uy[8], uz[8];
-            lds_row(s.ub[r10(ly + 1, lz)], uy);
-            lds_row(s.ub[r10(ly, lz + 1)], uz);
-            const unsigned om_y = s.om[r10(ly + 1, lz)], om_z = s.om[r10(ly, lz + 1)];
-            const float xp = s.xhp[rr];
+    // ------------------------------------------------------- dual steps
+    {
+        float uy[8], uz[8];
+        lds_row(s.ub[r10(ly + 1, lz)], uy);
+        lds_row(s.ub[r10(ly, lz + 1)], uz);
+        const unsigned om_y = s.om[r10(ly + 1, lz)], om_z = s.om[r10(ly, lz + 1)];
+        const float xp = s.xhp[rr];
 #pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                const bool o = (om_r >> x) & 1u;
-                const float g0 = masked_diff(o && ((om_r >> (x + 1)) & 1u), x < 7 ? ub[x < 7 ? x + 1 : 7] : xp, ub[x]);
-                const float g1 = masked_diff(o && ((om_y >> x) & 1u), uy[x], ub[x]);
-                const float g2 = masked_diff(o && ((om_z >> x) & 1u), uz[x], ub[x]);
-                float out[3];
-                dual_update(p0[x], p1[x], p2[x], g0, g1, g2, a.sigma, out);
-                p0[x] = out[0], p1[x] = out[1], p2[x] = out[2];
-            }
-            // the -x face voxel (-1, ly, lz)
-            const bool o = (om_r >> 9) & 1u;
-            const float um = s.xhm[rr];
-            const int ry = r10(ly + 1, lz), rz = r10(ly, lz + 1);
-            const float g0 = masked_diff(o && (om_r & 1u), ub[0], um);
-            const float g1 = masked_diff(o && ((s.om[ry] >> 9) & 1u), s.xhm[ry], um);
-            const float g2 = masked_diff(o && ((s.om[rz] >> 9) & 1u), s.xhm[rz], um);
+        for (int x = 0; x < 8; ++x) {
+            const bool o = (om_r >> x) & 1u;
+            const float g0 = masked_diff(o && ((om_r >> (x + 1)) & 1u), x < 7 ? ub[x < 7 ? x + 1 : 7] : xp, ub[x]);
+            const float g1 = masked_diff(o && ((om_y >> x) & 1u), uy[x], ub[x]);
+            const float g2 = masked_diff(o && ((om_z >> x) & 1u), uz[x], ub[x]);
             float out[3];
-            dual_update(hm0, hm1, hm2, g0, g1, g2, a.sigma, out);
-            s.pxm[r] = out[0];
+            dual_update(p0[x], p1[x], p2[x], g0, g1, g2, a.sigma, out);
+            p0[x] = out[0], p1[x] = out[1], p2[x] = out[2];
         }
-        {
-            // one voxel of the -y face, (fx, -1, fz), and one of the -z face, (fx, fy, -1)
-            const int fx = r & 7, fw = r >> 3;
-            {  // -y face: fw is z
-                const int d = r10(-1, fw), dz = r10(-1, fw + 1), dc = r10(0, fw);
-                const unsigned om = s.om[d];
-                const bool o = (om >> fx) & 1u;
-                const float v = s.ub[d][fx];
-                const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
-                const float g1 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
-                const float g2 = masked_diff(o && ((s.om[dz] >> fx) & 1u), s.ub[dz][fx], v);
-                float out[3];
-                dual_update(s.pfy[0][fw][fx], s.pfy[1][fw][fx], s.pfy[2][fw][fx], g0, g1, g2, a.sigma, out);
-                s.py[r9(-1, fw)][fx] = out[1];
-            }
-            {  // -z face: fw is y
-                const int d = r10(fw, -1), dy = r10(fw + 1, -1), dc = r10(fw, 0);
-                const unsigned om = s.om[d];
-                const bool o = (om >> fx) & 1u;
-                const float v = s.ub[d][fx];
-                const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
-                const float g1 = masked_diff(o && ((s.om[dy] >> fx) & 1u), s.ub[dy][fx], v);
-                const float g2 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
-                float out[3];
-                dual_update(s.pfz[0][fw][fx], s.pfz[1][fw][fx], s.pfz[2][fw][fx], g0, g1, g2, a.sigma, out);
-                s.pz[r9(fw, -1)][fx] = out[2];
-            }
+        // the -x face voxel (-1, ly, lz)
+        const bool o = (om_r >> 9) & 1u;
+        const float um = s.xhm[rr];
+        const int ry = r10(ly + 1, lz), rz = r10(ly, lz + 1);
+        const float g0 = masked_diff(o && (om_r & 1u), ub[0], um);
+        const float g1 = masked_diff(o && ((s.om[ry] >> 9) & 1u), s.xhm[ry], um);
+        const float g2 = masked_diff(o && ((s.om[rz] >> 9) & 1u), s.xhm[rz], um);
+        float out[3];
+        dual_update(hm0, hm1, hm2, g0, g1, g2, a.sigma, out);
+        s.pxm[r] = out[0];
+    }
+    {
+        // one voxel of the -y face, (fx, -1, fz), and one of the -z face, (fx, fy, -1)
+        const int fx = r & 7, fw = r >> 3;
+        {  // -y face: fw is z
+            const int d = r10(-1, fw), dz = r10(-1, fw + 1), dc = r10(0, fw);
+            const unsigned om = s.om[d];
+            const bool o = (om >> fx) & 1u;
+            const float v = s.ub[d][fx];
+            const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
+            const float g1 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
+            const float g2 = masked_diff(o && ((s.om[dz] >> fx) & 1u), s.ub[dz][fx], v);
+            float out[3];
+            dual_update(s.pfy[0][fw][fx], s.pfy[1][fw][fx], s.pfy[2][fw][fx], g0, g1, g2, a.sigma, out);
+            s.py[r9(-1, fw)][fx] = out[1];
         }
-        sts_row(s.py[r9(ly, lz)], p1);
-        sts_row(s.pz[r9(ly, lz)], p2);
-        __syncthreads();
+        {  // -z face: fw is y
+            const int d = r10(fw, -1), dy = r10(fw + 1, -1), dc = r10(fw, 0);
+            const unsigned om = s.om[d];
+            const bool o = (om >> fx) & 1u;
+            const float v = s.ub[d][fx];
+            const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
+            const float g1 = masked_diff(o && ((s.om[dy] >> fx) & 1u), s.ub[dy][fx], v);
+            const float g2 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
+            float out[3];
+            dual_update(s.pfz[0][fw][fx], s.pfz[1][fw][fx], s.pfz[2][fw][fx], g0, g1, g2, a.sigma, out);
+            s.pz[r9(fw, -1)][fx] = out[2];
+        }
+    }
+    sts_row(s.py[r9(ly, lz)], p1);
+    sts_row(s.pz[r9(ly, lz)], p2);
+    __syncthreads();
 
-        // ----------------------------------------------- primal + relaxation
-        {
-            float pym[8], pzm[8];
-            lds_row(s.py[r9(ly - 1, lz)], pym);
-            lds_row(s.pz[r9(ly, lz - 1)], pzm);
-            const unsigned om_ym = s.om[r10(ly - 1, lz)], om_zm = s.om[r10(ly, lz - 1)];
-            const unsigned om_yp = s.om[r10(ly + 1, lz)], om_zp = s.om[r10(ly, lz + 1)];
-            const float pxm = s.pxm[r];
-            float un[8], ubn[8];
+    // ----------------------------------------------- primal + relaxation
+    {
+        float pym[8], pzm[8];
+        lds_row(s.py[r9(ly - 1, lz)], pym);
+        lds_row(s.pz[r9(ly, lz - 1)], pzm);
+        const unsigned om_ym = s.om[r10(ly - 1, lz)], om_zm = s.om[r10(ly, lz - 1)];
+        const unsigned om_yp = s.om[r10(ly + 1, lz)], om_zp = s.om[r10(ly, lz + 1)];
+        const float pxm = s.pxm[r];
+        float un[8], ubn[8];
 #pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                const bool o = (om_r >> x) & 1u;
-                const bool exm = o && (x > 0 ? ((om_r >> (x - 1)) & 1u) : ((om_r >> 9) & 1u));
-                const float dv = div_terms(o && ((om_r >> (x + 1)) & 1u), p0[x], exm, x > 0 ? p0[x > 0 ? x - 1 : 0] : pxm,
-                                           o && ((om_yp >> x) & 1u), p1[x], o && ((om_ym >> x) & 1u), pym[x],
-                                           o && ((om_zp >> x) & 1u), p2[x], o && ((om_zm >> x) & 1u), pzm[x]);
-                primal_update(o, uo[x], o ? dv : 0.0f, fv[x], wv[x], a.tau, a.tau_lam, a.theta, &un[x], &ubn[x]);
-            }
-            st_row<T>(a.u + base, un);
-            st_row<T>(a.ub_out + base, ubn);
-            st_row<T>(a.p_out + base, p0);
-            st_row<T>(a.p_out + ps + base, p1);
-            st_row<T>(a.p_out + 2 * ps + base, p2);
+        for (int x = 0; x < 8; ++x) {
+            const bool o = (om_r >> x) & 1u;
+            const bool exm = o && (x > 0 ? ((om_r >> (x - 1)) & 1u) : ((om_r >> 9) & 1u));
+            const float dv = div_terms(o && ((om_r >> (x + 1)) & 1u), p0[x], exm, x > 0 ? p0[x > 0 ? x - 1 : 0] : pxm,
+                                       o && ((om_yp >> x) & 1u), p1[x], o && ((om_ym >> x) & 1u), pym[x],
+                                       o && ((om_zp >> x) & 1u), p2[x], o && ((om_zm >> x) & 1u), pzm[x]);
+            primal_update(o, uo[x], o ? dv : 0.0f, fv[x], wv[x], a.tau, a.tau_lam, a.theta, &un[x], &ubn[x]);
         }
+        st_row<T>(a.u + base, un);
+        st_row<T>(a.ub_out + base, ubn);
+        st_row<T>(a.p_out + base, p0);
+        st_row<T>(a.p_out + ps + base, p1);
+        st_row<T>(a.p_out + 2 * ps + base, p2);
+    }
+}
+
+// Loads the neighbour row of block b (every thread reads the same 48 bytes).
+__device__ inline void load_nbr_row(const int32_t* __restrict__ nbr, int b, int* out) {
+    const int4* p = reinterpret_cast<const int4*>(nbr + (size_t)b * kNeighbours);
+    const int4 x = __ldg(p), y = __ldg(p + 1), z = __ldg(p + 2);
+    out[0] = x.x, out[1] = x.y, out[2] = x.z, out[3] = x.w, out[4] = y.x, out[5] = y.y;
+    out[6] = y.z, out[7] = y.w, out[8] = z.x, out[9] = z.y, out[10] = z.z, out[11] = z.w;
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs<T> a) {
+    __shared__ RowTiles s;
+    const int G = gridDim.x;
+    int k = blockIdx.x;
+    if (k >= a.n_blocks) return;
+    // the next block's index and neighbour row are fetched one block ahead, so that a
+    // block's halo loads do not wait behind two dependent round trips
+    int b = a.order ? __ldg(a.order + k) : k;
+    int nb[kNeighbours], nb_next[kNeighbours];
+    load_nbr_row(a.nbr, b, nb);
+    for (; k < a.n_blocks; k += G) {
+        const int kn = k + G;
+        int b_next = -1;
+        if (kn < a.n_blocks) {
+            b_next = a.order ? __ldg(a.order + kn) : kn;
+            load_nbr_row(a.nbr, b_next, nb_next);
+        }
+        rows_block<T>(a, s, b, threadIdx.x, nullptr, nb);
         __syncthreads();  // the tiles are rewritten for the next block
+        b = b_next;
+#pragma unroll
+        for (int i = 0; i < kNeighbours; ++i) nb[i] = nb_next[i];
+    }
+}
+
+// ------------------------------------------------------- row sweep with TMA
+// The row sweep with the next block's own fields prefetched: while a CTA computes
+// block k, one thread has already issued 1-D bulk copies (cp.async.bulk, the TMA
+// engine) of block k + grid into the other half of a double-buffered stage, completing
+// on that half's mbarrier.  The waits are bounded: a copy that never lands sets the
+// timeout flag and the CTA stops instead of spinning forever.
+__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((unsigned)__cvta_generic_to_shared(bar)), "r"(count)
+                 : "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ inline void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
+
+template <typename T>
+__device__ inline void stage_issue(const SweepArgs<T>& a, char* dst, int b, uint64_t* bar) {
+    using L = RowStage<T>;
+    const size_t v0 = (size_t)b * kBlockVoxels;
+    // order earlier generic reads of this half before the asynchronous writes into it
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, L::kTx);
+    bulk_load(dst + L::kUb, a.ub_in + v0, L::kField, bar);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bulk_load(dst + L::kP + c * L::kField, a.p_in + c * a.pstride + v0, L::kField, bar);
+    bulk_load(dst + L::kU, a.u + v0, L::kField, bar);
+    bulk_load(dst + L::kF, a.f + v0, kBlockVoxels * 4, bar);
+    bulk_load(dst + L::kW, a.w + v0, kBlockVoxels * 4, bar);
+    bulk_load(dst + L::kBits, a.bits + (size_t)b * 16, 64, bar);
+}
+
+constexpr long long kWaitLimit = 1ll << 22;  // try_wait rounds before a wait counts as lost
+
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads, 4) sweep_rows_tma_kernel(SweepArgs<T> a) {
+    using L = RowStage<T>;
+    __shared__ RowTiles s;
+    __shared__ __align__(8) uint64_t bars[2];
+    extern __shared__ __align__(128) char stages[];  // [2][L::kBytes]
+    const int t = threadIdx.x;
+    const int G = gridDim.x;
+    int k = blockIdx.x;
+    if (k >= a.n_blocks) return;
+    if (t == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    auto block_at = [&](int kk) { return a.order ? __ldg(a.order + kk) : kk; };
+    if (t == 0) stage_issue<T>(a, stages, block_at(k), &bars[0]);
+    unsigned parity[2] = {0u, 0u};
+    for (int i = 0; k < a.n_blocks; ++i, k += G) {
+        const int h = i & 1;
+        if (t == 0 && k + G < a.n_blocks) stage_issue<T>(a, stages + (h ^ 1) * L::kBytes, block_at(k + G), &bars[h ^ 1]);
+        long long it = 0;
+        while (!mbar_try_wait(&bars[h], parity[h]) && ++it < kWaitLimit) {
+        }
+        if (it >= kWaitLimit) {
+            if (t == 0) atomicOr(a.err, kErrTimeout);
+            return;
+        }
+        parity[h] ^= 1u;
+        const int b = block_at(k);
+        int nb[kNeighbours];
+        load_nbr_row(a.nbr, b, nb);
+        rows_block<T>(a, s, b, t, stages + h * L::kBytes, nb);
+        __syncthreads();  // tiles and this stage half are reused
     }
 }
 
@@ -883,16 +1039,38 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
     a.tau_lam = (float)(c->prm.tau * c->prm.lambda);
     a.theta = (float)c->prm.theta;
     a.order = c->sched.order ? c->order : nullptr;
+    a.err = c->d.counters + kErrorBits;
     if (c->sched.sweep_kernel == 0) {
         const int per_sm = c->sched.ctas_per_sm > 0 ? c->sched.ctas_per_sm : 4;
         const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * per_sm);
         sweep_kernel<T><<<grid, kSweepThreads, 0, s>>>(a);
     } else if (c->sched.sweep_kernel == 2) {
-        int per_sm = c->sched.ctas_per_sm * 4;  // 64-thread CTAs: four per 256 threads
-        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T>, kRowThreads, 0);
-        if (per_sm <= 0) per_sm = 8;
-        const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * per_sm);
-        sweep_rows_kernel<T><<<grid, kRowThreads, 0, s>>>(a);
+        // ctas_per_sm selects the register budget: 0 / 1: up to 8 resident CTAs per SM
+        // (128 registers), 2: 10 (96 registers), 3: 12
+        int per_sm = 0;
+        switch (c->sched.ctas_per_sm) {
+            case 2:
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 10>, kRowThreads, 0);
+                sweep_rows_kernel<T, 10><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
+                                           kRowThreads, 0, s>>>(a);
+                break;
+            case 3:
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 12>, kRowThreads, 0);
+                sweep_rows_kernel<T, 12><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
+                                           kRowThreads, 0, s>>>(a);
+                break;
+            default:
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 8>, kRowThreads, 0);
+                sweep_rows_kernel<T, 8><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
+                                          kRowThreads, 0, s>>>(a);
+        }
+    } else if (c->sched.sweep_kernel == 3) {
+        int per_sm = 0;
+        const size_t smem = 2 * (size_t)RowStage<T>::kBytes;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_tma_kernel<T>, kRowThreads, smem);
+        if (c->sched.ctas_per_sm > 0) per_sm = std::min(per_sm, 2 * c->sched.ctas_per_sm);
+        const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1));
+        sweep_rows_tma_kernel<T><<<grid, kRowThreads, smem, s>>>(a);
     } else {
         const int per_sm = c->sched.ctas_per_sm > 0 ? c->sched.ctas_per_sm : 2;
         const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * per_sm);
