@@ -195,6 +195,30 @@ int denser_extract(denser_ctx* ctx, int32_t* coords, float* f, float* w, uint8_t
 int denser_extract_dual(denser_ctx* ctx, float* u_bar, float* p, int64_t capacity_blocks,
                         void* stream);
 
+/* Surface extraction: the zero level set of u over the observed voxels, as a list of
+ * triangles.  The paper's pipeline extracts a surface from the regularised model for
+ * other components (Section II, Fig. 1) but names no method; this one meshes each cube
+ * of 2x2x2 voxel centres whose eight corners are observed (w > 0), split into the six
+ * Kuhn tetrahedra around its main diagonal, with a vertex at the linear zero of u on
+ * every tetrahedron edge whose ends differ in sign (u < 0 negative, u >= 0 not).
+ * Triangles are wound so that (v1 - v0) x (v2 - v0) points to the side u >= 0, and are
+ * ordered by block index, cube (lower corner's local index), tetrahedron, triangle.
+ *   tri_pos  float32 [capacity][3][3]: vertex world positions in metres (voxel (i,j,k)
+ *            has its centre at ((i,j,k) + 1/2) voxel_size in its segment's frame);
+ *   tri_ids  int64 [capacity][3]: vertex ids, (flat voxel index of the edge's lower end
+ *            = block * 512 + local index) * 8 + direction bits (1 +x, 2 +y, 4 +z); equal
+ *            ids are the same vertex.
+ *   block_first  int64 [n_blocks + 1]: index of each block's first triangle (the
+ *            triangles of block b, those whose cube has its lower corner in b, are
+ *            [block_first[b], block_first[b + 1])), block_first[n_blocks] = total.
+ * Any of the three may be NULL (all NULL counts only); each may be host or device
+ * memory (host triangle buffers are staged through device scratch the context keeps).
+ * *n_tri_out (host, required) receives the total number of triangles.  The call waits
+ * for the stream.  When the total exceeds capacity, the first `capacity` triangles are
+ * written and DENSER_ERR_TOO_LARGE is returned (block_first is complete either way). */
+int denser_extract_surface(denser_ctx* ctx, float* tri_pos, int64_t* tri_ids, int64_t capacity,
+                           int64_t* n_tri_out, int64_t* block_first, void* stream);
+
 /* Appends n blocks with the given coordinates (int32 [n][4]) and fusion state
  * (f, w float32 [n][512]; NULL = zeros) in the given order, with zero primal-dual
  * state.  A coordinate already in the map is DENSER_ERR_INVALID_ARG. */

@@ -140,11 +140,12 @@ def voxel_world(keys, voxel_size: float):
     return ((ijk.astype(np.float64) + 0.5) * voxel_size).reshape(-1, 3)
 
 
-def extract_surface(keys, u, om, voxel_size: float):
+def extract_surface(keys, u, om, voxel_size: float, blocks=None):
     """Zero level set of u over Omega (S1-S5).
 
     keys: [nb] (segment, bx, by, bz) in block-index order; u: [nb, 512]; om: [nb, 512]
-    bool.  Returns (pos [n, 3, 3] float64 world metres, ids [n, 3] int64 edge ids)."""
+    bool; blocks: optional block indices whose cubes (by lower corner) alone are meshed.
+    Returns (pos [n, 3, 3] float64 world metres, ids [n, 3] int64 edge ids)."""
     nb = len(keys)
     u = np.asarray(u, dtype=np.float64).reshape(-1)
     om = np.asarray(om, dtype=bool).reshape(-1)
@@ -156,6 +157,10 @@ def extract_surface(keys, u, om, voxel_size: float):
     cu = np.where(valid[:, None], u[np.where(corners >= 0, corners, 0)], 0.0)
     neg = cu < 0
     crossing = valid & np.any(neg, axis=1) & ~np.all(neg, axis=1)
+    if blocks is not None:
+        chosen = np.zeros(nb, dtype=bool)
+        chosen[np.asarray(blocks, dtype=np.int64)] = True
+        crossing &= np.repeat(chosen, BLOCK_VOXELS)
     tets = kuhn_tets()
     pos, ids = [], []
     for cube in np.nonzero(crossing)[0]:  # ascending = block, then local index

@@ -168,7 +168,7 @@ __device__ inline void warp_insert(const DeviceMap& m, const RayKeys& rk, int la
     }
 }
 
-__global__ void __maxnreg__(96) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
+__global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
     const int npix = a.W * a.H;
     const int lane = threadIdx.x & 31;
     bool range_err = false;

@@ -171,7 +171,8 @@ void free_all(denser_ctx* c) {
     void* ptrs[] = {c->d.hash_keys, c->d.hash_vals, c->d.coords, c->d.f, c->d.w, c->d.u, c->d.ub[0], c->d.ub[1],
                     c->d.p[0], c->d.p[1], c->d.omega_bits, c->d.nbr, c->d.counters, c->d.new_keys,
                     c->d.new_slots, c->d.visible, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch,
-                    c->order, c->order_keys, c->order_vals, c->ctl_i, c->ctl_d};
+                    c->order, c->order_keys, c->order_vals, c->ctl_i, c->ctl_d, c->surf_counts,
+                    c->surf_offsets, c->surf_scratch};
     release_graph_loop(c);
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -224,6 +225,7 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->nbr_valid_blocks = -1;
     c->stage = nullptr, c->stage_bytes = 0, c->hstage = nullptr, c->hstage_bytes = 0;
     c->omega_bytes = nullptr, c->conv_scratch = nullptr, c->conv_bytes = 0;
+    c->surf_counts = nullptr, c->surf_offsets = nullptr, c->surf_scratch = nullptr, c->surf_bytes = 0;
     c->h_counters = nullptr, c->h_energy = nullptr;
     c->launches = 0;
     c->sched.sweep_kernel = 2;
@@ -550,6 +552,66 @@ int denser_extract_dual(denser_ctx* c, float* u_bar, float* p, int64_t capacity_
                 if ((rc = copy_state_out(c, p + a * nv, (char*)c->d.p[c->cur] + a * pstride, nv, s))) return rc;
         }
         return cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+    });
+}
+
+int denser_extract_surface(denser_ctx* c, float* tri_pos, int64_t* tri_ids, int64_t capacity, int64_t* n_tri_out,
+                           int64_t* block_first, void* stream) {
+    return guarded(c, [&]() -> int {
+        if (!n_tri_out || capacity < 0)
+            return set_error(c, DENSER_ERR_INVALID_ARG, "extract_surface: n_tri_out is required and capacity >= 0");
+        *n_tri_out = 0;
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if (nb == 0) {
+            if (block_first) {  // host or device memory: written through a copy
+                const long long zero = 0;
+                if ((rc = copy_out(c, block_first, &zero, 8, s, "copy block offsets"))) return rc;
+                return cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+            }
+            return DENSER_OK;
+        }
+        if (!c->surf_counts) {
+            if ((rc = cuda_check(c, cudaMalloc(&c->surf_counts, (size_t)c->d.max_blocks * 4), "cudaMalloc(surface counts)")))
+                return rc;
+            if ((rc = cuda_check(c, cudaMalloc(&c->surf_offsets, ((size_t)c->d.max_blocks + 1) * 8),
+                                 "cudaMalloc(surface offsets)")))
+                return rc;
+        }
+        if ((rc = launch_surface(c, nb, 0, nullptr, nullptr, 0, s))) return rc;
+        long long total = 0;
+        if ((rc = copy_out(c, &total, c->surf_offsets + nb, 8, s, "read triangle count"))) return rc;
+        if ((rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize"))) return rc;
+        *n_tri_out = total;
+        if (block_first && (rc = copy_out(c, block_first, c->surf_offsets, ((size_t)nb + 1) * 8, s, "copy block offsets")))
+            return rc;
+        if (!tri_pos && !tri_ids) return cuda_check(c, cudaStreamSynchronize(s), "stream synchronize");
+        const int64_t n_out = std::min<int64_t>(total, capacity);
+        if (n_out > 0) {
+            // host outputs go through device scratch: ids first (8-byte aligned), then positions
+            const bool host_ids = tri_ids && !is_device_ptr(tri_ids), host_pos = tri_pos && !is_device_ptr(tri_pos);
+            const size_t ids_bytes = (size_t)n_out * 24, pos_bytes = (size_t)n_out * 36;
+            const size_t need = (host_ids ? ids_bytes : 0) + (host_pos ? pos_bytes : 0);
+            if (need > c->surf_bytes) {
+                if (c->surf_scratch) cudaFree(c->surf_scratch);
+                c->surf_scratch = nullptr;
+                c->surf_bytes = 0;
+                if ((rc = cuda_check(c, cudaMalloc(&c->surf_scratch, need), "cudaMalloc(surface scratch)"))) return rc;
+                c->surf_bytes = need;
+            }
+            long long* dids = host_ids ? (long long*)c->surf_scratch : (long long*)tri_ids;
+            float* dpos = host_pos ? (float*)((char*)c->surf_scratch + (host_ids ? ids_bytes : 0)) : tri_pos;
+            if ((rc = launch_surface(c, nb, 1, dpos, dids, n_out, s))) return rc;
+            if (host_ids && (rc = copy_out(c, tri_ids, dids, ids_bytes, s, "copy triangle ids"))) return rc;
+            if (host_pos && (rc = copy_out(c, tri_pos, dpos, pos_bytes, s, "copy triangles"))) return rc;
+        }
+        if ((rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize"))) return rc;
+        if (total > capacity)
+            return set_error(c, DENSER_ERR_TOO_LARGE,
+                             "extract_surface: more triangles than capacity (*n_tri_out holds the total)");
+        return DENSER_OK;
     });
 }
 

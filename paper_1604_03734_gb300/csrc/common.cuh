@@ -134,6 +134,10 @@ struct denser_ctx {
     uint8_t* omega_bytes;      // extract scratch
     float* conv_scratch;       // float32 staging of converted state
     size_t conv_bytes;
+    int32_t* surf_counts;      // [max_blocks] triangles per block (surface extraction)
+    long long* surf_offsets;   // [max_blocks + 1] their exclusive scan
+    void* surf_scratch;        // device staging of host surface outputs
+    size_t surf_bytes;
     int32_t* h_counters;       // pinned copy of the device counters
     double* h_energy;          // pinned [2]
     unsigned long long launches;
@@ -173,6 +177,8 @@ int launch_energy(denser_ctx* c, int64_t n_blocks, cudaStream_t s);
 int launch_omega_bytes(denser_ctx* c, int64_t n_blocks, uint8_t* out, cudaStream_t s);
 int launch_convert_state(denser_ctx* c, const void* src, float* dst, int64_t n, bool to_float,
                          cudaStream_t s);
+int launch_surface(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long long* tri_ids, int64_t capacity,
+                   cudaStream_t s);
 int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s);
 int launch_sort_pairs(denser_ctx* c, unsigned long long* keys, uint32_t* vals, const int32_t* count, int capacity,
                       cudaStream_t s);

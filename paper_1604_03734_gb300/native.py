@@ -29,7 +29,7 @@ DENSER_FP32, DENSER_FP16, DENSER_BF16 = 0, 1, 2
 # every symbol include/denser.h declares
 EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_reset",
            "denser_last_error", "denser_sync", "denser_alloc_blocks", "denser_fuse_depth",
-           "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual",
+           "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual", "denser_extract_surface",
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
            "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc",
            "denser_net_gather", "denser_net_targets", "denser_net_apply", "denser_conv3", "denser_conv3_wgrad",
@@ -96,6 +96,7 @@ def lib():
             "denser_energy": (_i32, [_vp, P(_dbl), P(_dbl), _vp]),
             "denser_extract": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, P(_i64), _vp]),
             "denser_extract_dual": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+            "denser_extract_surface": (_i32, [_vp, _vp, _vp, _i64, P(_i64), _vp, _vp]),
             "denser_load_blocks": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
             "denser_load_state": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
             "denser_num_blocks": (_i64, [_vp, _vp]),
@@ -139,7 +140,7 @@ def _ptr(buf, dtype=None):
             raise ValueError("tensor must be contiguous")
         if dtype is not None:
             want = {np.float32: torch.float32, np.int32: torch.int32, np.uint8: torch.uint8,
-                    np.float64: torch.float64}[dtype]
+                    np.float64: torch.float64, np.int64: torch.int64}[dtype]
             if buf.dtype != want:
                 raise TypeError(f"expected {want}, got {buf.dtype}")
         return buf.data_ptr()
@@ -249,6 +250,19 @@ def denser_extract(ctx, coords=None, f=None, w=None, omega=None, u=None, capacit
 def denser_extract_dual(ctx, u_bar=None, p=None, capacity_blocks=0, stream=None):
     return _check(ctx, lib().denser_extract_dual(ctx, _ptr(u_bar, np.float32), _ptr(p, np.float32),
                                                  int(capacity_blocks), _stream(stream)))
+
+
+def denser_extract_surface(ctx, tri_pos=None, tri_ids=None, capacity=0, block_first=None, stream=None) -> int:
+    """Triangles of the zero level set of u over Omega (float32 [cap][3][3] positions,
+    int64 [cap][3] vertex ids, int64 [n_blocks + 1] first triangle per block); returns
+    the total triangle count.  A total above `capacity` with a triangle buffer raises
+    DenserError (DENSER_ERR_TOO_LARGE) after the first `capacity` triangles are written;
+    count first with the triangle buffers None."""
+    n = _i64(0)
+    _check(ctx, lib().denser_extract_surface(ctx, _ptr(tri_pos, np.float32), _ptr(tri_ids, np.int64),
+                                             int(capacity), ctypes.byref(n), _ptr(block_first, np.int64),
+                                             _stream(stream)))
+    return n.value
 
 
 def denser_load_blocks(ctx, coords, f=None, w=None, n=None, stream=None):
@@ -387,3 +401,13 @@ class DenserMap:
             out["p"] = np.zeros((3, n, 512), np.float32)
             denser_extract_dual(self.ctx, out["u_bar"], out["p"], n)
         return out
+
+    def surface(self, with_ids=True, stream=None):
+        """Host copies of the surface triangles: positions float32 [n, 3, 3] (metres) and,
+        with_ids, vertex ids int64 [n, 3]."""
+        n = denser_extract_surface(self.ctx, stream=stream)
+        pos = np.zeros((n, 3, 3), np.float32)
+        ids = np.zeros((n, 3), np.int64) if with_ids else None
+        if n:
+            denser_extract_surface(self.ctx, pos, ids, n, stream=stream)
+        return (pos, ids) if with_ids else pos
