@@ -25,7 +25,11 @@
  *   pageable); the library looks the pointer up with cudaPointerGetAttributes and
  *   stages host memory through its own device buffers.  The caller owns every
  *   buffer it passes; the context owns the hash table, the block pool and the
- *   primal-dual state.
+ *   primal-dual state.  Host depth maps are copied on a stream of the context's own
+ *   (into one of two buffers, so that a frame's copy overlaps the previous frame's
+ *   kernels) and the call's stream waits for that copy: like any asynchronous copy
+ *   from pinned memory, the host buffer must stay unchanged until the call's stream
+ *   has passed the call.
  *
  * Streams and errors
  *   `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls enqueue
@@ -164,6 +168,11 @@ int denser_alloc_blocks(denser_ctx* ctx, const float* depth, const denser_intrin
  * float64 (bit-exact with the oracle); f is accumulated in float32. */
 int denser_fuse_depth(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
                       const double T_gc[16], int32_t segment, void* stream);
+
+/* denser_alloc_blocks followed by denser_fuse_depth on the same depth map, which is
+ * staged once when it is in host memory.  Arguments and results as those two calls. */
+int denser_integrate(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
+                     const double T_gc[16], int32_t segment, void* stream, int32_t* n_new_out);
 
 /* Regularisation (Section III-B/C): Chambolle-Pock iterations on the Omega-aware
  * TV-L2 energy over the allocated blocks, Omega = {w > 0}:

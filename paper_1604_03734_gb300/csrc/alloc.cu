@@ -94,49 +94,6 @@ __device__ __forceinline__ unsigned long long sample_key(const AllocArgs& a, int
     return pack_key(a.seg, (int32_t)k[0], (int32_t)k[1], (int32_t)k[2]);
 }
 
-// Float32 evaluation of sample n's key with a forward error bound.  The key of a
-// sample is floor(t/bs + z D), D = R (u/fx, v/fy, 1) / bs the pixel's ray step per
-// metre of depth in block units, z = d + n h.  D is evaluated once per pixel in float32
-// and DA bounds the magnitude of its terms (its rounding error is below 2^-21 DA).
-// Returns 1 when every floor is certified (key, or kEmptyKey for z <= 0, in *key),
-// 0 when the float64 path must decide.
-__device__ __forceinline__ int sample_key_f32(const AllocArgs& a, const float* D, const float* DA, float d, float nf,
-                                              bool* range_err, unsigned long long* key) {
-    const float eps = 9.53674316e-7f;  // 2^-20
-    const float nh = a.nhf;
-    const float z = fmaf(nf, a.hf, d);
-    const float ez = eps * (fabsf(d) + nh) + 1e-30f;
-    if (z < -ez) {
-        *key = kEmptyKey;
-        return 1;
-    }
-    if (!(z > ez)) return 0;
-    int kf[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const float q = fmaf(z, D[r], a.tf[r]);
-        if (!(fabsf(q) < 2097152.0f)) {  // |q| >= 2^21: the key is beyond 2^18 whatever Ti is
-            *range_err = true;
-            *key = kEmptyKey;
-            return 1;
-        }
-        // |q - q_real| <= 2^-21 DA (1.25 z + 0.125 nh) + 2^-24 (|q| + 1) (the rounding of D, of
-        // z, of the fma and of t / bs); e covers each term at least twice
-        const float e = fmaf(1.25f * eps, DA[r] * (z + nh), 0.25f * eps * (fabsf(q) + 1.0f));
-        const int lo = floor_small(q - e);
-        if (lo != floor_small(q + e)) return 0;
-        kf[r] = lo;
-    }
-    const int k0 = a.Ti[0] + kf[0], k1 = a.Ti[1] + kf[1], k2 = a.Ti[2] + kf[2];
-    if (!key_in_range(a.seg, k0, k1, k2)) {
-        *range_err = true;
-        *key = kEmptyKey;
-        return 1;
-    }
-    *key = pack_key(a.seg, k0, k1, k2);
-    return 1;
-}
-
 // A ray's distinct keys, held in four registers (selected by constant indices only, so
 // that they never spill to local memory).
 struct RayKeys {
@@ -168,9 +125,23 @@ __device__ inline void warp_insert(const DeviceMap& m, const RayKeys& rk, int la
     }
 }
 
+// Keys of every valid pixel's band samples (reading R1), inserted into the hash.
+//
+// The key of a sample is floor(t/bs + z D) per axis, D = R (u/fx, v/fy, 1) / bs the
+// pixel's ray step per metre of depth in block units and z = d + n h.  It is
+// evaluated in float32 with an error bound and certified when no integer lies within
+// the bound; otherwise the float64 path in the oracle's operation order decides.
+// Per ray: D (rounding error below 2^-21 DA, DA the magnitude of its terms), the
+// bound on |z| error ez = 2^-20 (d + N h), and per axis one bound e for all samples,
+//   |q - q_real| <= 2^-21 DA (1.25 z + 0.125 N h) + 2^-24 (|q| + 1)
+// (rounding of D, of z, of the fma and of t/bs), covered at least twice by
+//   e = 2.5 2^-21 DA (z_max + N h) + 2^-22 (q_max + 1),
+// q linear in z so that q_max = max |q| over the band's two ends.
 __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
     const int npix = a.W * a.H;
     const int lane = threadIdx.x & 31;
+    const float eps = 9.53674316e-7f;  // 2^-20
+    const float kMagic = 12582912.0f;  // 1.5 2^23: v + kMagic holds the integer nearest v for |v| < 2^22
     bool range_err = false;
     // The loop bound is warp-uniform so every lane reaches the warp collectives.
     for (int base = blockIdx.x * blockDim.x; base < npix; base += gridDim.x * blockDim.x) {
@@ -178,26 +149,68 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
         float dv = pix < npix ? __ldg(depth + pix) : 0.0f;
         const bool valid = pix < npix && isfinite(dv) && dv > 0.0f;
         const int y = (int)__umul64hi((unsigned long long)(unsigned)pix, a.w_magic), x = pix - y * a.W;
-        float D[3] = {0.0f, 0.0f, 0.0f}, DA[3] = {0.0f, 0.0f, 0.0f};
+        float D[3] = {0.0f, 0.0f, 0.0f}, e[3] = {0.0f, 0.0f, 0.0f};
+        float ez = 0.0f;
+        bool fast = false;
         if (valid) {
             // u = (x + 0.5) - cx with cx as hi + lo: relative error below 2^-23
             const float ua = (((float)x + 0.5f) - a.cx_hi) - a.cx_lo;
             const float va = (((float)y + 0.5f) - a.cy_hi) - a.cy_lo;
             const float ax = ua * a.ifx, ay = va * a.ify;
+            const float zmax = dv + a.nhf, zmin = dv - a.nhf;
+            ez = eps * zmax + 1e-30f;
+            fast = true;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 D[r] = fmaf(a.Rf[3 * r], ax, fmaf(a.Rf[3 * r + 1], ay, a.Rf[3 * r + 2])) * a.ibs;
-                DA[r] = (fabsf(a.Rf[3 * r] * ax) + fabsf(a.Rf[3 * r + 1] * ay) + fabsf(a.Rf[3 * r + 2])) * a.ibs;
+                const float DA = (fabsf(a.Rf[3 * r] * ax) + fabsf(a.Rf[3 * r + 1] * ay) + fabsf(a.Rf[3 * r + 2])) * a.ibs;
+                const float qm = fmaxf(fabsf(fmaf(zmin, D[r], a.tf[r])), fabsf(fmaf(zmax, D[r], a.tf[r])));
+                fast = fast && qm < 2097152.0f;  // beyond 2^21 the float64 path reports the range
+                e[r] = fmaf(1.25f * eps, DA * (zmax + a.nhf), 0.25f * eps * (qm + 1.0f));
             }
         }
         // the distinct block keys of this ray's band samples, in sample order (consecutive
         // samples mostly share a block), inserted a warp round at a time once collected
         RayKeys rk;
         unsigned long long last = kEmptyKey;
+        int l0 = INT_MIN, l1 = 0, l2 = 0;  // last certified floor triple (INT_MIN: none)
         float nf = (float)(-a.N);
         for (int n = -a.N; valid && n <= a.N; ++n, nf += 1.0f) {
             unsigned long long key = kEmptyKey;
-            if (!sample_key_f32(a, D, DA, dv, nf, &range_err, &key)) key = sample_key(a, x, y, (double)dv, n, &range_err);
+            bool decided = false;
+            if (fast) {
+                const float z = fmaf(nf, a.hf, dv);
+                if (z < -ez) continue;  // certainly behind the camera
+                if (z > ez) {
+                    bool ok = true;
+                    int k[3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        const float q = fmaf(z, D[r], a.tf[r]);
+                        const float tq = __fadd_rn(q, kMagic);  // nearest integer n + kMagic
+                        const float nq = tq - kMagic;
+                        const bool down = nq > q;               // floor(q) = n - 1
+                        const float fr = q - (down ? nq - 1.0f : nq);  // q - floor(q), exact
+                        ok = ok && fr >= e[r] && 1.0f - fr > e[r];
+                        k[r] = __float_as_int(tq) - 0x4B400000 - (down ? 1 : 0);
+                    }
+                    if (ok) {
+                        if (k[0] == l0 && k[1] == l1 && k[2] == l2) continue;  // same block as before
+                        l0 = k[0], l1 = k[1], l2 = k[2];
+                        const int b0 = a.Ti[0] + k[0], b1 = a.Ti[1] + k[1], b2 = a.Ti[2] + k[2];
+                        if (!key_in_range(a.seg, b0, b1, b2)) {
+                            range_err = true;
+                            continue;
+                        }
+                        key = pack_key(a.seg, b0, b1, b2);
+                        decided = true;
+                    }
+                }
+            }
+            if (!decided) {
+                key = sample_key(a, x, y, (double)dv, n, &range_err);
+                l0 = INT_MIN;
+            }
             if (key == kEmptyKey || key == last) continue;
             last = key;
             if (rk.count == 4) {  // a very oblique ray: insert what it holds (divergent, rare)

@@ -86,6 +86,47 @@ int device_input(denser_ctx* c, const void* src, size_t bytes, cudaStream_t s, c
     return DENSER_OK;
 }
 
+// A device pointer to a depth map: `src` itself when it is device memory, else a copy
+// made on the context's copy stream into the next of two staging buffers.  The copy
+// waits until the kernels that read that buffer two frames ago are done, and `s` waits
+// for the copy; *slot names the buffer for release_depth (-1: none).
+int stage_depth(denser_ctx* c, const float* src, size_t bytes, cudaStream_t s, const float** out, int* slot) {
+    *slot = -1;
+    if (is_device_ptr(src)) {
+        *out = src;
+        return DENSER_OK;
+    }
+    const int i = c->dstage_next;
+    c->dstage_next ^= 1;
+    int rc;
+    if (c->dstage_bytes[i] < bytes) {
+        // the buffer may still be read by queued kernels: wait for them before freeing
+        if (c->dstage[i]) {
+            if ((rc = cuda_check(c, cudaEventSynchronize(c->dstage_free[i]), "wait for staging buffer"))) return rc;
+            cudaFree(c->dstage[i]);
+        }
+        c->dstage[i] = nullptr;
+        c->dstage_bytes[i] = 0;
+        if ((rc = cuda_check(c, cudaMalloc(&c->dstage[i], bytes), "cudaMalloc(depth staging)"))) return rc;
+        c->dstage_bytes[i] = bytes;
+    }
+    if ((rc = cuda_check(c, cudaStreamWaitEvent(c->copy_stream, c->dstage_free[i], 0), "copy stream wait"))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(c->dstage[i], src, bytes, cudaMemcpyHostToDevice, c->copy_stream),
+                         "copy depth to device")))
+        return rc;
+    if ((rc = cuda_check(c, cudaEventRecord(c->dstage_copied[i], c->copy_stream), "record copy"))) return rc;
+    if ((rc = cuda_check(c, cudaStreamWaitEvent(s, c->dstage_copied[i], 0), "stream wait for copy"))) return rc;
+    *out = c->dstage[i];
+    *slot = i;
+    return DENSER_OK;
+}
+
+// Marks staging buffer `slot` free once the work queued so far on `s` is done.
+int release_depth(denser_ctx* c, int slot, cudaStream_t s) {
+    if (slot < 0) return DENSER_OK;
+    return cuda_check(c, cudaEventRecord(c->dstage_free[slot], s), "record staging release");
+}
+
 int device_error_code(denser_ctx* c, int32_t bits) {
     if (!bits) return DENSER_OK;
     if (bits & kErrHashFull) return set_error(c, DENSER_ERR_HASH_FULL, "hash table full (probe limit reached)");
@@ -172,7 +213,7 @@ void free_all(denser_ctx* c) {
                     c->d.p[0], c->d.p[1], c->d.omega_bits, c->d.nbr, c->d.counters, c->d.new_keys,
                     c->d.new_slots, c->d.visible, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch,
                     c->order, c->order_keys, c->order_vals, c->ctl_i, c->ctl_d, c->surf_counts,
-                    c->surf_offsets, c->surf_scratch};
+                    c->surf_offsets, c->surf_scratch, c->surf_up, c->surf_list, c->surf_cursor};
     release_graph_loop(c);
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -181,6 +222,12 @@ void free_all(denser_ctx* c) {
     if (c->h_ctl_i) cudaFreeHost(c->h_ctl_i);
     if (c->h_ctl_d) cudaFreeHost(c->h_ctl_d);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    for (int i = 0; i < 2; ++i) {
+        if (c->dstage[i]) cudaFree(c->dstage[i]);
+        if (c->dstage_copied[i]) cudaEventDestroy(c->dstage_copied[i]);
+        if (c->dstage_free[i]) cudaEventDestroy(c->dstage_free[i]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
 }
 
 }  // namespace
@@ -226,6 +273,8 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->stage = nullptr, c->stage_bytes = 0, c->hstage = nullptr, c->hstage_bytes = 0;
     c->omega_bytes = nullptr, c->conv_scratch = nullptr, c->conv_bytes = 0;
     c->surf_counts = nullptr, c->surf_offsets = nullptr, c->surf_scratch = nullptr, c->surf_bytes = 0;
+    c->surf_up = nullptr, c->surf_list = nullptr, c->surf_list_cap = 0, c->surf_cursor = nullptr;
+    c->surf_items = 0;
     c->h_counters = nullptr, c->h_energy = nullptr;
     c->launches = 0;
     c->sched.sweep_kernel = 2;
@@ -235,6 +284,12 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->order = nullptr, c->order_keys = nullptr, c->order_vals = nullptr;
     c->order_valid_blocks = -1;
     c->capture_stream = nullptr;
+    c->copy_stream = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        c->dstage[i] = nullptr, c->dstage_bytes[i] = 0;
+        c->dstage_copied[i] = nullptr, c->dstage_free[i] = nullptr;
+    }
+    c->dstage_next = 0;
     c->ctl_i = nullptr, c->ctl_d = nullptr, c->h_ctl_i = nullptr, c->h_ctl_d = nullptr;
     c->loop.valid = false;
     c->elem_size = p.precision == DENSER_FP32 ? 4 : 2;
@@ -283,7 +338,12 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
         cudaMallocHost((void**)&c->h_energy, 2 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_ctl_i, 4 * sizeof(int32_t)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_ctl_d, 4 * sizeof(double)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->dstage_copied[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->dstage_copied[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->dstage_free[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->dstage_free[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         free_all(c);
         delete c;
@@ -337,11 +397,13 @@ int denser_alloc_blocks(denser_ctx* c, const float* depth, const denser_intrinsi
         if (!depth || !valid_intrinsics(K) || !valid_pose(T_gc) || segment < 0 || segment > kMaxSegment)
             return set_error(c, DENSER_ERR_INVALID_ARG, "alloc_blocks: bad depth, intrinsics, pose or segment");
         cudaStream_t s = (cudaStream_t)stream;
-        const void* dd;
-        int rc = device_input(c, depth, (size_t)K->width * K->height * 4, s, &dd);
+        const float* dd;
+        int slot;
+        int rc = stage_depth(c, depth, (size_t)K->width * K->height * 4, s, &dd, &slot);
         if (rc) return rc;
-        rc = launch_alloc(c, (const float*)dd, K, T_gc, segment, s);
-        if (rc) return rc;
+        rc = launch_alloc(c, dd, K, T_gc, segment, s);
+        const int rr = release_depth(c, slot, s);
+        if (rc || (rc = rr)) return rc;
         if (n_new_out) {
             rc = read_counters(c, s);
             *n_new_out = c->h_counters[kLastNew];
@@ -357,10 +419,36 @@ int denser_fuse_depth(denser_ctx* c, const float* depth, const denser_intrinsics
         if (!depth || !valid_intrinsics(K) || !valid_pose(T_gc) || segment < 0 || segment > kMaxSegment)
             return set_error(c, DENSER_ERR_INVALID_ARG, "fuse_depth: bad depth, intrinsics, pose or segment");
         cudaStream_t s = (cudaStream_t)stream;
-        const void* dd;
-        int rc = device_input(c, depth, (size_t)K->width * K->height * 4, s, &dd);
+        const float* dd;
+        int slot;
+        int rc = stage_depth(c, depth, (size_t)K->width * K->height * 4, s, &dd, &slot);
         if (rc) return rc;
-        return launch_fuse(c, (const float*)dd, K, T_gc, segment, s);
+        rc = launch_fuse(c, dd, K, T_gc, segment, s);
+        const int rr = release_depth(c, slot, s);
+        return rc ? rc : rr;
+    });
+}
+
+int denser_integrate(denser_ctx* c, const float* depth, const denser_intrinsics* K, const double T_gc[16],
+                     int32_t segment, void* stream, int32_t* n_new_out) {
+    return guarded(c, [&]() -> int {
+        if (!depth || !valid_intrinsics(K) || !valid_pose(T_gc) || segment < 0 || segment > kMaxSegment)
+            return set_error(c, DENSER_ERR_INVALID_ARG, "integrate: bad depth, intrinsics, pose or segment");
+        cudaStream_t s = (cudaStream_t)stream;
+        const float* dd;
+        int slot;
+        int rc = stage_depth(c, depth, (size_t)K->width * K->height * 4, s, &dd, &slot);
+        if (rc) return rc;
+        rc = launch_alloc(c, dd, K, T_gc, segment, s);
+        if (!rc) rc = launch_fuse(c, dd, K, T_gc, segment, s);
+        const int rr = release_depth(c, slot, s);
+        if (rc || (rc = rr)) return rc;
+        if (n_new_out) {
+            rc = read_counters(c, s);
+            *n_new_out = c->h_counters[kLastNew];
+            return rc;
+        }
+        return DENSER_OK;
     });
 }
 
@@ -579,11 +667,30 @@ int denser_extract_surface(denser_ctx* c, float* tri_pos, int64_t* tri_ids, int6
             if ((rc = cuda_check(c, cudaMalloc(&c->surf_offsets, ((size_t)c->d.max_blocks + 1) * 8),
                                  "cudaMalloc(surface offsets)")))
                 return rc;
+            if ((rc = cuda_check(c, cudaMalloc(&c->surf_up, (size_t)c->d.max_blocks * 32), "cudaMalloc(surface neighbours)")))
+                return rc;
+            if ((rc = cuda_check(c, cudaMalloc(&c->surf_cursor, 8), "cudaMalloc(surface cursor)"))) return rc;
         }
-        if ((rc = launch_surface(c, nb, 0, nullptr, nullptr, 0, s))) return rc;
         long long total = 0;
-        if ((rc = copy_out(c, &total, c->surf_offsets + nb, 8, s, "read triangle count"))) return rc;
-        if ((rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize"))) return rc;
+        unsigned long long items = 0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            // first a guess of 32 listed cubes per block, then exactly what the count found
+            const long long need = attempt == 0 ? (long long)nb * 32 : (long long)items;
+            if (c->surf_list_cap < need) {
+                if (c->surf_list) cudaFree(c->surf_list);
+                c->surf_list = nullptr;
+                c->surf_list_cap = 0;
+                if ((rc = cuda_check(c, cudaMalloc(&c->surf_list, (size_t)need * 8), "cudaMalloc(surface list)")))
+                    return rc;
+                c->surf_list_cap = need;
+            }
+            if ((rc = launch_surface(c, nb, 0, nullptr, nullptr, 0, s))) return rc;
+            if ((rc = copy_out(c, &total, c->surf_offsets + nb, 8, s, "read triangle count"))) return rc;
+            if ((rc = copy_out(c, &items, c->surf_cursor, 8, s, "read cube count"))) return rc;
+            if ((rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize"))) return rc;
+            if ((long long)items <= c->surf_list_cap) break;  // else grow to the exact need and count again
+        }
+        c->surf_items = (long long)items;
         *n_tri_out = total;
         if (block_first && (rc = copy_out(c, block_first, c->surf_offsets, ((size_t)nb + 1) * 8, s, "copy block offsets")))
             return rc;

@@ -129,6 +129,14 @@ struct denser_ctx {
     int64_t nbr_valid_blocks;  // blocks covered by the neighbour table (-1: rebuild)
     float* stage;              // device staging for host inputs
     size_t stage_bytes;
+    // depth maps from host memory: two device buffers filled on copy_stream, so that a
+    // frame's copy overlaps the previous frame's kernels
+    cudaStream_t copy_stream;
+    float* dstage[2];
+    size_t dstage_bytes[2];
+    cudaEvent_t dstage_copied[2];  // recorded on copy_stream after the copy into dstage[i]
+    cudaEvent_t dstage_free[2];    // recorded on the call's stream after the kernels reading dstage[i]
+    int dstage_next;
     void* hstage;              // pinned host staging for host outputs
     size_t hstage_bytes;
     uint8_t* omega_bytes;      // extract scratch
@@ -136,6 +144,11 @@ struct denser_ctx {
     size_t conv_bytes;
     int32_t* surf_counts;      // [max_blocks] triangles per block (surface extraction)
     long long* surf_offsets;   // [max_blocks + 1] their exclusive scan
+    int32_t* surf_up;          // [max_blocks][8] upper-neighbour block indices
+    unsigned long long* surf_list;    // cubes with triangles (count pass)
+    long long surf_list_cap;
+    unsigned long long* surf_cursor;  // device: entries the count pass produced
+    long long surf_items;             // host copy of *surf_cursor
     void* surf_scratch;        // device staging of host surface outputs
     size_t surf_bytes;
     int32_t* h_counters;       // pinned copy of the device counters
@@ -221,12 +234,16 @@ __host__ __device__ inline void neighbour_offset(int i, int* dx, int* dy, int* d
     *dz = t[i][2];
 }
 
-// floor(v) for |v| < 2^22 using only an FP32 add in round-down mode and an integer
-// subtract: v + 1.5*2^23 lands in [2^23, 2^24), where the float spacing is 1, so its
-// mantissa holds floor(v).  (Conversions from float to 64-bit integers and the
-// rounding instructions run on the narrow FP64 pipe of this GPU; this does not.)
+// floor(v) for |v| < 2^22 with plain round-to-nearest FP32 arithmetic and integer
+// operations: v + 1.5*2^23 lands in [2^23, 2^24), where the float spacing is 1, so it
+// rounds to n + 1.5*2^23 with n the integer nearest v, held in its mantissa; floor(v)
+// is n, or n - 1 when n > v.  (Conversions from float to 64-bit integers, rounding
+// instructions and directed-rounding adds are avoided: this GPU runs some of them on
+// its narrow FP64 pipe.)
 __device__ inline int floor_small(float v) {
-    return __float_as_int(__fadd_rd(v, 12582912.0f)) - 0x4B400000;
+    const float t = __fadd_rn(v, 12582912.0f);
+    const int n = __float_as_int(t) - 0x4B400000;
+    return (t - 12582912.0f) > v ? n - 1 : n;
 }
 
 inline int grid_for(int sm_count, long long work, int threads, int per_sm) {

@@ -17,7 +17,9 @@
 //
 // Triangles are ordered by block index, cube (lower corner's local index), tetrahedron
 // (lexicographic pi) and triangle within the tetrahedron, so the output is
-// deterministic.  Two passes over the blocks: count (per block), exclusive scan, emit.
+// deterministic.  Passes: upper-neighbour lookup; count (per block), which also lists
+// every cube with triangles; exclusive scan of the counts; emit, one thread per listed
+// cube.
 // A vertex also gets an integer id, (flat voxel index of the lower end) * 8 + direction
 // bits, which identifies the edge it lies on: equal ids are the same vertex.
 #include "common.cuh"
@@ -45,93 +47,144 @@ __device__ __forceinline__ int tet_tris(unsigned m) {
     return k == 2 ? 2 : ((k & 1) ? 1 : 0);
 }
 
-struct Region {
-    float u[kRegion];
-    unsigned char om[kRegion];
-    int nbk[8];  // block index of each carry (bit a: the region coordinate along a is 8)
-};
-
-// Stages u and Omega on the 9^3 corner region of block b: the block itself and its
-// +x, +y, +z, +xy, +xz, +yz and +xyz neighbours' first layers.
-template <typename T>
-__device__ void load_region(const DeviceMap& m, const T* __restrict__ u, int b, Region& r) {
-    const int t = threadIdx.x;
-    if (t < 8) {
+// Block index of each upper neighbour (carry code c: +x for bit 0, +y bit 1, +z bit 2;
+// entry 0 is the block itself), -1 where unallocated: 8 int32 per block.  One thread
+// per lookup, so that the hash probes of all blocks overlap.
+__global__ void surface_nbr_kernel(DeviceMap m, int32_t* __restrict__ up) {
+    const int nb = m.counters[kNumBlocks];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)nb * 8;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i >> 3), c = (int)(i & 7);
         int nbk = b;
-        if (t > 0) {
+        if (c) {
             const int4 k = reinterpret_cast<const int4*>(m.coords)[b];
-            const long long bx = (long long)k.y + (t & 1), by = (long long)k.z + ((t >> 1) & 1),
-                            bz = (long long)k.w + ((t >> 2) & 1);
+            const long long bx = (long long)k.y + (c & 1), by = (long long)k.z + ((c >> 1) & 1),
+                            bz = (long long)k.w + ((c >> 2) & 1);
             nbk = key_in_range(k.x, bx, by, bz) ? hash_lookup(m, pack_key(k.x, (int32_t)bx, (int32_t)by, (int32_t)bz))
                                                 : -1;
             if (nbk < 0) nbk = -1;  // pending or rejected slots are not blocks
         }
-        r.nbk[t] = nbk;
+        up[i] = nbk;
     }
-    __syncthreads();
-    for (int i = t; i < kRegion; i += kSurfThreads) {
-        const int x = i % kR, y = (i / kR) % kR, z = i / (kR * kR);
-        const int carry = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
-        const int nbk = r.nbk[carry];
-        float uv = 0.0f;
-        unsigned char o = 0;
-        if (nbk >= 0) {
-            const size_t v = (size_t)nbk * kBlockVoxels + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
-            o = __ldg(m.w + v) > 0.0f;
-            uv = Store<T>::ld(u + v);
-        }
-        r.u[i] = uv;
-        r.om[i] = o;
-    }
-    __syncthreads();
 }
 
-// Negative-corner masks of the six tetrahedra of cube (lx, ly, lz), or 0 for all when
-// the cube has an unobserved corner.  Returns the cube's triangle count; fills
-// cu[8] with the corner values (corner code order).
-__device__ __forceinline__ int cube_case(const Region& r, int lx, int ly, int lz, float* cu, unsigned* neg8) {
-    bool all = true;
-    unsigned neg = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int i = ridx(lx + (c & 1), ly + ((c >> 1) & 1), lz + ((c >> 2) & 1));
-        all = all && r.om[i];
-        cu[c] = r.u[i];
-        neg |= (cu[c] < 0.0f ? 1u : 0u) << c;
-    }
-    *neg8 = neg;
-    if (!all || neg == 0 || neg == 0xffu) return 0;
-    int n = 0;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const unsigned m4 = (neg & 1u) | (((neg >> kTetC1[q]) & 1u) << 1) | (((neg >> kTetC2[q]) & 1u) << 2) |
-                            (((neg >> 7) & 1u) << 3);
-        n += tet_tris(m4);
-    }
-    return n;
+// Negative-corner mask (bit i: tetrahedron corner i) of Kuhn tetrahedron q of a cube
+// whose corner c is negative when bit c of neg8 is set.
+__device__ __forceinline__ unsigned tet_mask(unsigned neg8, int q) {
+    return (neg8 & 1u) | (((neg8 >> kTetC1[q]) & 1u) << 1) | (((neg8 >> kTetC2[q]) & 1u) << 2) |
+           (((neg8 >> 7) & 1u) << 3);
 }
 
+// Count pass.  Each thread takes four consecutive cubes along x (their 20 corners are
+// read once), finds each cube's negative-corner mask and whether all eight corners are
+// observed, and takes the cube's triangle count from a 256-entry table.  Per block:
+// counts[b] = the block's triangles; every cube with triangles is appended to `list`
+// as (block << 32 | cube << 23 | mask << 15 | first triangle within the block), in
+// cube order within the block (the blocks' chunks land in any order).  *cursor counts
+// the entries; entries beyond `cap` are not written (the host then grows the list and
+// runs the pass again).
 template <typename T>
-__global__ void __launch_bounds__(kSurfThreads) surface_count_kernel(DeviceMap m, const T* __restrict__ u,
-                                                                     int32_t* __restrict__ counts) {
-    __shared__ Region r;
-    __shared__ int red[kSurfThreads / 32];
+__global__ void __launch_bounds__(kSurfThreads, 12) surface_count_kernel(DeviceMap m, const T* __restrict__ u,
+                                                                         const int32_t* __restrict__ up,
+                                                                         int32_t* __restrict__ counts,
+                                                                         unsigned long long* __restrict__ list,
+                                                                         long long cap,
+                                                                         unsigned long long* __restrict__ cursor) {
+    __shared__ float su[kRegion];
+    __shared__ unsigned char som[kRegion];
+    __shared__ int nbk[8];
+    __shared__ unsigned char lut[256];  // triangles of a cube by its negative-corner mask
+    __shared__ int wsum[kSurfThreads / 32];
+    __shared__ unsigned long long chunk;
     const int nb = m.counters[kNumBlocks];
-    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-        load_region<T>(m, u, b, r);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int i = t; i < 256; i += kSurfThreads) {
         int n = 0;
+        if (i != 0 && i != 255)
+            for (int q = 0; q < 6; ++q) n += tet_tris(tet_mask((unsigned)i, q));
+        lut[i] = (unsigned char)n;
+    }
+    const int lx0 = (4 * t) & 7, ly = ((4 * t) >> 3) & 7, lz = (4 * t) >> 6;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        if (t < 8) nbk[t] = __ldg(up + 8 * (size_t)b + t);
+        __syncthreads();
+        for (int i = t; i < kRegion; i += kSurfThreads) {
+            const int x = i % kR, y = (i / kR) % kR, z = i / (kR * kR);
+            const int nk = nbk[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
+            float uv = 0.0f;
+            unsigned char o = 0;
+            if (nk >= 0) {
+                const size_t v = (size_t)nk * kBlockVoxels + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+                o = __ldg(m.w + v) > 0.0f;
+                uv = Store<T>::ld(u + v);
+            }
+            su[i] = uv;
+            som[i] = o;
+        }
+        __syncthreads();
+        // rows (y, z), (y+1, z), (y, z+1), (y+1, z+1) of x = lx0 .. lx0 + 4: 5-bit masks
+        unsigned negr[4], omr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int base = ridx(lx0, ly + (r & 1), lz + (r >> 1));
+            unsigned nm = 0, om = 0;
+#pragma unroll
+            for (int x = 0; x < 5; ++x) {
+                nm |= (su[base + x] < 0.0f ? 1u : 0u) << x;
+                om |= (som[base + x] ? 1u : 0u) << x;
+            }
+            negr[r] = nm;
+            omr[r] = om;
+        }
+        unsigned neg8[4];
+        int cnt[4], n = 0, items = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int l = 4 * threadIdx.x + q;
-            float cu[8];
-            unsigned neg;
-            n += cube_case(r, l & 7, (l >> 3) & 7, l >> 6, cu, &neg);
+            // corner c = (x bit, y bit, z bit): row r = c >> 1, x offset c & 1
+            unsigned ng = 0, ob = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                ng |= ((negr[r] >> q) & 3u) << (2 * r);
+                ob |= ((omr[r] >> q) & 3u) << (2 * r);
+            }
+            neg8[q] = ng;
+            cnt[q] = ob == 0xffu ? lut[ng] : 0;
+            n += cnt[q];
+            items += cnt[q] ? 1 : 0;
         }
-        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n;
+        // exclusive scan of (cubes listed, triangles) in thread (= cube) order, packed
+        const int packed = (items << 16) | n;
+        int inc = packed;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) wsum[warp] = inc;
         __syncthreads();
-        if (threadIdx.x == 0) counts[b] = red[0] + red[1] + red[2] + red[3];
-        __syncthreads();  // r and red are rewritten by the next block
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kSurfThreads / 32; ++w) {
+            before += w < warp ? wsum[w] : 0;
+            total += wsum[w];
+        }
+        if (t == 0) {
+            counts[b] = total & 0xffff;
+            chunk = (total >> 16) ? atomicAdd(cursor, (unsigned long long)(total >> 16)) : 0ull;
+        }
+        __syncthreads();
+        const int ex = before + inc - packed;
+        long long slot = (long long)chunk + (ex >> 16);
+        int tri = ex & 0xffff;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!cnt[q]) continue;
+            if (slot < cap)
+                list[slot] = ((unsigned long long)(unsigned)b << 32) | ((unsigned long long)(4 * t + q) << 23) |
+                             ((unsigned long long)neg8[q] << 15) | (unsigned long long)tri;
+            ++slot;
+            tri += cnt[q];
+        }
+        __syncthreads();  // shared state is rewritten by the next block
     }
 }
 
@@ -163,117 +216,106 @@ __global__ void __launch_bounds__(1024) surface_scan_kernel(const DeviceMap m, c
     if (t == 1023) offsets[nb] = part[1023];
 }
 
-// Vertex on the edge from tetrahedron corner code ca (lower) to cb of cube (lx, ly, lz).
-__device__ __forceinline__ void emit_vertex(const Region& r, int4 key, float s, int lx, int ly, int lz, int ca, int cb,
-                                            float ua, float ub, float* pos, long long* id) {
-    const int ox = lx + (ca & 1), oy = ly + ((ca >> 1) & 1), oz = lz + ((ca >> 2) & 1);
-    const int dir = ca ^ cb;
-    const float t = ua / (ua - ub);
-    pos[0] = ((float)(8 * key.y + ox) + 0.5f + ((dir & 1) ? t : 0.0f)) * s;
-    pos[1] = ((float)(8 * key.z + oy) + 0.5f + ((dir & 2) ? t : 0.0f)) * s;
-    pos[2] = ((float)(8 * key.w + oz) + 0.5f + ((dir & 4) ? t : 0.0f)) * s;
-    const int carry = (ox >> 3) | ((oy >> 3) << 1) | ((oz >> 3) << 2);
-    const long long flat = (long long)r.nbk[carry] * kBlockVoxels + (ox & 7) + 8 * (oy & 7) + 64 * (oz & 7);
-    *id = flat * 8 + dir;
+// The edges (i, j), i < j, of the triangles of a tetrahedron with negative-corner mask
+// m4 and orientation sign sg, wound so that (v1 - v0) x (v2 - v0) points to the
+// non-negative side; returns the triangle count.
+__device__ __forceinline__ int tet_edges(unsigned m4, int sg, int e[2][3][2]) {
+    const int k = __popc(m4);
+    if (k & 1) {
+        const int lone = __ffs(k == 1 ? m4 : (~m4 & 15u)) - 1;
+        // the other three in the order of an even permutation that puts the lone corner
+        // first: on a positively oriented tetrahedron the triangle's normal then points
+        // away from it
+        const int o0 = lone == 0 ? 1 : (lone == 1 ? 0 : (lone == 2 ? 3 : 2));
+        const int o1 = lone == 0 ? 2 : (lone == 1 ? 3 : (lone == 2 ? 0 : 1));
+        const int o2 = lone == 0 ? 3 : (lone == 1 ? 2 : (lone == 2 ? 1 : 0));
+        const bool flip = (sg > 0) != (k == 1);
+        const int oo[3] = {o0, flip ? o2 : o1, flip ? o1 : o2};
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            e[0][v][0] = min(lone, oo[v]);
+            e[0][v][1] = max(lone, oo[v]);
+        }
+        return 1;
+    }
+    const int A = __ffs(m4) - 1, B = 31 - __clz(m4);
+    const unsigned pm = ~m4 & 15u;
+    const int C = __ffs(pm) - 1, D = 31 - __clz(pm);
+    // parity of (A, B, C, D) as a permutation of (0, 1, 2, 3): odd exactly for the
+    // negative pairs {0, 2} and {1, 3}
+    const int par = (m4 == 5u || m4 == 10u) ? -1 : 1;
+    const bool flip = sg * par < 0;
+    const int t0[3][2] = {{A, C}, {A, D}, {B, D}};
+    const int t1[3][2] = {{A, C}, {B, D}, {B, C}};
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const int vv = flip ? (v == 0 ? 0 : 3 - v) : v;
+        e[0][v][0] = min(t0[vv][0], t0[vv][1]);
+        e[0][v][1] = max(t0[vv][0], t0[vv][1]);
+        e[1][v][0] = min(t1[vv][0], t1[vv][1]);
+        e[1][v][1] = max(t1[vv][0], t1[vv][1]);
+    }
+    return 2;
 }
 
+// Emit pass: one thread per listed cube.  It reads the cube's eight corner values
+// (from the block and its upper neighbours), and writes the triangles of its six
+// tetrahedra from the block's first triangle plus the cube's offset.
 template <typename T>
-__global__ void __launch_bounds__(kSurfThreads) surface_emit_kernel(DeviceMap m, const T* __restrict__ u,
-                                                                    const long long* __restrict__ offsets, float s,
-                                                                    long long capacity, float* __restrict__ tri_pos,
-                                                                    long long* __restrict__ tri_ids) {
-    __shared__ Region r;
-    __shared__ int wsum[kSurfThreads / 32];
-    const int nb = m.counters[kNumBlocks];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-        load_region<T>(m, u, b, r);
+__global__ void __launch_bounds__(64) surface_emit_kernel(DeviceMap m, const T* __restrict__ u,
+                                                           const int32_t* __restrict__ up,
+                                                           const unsigned long long* __restrict__ list,
+                                                           long long n_items, const long long* __restrict__ offsets,
+                                                           float s, long long capacity, float* __restrict__ tri_pos,
+                                                           long long* __restrict__ tri_ids) {
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < n_items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long w = list[it];
+        const int b = (int)(w >> 32);
+        const int l = (int)((w >> 23) & 511u);
+        const unsigned neg8 = (unsigned)((w >> 15) & 255u);
+        long long out = offsets[b] + (long long)(w & 32767u);
+        const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
         const int4 key = reinterpret_cast<const int4*>(m.coords)[b];
-        int cnt[4];
-        int n = 0;
+        const int4 u0 = __ldg(reinterpret_cast<const int4*>(up) + 2 * (size_t)b);
+        const int4 u1 = __ldg(reinterpret_cast<const int4*>(up) + 2 * (size_t)b + 1);
+        const int nbk[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        float cu[8];
+        long long flat[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int l = 4 * threadIdx.x + q;
-            float cu[8];
-            unsigned neg;
-            cnt[q] = cube_case(r, l & 7, (l >> 3) & 7, l >> 6, cu, &neg);
-            n += cnt[q];
+        for (int c = 0; c < 8; ++c) {
+            const int ox = lx + (c & 1), oy = ly + ((c >> 1) & 1), oz = lz + ((c >> 2) & 1);
+            flat[c] = (long long)nbk[(ox >> 3) | ((oy >> 3) << 1) | ((oz >> 3) << 2)] * kBlockVoxels + (ox & 7) +
+                      8 * (oy & 7) + 64 * (oz & 7);
+            cu[c] = Store<T>::ld(u + flat[c]);
         }
-        // exclusive scan of the per-thread counts in thread (= cube) order
-        int inc = n;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += v;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        int base = 0;
-        for (int w = 0; w < warp; ++w) base += wsum[w];
-        long long out = offsets[b] + base + inc - n;
+        const float gx = (float)(8 * key.y + lx) + 0.5f, gy = (float)(8 * key.z + ly) + 0.5f,
+                    gz = (float)(8 * key.w + lz) + 0.5f;
 #pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-            if (cnt[q] == 0) continue;
-            const int l = 4 * threadIdx.x + q;
-            const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-            float cu[8];
-            unsigned neg;
-            cube_case(r, lx, ly, lz, cu, &neg);
-#pragma unroll 1
-            for (int q6 = 0; q6 < 6; ++q6) {
-                const int code[4] = {0, kTetC1[q6], kTetC2[q6], 7};
-                unsigned m4 = 0;
+        for (int q = 0; q < 6; ++q) {
+            const unsigned m4 = tet_mask(neg8, q);
+            const int k = __popc(m4);
+            if (k == 0 || k == 4) continue;
+            const int code[4] = {0, kTetC1[q], kTetC2[q], 7};
+            int e[2][3][2];
+            const int ntri = tet_edges(m4, kTetSign[q], e);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) m4 |= ((neg >> code[i]) & 1u) << i;
-                const int k = __popc(m4);
-                if (k == 0 || k == 4) continue;
-                // edges (i, j), i < j, of the (up to) two triangles, wound per the header
-                int e[2][3][2];
-                int ntri;
-                if (k & 1) {
-                    const int lone = __ffs(k == 1 ? m4 : (~m4 & 15u)) - 1;
-                    // the other three in the order of an even permutation that puts the
-                    // lone corner first: the triangle's normal then points away from it on a
-                    // positively oriented tetrahedron
-                    const int o0 = lone == 0 ? 1 : (lone == 1 ? 0 : (lone == 2 ? 3 : 2));
-                    const int o1 = lone == 0 ? 2 : (lone == 1 ? 3 : (lone == 2 ? 0 : 1));
-                    const int o2 = lone == 0 ? 3 : (lone == 1 ? 2 : (lone == 2 ? 1 : 0));
-                    const bool flip = (kTetSign[q6] > 0) != (k == 1);
-                    const int oo[3] = {o0, flip ? o2 : o1, flip ? o1 : o2};
-#pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        e[0][v][0] = min(lone, oo[v]);
-                        e[0][v][1] = max(lone, oo[v]);
-                    }
-                    ntri = 1;
-                } else {
-                    const int A = __ffs(m4) - 1, B = 31 - __clz(m4);
-                    const unsigned pm = ~m4 & 15u;
-                    const int C = __ffs(pm) - 1, D = 31 - __clz(pm);
-                    // parity of (A, B, C, D) as a permutation of (0, 1, 2, 3): odd exactly
-                    // for the negative pairs {0, 2} and {1, 3}
-                    const int par = (m4 == 5u || m4 == 10u) ? -1 : 1;
-                    const bool flip = kTetSign[q6] * par < 0;
-                    const int t0[3][2] = {{A, C}, {A, D}, {B, D}};
-                    const int t1[3][2] = {{A, C}, {B, D}, {B, C}};
-#pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        const int vv = flip ? (v == 0 ? 0 : 3 - v) : v;
-                        e[0][v][0] = min(t0[vv][0], t0[vv][1]);
-                        e[0][v][1] = max(t0[vv][0], t0[vv][1]);
-                        e[1][v][0] = min(t1[vv][0], t1[vv][1]);
-                        e[1][v][1] = max(t1[vv][0], t1[vv][1]);
-                    }
-                    ntri = 2;
-                }
-                for (int tr = 0; tr < ntri; ++tr, ++out) {
-                    if (out >= capacity) continue;
+            for (int tr = 0; tr < 2; ++tr) {
+                if (tr >= ntri) continue;
+                if (out < capacity) {
                     float pos[9];
                     long long id[3];
 #pragma unroll
                     for (int v = 0; v < 3; ++v) {
-                        const int i = e[tr][v][0], j = e[tr][v][1];
-                        emit_vertex(r, key, s, lx, ly, lz, code[i], code[j], cu[code[i]], cu[code[j]], pos + 3 * v,
-                                    id + v);
+                        // the vertex on the edge from corner ca (the lower end) to cb
+                        const int ca = code[e[tr][v][0]], cb = code[e[tr][v][1]];
+                        const int dir = ca ^ cb;
+                        const float ua = cu[ca], ub = cu[cb];
+                        const float tt = ua / (ua - ub);
+                        pos[3 * v + 0] = (gx + (float)(ca & 1) + ((dir & 1) ? tt : 0.0f)) * s;
+                        pos[3 * v + 1] = (gy + (float)((ca >> 1) & 1) + ((dir & 2) ? tt : 0.0f)) * s;
+                        pos[3 * v + 2] = (gz + (float)((ca >> 2) & 1) + ((dir & 4) ? tt : 0.0f)) * s;
+                        id[v] = flat[ca] * 8 + dir;
                     }
                     if (tri_pos) {
                         float* dst = tri_pos + out * 9;
@@ -285,32 +327,41 @@ __global__ void __launch_bounds__(kSurfThreads) surface_emit_kernel(DeviceMap m,
                         dst[0] = id[0], dst[1] = id[1], dst[2] = id[2];
                     }
                 }
+                ++out;
             }
         }
-        __syncthreads();  // r and wsum are rewritten by the next block
     }
 }
 
 template <typename T>
 int surface_launch(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long long* tri_ids, int64_t capacity,
                    cudaStream_t s) {
-    const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * 8);
     if (pass == 0) {
-        surface_count_kernel<T><<<grid, kSurfThreads, 0, s>>>(c->d, (const T*)c->d.u, c->surf_counts);
+        surface_nbr_kernel<<<grid_for(c->sm_count, nb * 8, 256, 8), 256, 0, s>>>(c->d, c->surf_up);
+        const int grid = (int)std::min<int64_t>(nb, (int64_t)c->sm_count * 12);
+        cudaMemsetAsync(c->surf_cursor, 0, sizeof(unsigned long long), s);
+        surface_count_kernel<T><<<grid, kSurfThreads, 0, s>>>(c->d, (const T*)c->d.u, c->surf_up, c->surf_counts,
+                                                              c->surf_list, c->surf_list_cap, c->surf_cursor);
         surface_scan_kernel<<<1, 1024, 0, s>>>(c->d, c->surf_counts, c->surf_offsets);
-        c->launches += 2;
+        c->launches += 3;
     } else {
-        surface_emit_kernel<T><<<grid, kSurfThreads, 0, s>>>(c->d, (const T*)c->d.u, c->surf_offsets,
-                                                             (float)c->prm.voxel_size, capacity, tri_pos, tri_ids);
-        c->launches += 1;
+        const long long n_items = c->surf_items;
+        if (n_items > 0) {
+            // small CTAs: a few tens of thousands of listed cubes still spread over every SM
+            surface_emit_kernel<T><<<grid_for(c->sm_count, n_items, 64, 16), 64, 0, s>>>(
+                c->d, (const T*)c->d.u, c->surf_up, c->surf_list, n_items, c->surf_offsets, (float)c->prm.voxel_size,
+                capacity, tri_pos, tri_ids);
+            c->launches += 1;
+        }
     }
     return cuda_check(c, cudaGetLastError(), "surface kernel");
 }
 
 }  // namespace
 
-// pass 0: count per block and scan into c->surf_offsets (offsets[nb] = total);
-// pass 1: write the first `capacity` triangles.
+// pass 0: neighbour rows, counts per block, the list of cubes with triangles, and the
+// scan into c->surf_offsets (offsets[nb] = total, *c->surf_cursor = listed cubes);
+// pass 1: write the first `capacity` triangles of the c->surf_items listed cubes.
 int launch_surface(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long long* tri_ids, int64_t capacity,
                    cudaStream_t s) {
     if (nb <= 0) return DENSER_OK;

@@ -321,3 +321,64 @@ def test_schedule_rejects_bad_fields():
             N.denser_set_schedule(m.ctx, 1, 0, 9)
         with pytest.raises(N.DenserError):
             N.denser_set_schedule(m.ctx, 1, 0, 0, 2)
+
+
+def test_integrate_matches_alloc_then_fuse(tiny):
+    """denser_integrate (one staging of the depth map) leaves the same map as
+    alloc + fuse, for device inputs and for pinned and pageable host inputs (the
+    latter through the two copy-stream staging buffers, several frames in flight)."""
+    sc, depths = tiny
+    cam = sc.camera
+    K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    ref, _, _ = run_gpu(sc, depths, 0)
+    want = ref.snapshot()
+    ref.close()
+    for kind in ("device", "pinned", "pageable"):
+        m = N.DenserMap()
+        news = []
+        for k in range(len(depths)):
+            d = torch.from_numpy(np.ascontiguousarray(depths[k]))
+            d = d.cuda() if kind == "device" else (d.pin_memory() if kind == "pinned" else d)
+            news.append(N.denser_integrate(m.ctx, d, K, sc.poses[k], 0, count=(k == len(depths) - 1)))
+        got = m.snapshot()
+        for key in ("coords", "f", "w", "u"):
+            np.testing.assert_array_equal(got[key], want[key], err_msg=f"{kind} {key}")
+        m.close()
+
+
+def test_twenty_centimetre_configuration():
+    """Table I's 20 cm column: s = 0.2 m, lambda = 0.4, mu = 1.6 m (33 band samples per ray)."""
+    sc = tiny_scene(seed=0)
+    d = sc.depth_maps()
+    prm = O.Params(voxel_size=0.2, mu=1.6, lam=0.4)
+    g, news_o, _ = run_oracle(sc, d, 50, params=prm)
+    m, news_g, st = run_gpu(sc, d, 50, voxel_size=0.2, mu=1.6, **{"lambda": 0.4})
+    snap = m.snapshot(dual=True)
+    m.close()
+    assert news_g == news_o and st.iters == 50
+    np.testing.assert_array_equal(snap["coords"], oracle_coords(g))
+    np.testing.assert_array_equal(snap["w"], g.w.astype(np.float32))
+    assert np.max(np.abs(snap["f"] - g.f)) <= TOL
+    assert np.max(np.abs(snap["u"] - g.u)) <= TOL
+    assert np.max(np.abs(snap["p"] - g.p)) <= TOL
+
+
+def test_checkpoint_and_restore_continue_bit_identically(tiny):
+    """Save/restore of the block state: extract everything after 30 iterations, load it
+    into a fresh context (same block order), run 20 more; the iterates equal 50
+    uninterrupted iterations bit for bit."""
+    sc, d = tiny
+    m50, _, _ = run_gpu(sc, d, 50)
+    want = m50.snapshot(dual=True)
+    m50.close()
+    m30, _, _ = run_gpu(sc, d, 30)
+    s30 = m30.snapshot(dual=True)
+    m30.close()
+    nb = len(s30["coords"])
+    with N.DenserMap() as m:
+        N.denser_load_blocks(m.ctx, s30["coords"], s30["f"], s30["w"])
+        N.denser_load_state(m.ctx, s30["u"], s30["u_bar"], s30["p"], nb)
+        N.denser_regularize(m.ctx, 20, 0.0, 1)
+        got = m.snapshot(dual=True)
+    for key in ("coords", "f", "w", "u", "u_bar", "p"):
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
