@@ -44,6 +44,20 @@ class Camera:
                       height / 2.0 + PP_OFFSET[1], int(width), int(height))
 
 
+@dataclass(frozen=True)
+class Lidar:
+    """A spinning multi-beam laser: ``beams`` elevations evenly spaced in
+    [el_lo, el_hi] degrees (up positive), ``azimuths`` rays per turn.  The default is
+    shaped like the 64-beam scanner of the paper's driving sequences."""
+    beams: int = 64
+    azimuths: int = 2000
+    el_lo: float = -24.9
+    el_hi: float = 2.0
+    r_max: float = 40.0
+    noise: float = 0.02
+    invalid_prob: float = 0.05
+
+
 @dataclass
 class Box:
     lo: np.ndarray
@@ -128,6 +142,36 @@ class Scene:
         out = np.where(valid, d, 0.0).astype(np.float32)
         return out
 
+    # ---------------------------------------------------------------- laser
+    def lidar_scan(self, frame: int, lidar: "Lidar") -> np.ndarray:
+        """Points [n, 3] float32 in the sensor frame (the camera frame of pose ``frame``:
+        x right, y down, z forward) of one spinning-lidar sweep: ``lidar.beams``
+        elevations x ``lidar.azimuths`` azimuths, every ray cast from the pose's origin.
+        A ray with no hit within ``lidar.r_max``, or dropped (``lidar.invalid_prob``),
+        gives a NaN point.  Range noise N(0, lidar.noise) from PCG64([seed, 2, frame])."""
+        T = self.poses[frame]
+        R, o = T[:3, :3], T[:3, 3]
+        el = np.linspace(lidar.el_lo, lidar.el_hi, lidar.beams) * (np.pi / 180.0)
+        az = (np.arange(lidar.azimuths) + 0.5) * (2.0 * np.pi / lidar.azimuths)
+        E, A = np.meshgrid(el, az, indexing="ij")
+        # unit directions in the sensor frame: elevation up is -y
+        ds = np.stack([np.cos(E) * np.sin(A), -np.sin(E), np.cos(E) * np.cos(A)], axis=0)
+        D = np.einsum("ij,jhw->ihw", R, ds)
+        best = np.full(D.shape[1:], np.inf)
+        for r in self.rects:
+            _hit_rect(best, o, D, r)
+        for b in self.boxes:
+            _hit_box(best, o, D, b, None, T)
+        for f in self.facades:
+            _hit_facade(best, o, D, f)
+        rng = np.random.Generator(np.random.PCG64([self.seed, 2, frame]))
+        rng_noise = rng.standard_normal(best.shape) * lidar.noise
+        drop = rng.random(best.shape) < lidar.invalid_prob
+        valid = (best <= lidar.r_max) & ~drop
+        rho = np.where(valid, best + rng_noise, np.nan)
+        pts = (ds * rho[None]).reshape(3, -1).T
+        return pts.astype(np.float32)
+
     def depth_maps(self, frames=None) -> np.ndarray:
         """Depth maps [n, H, W] float32; frame k draws its noise from PCG64([seed, 1, k])."""
         n = len(self.poses)
@@ -177,8 +221,8 @@ def _box_pixel_window(b: Box, cam: Camera, T: np.ndarray):
     return (y0, y1, x0, x1)
 
 
-def _hit_box(best, o, D, b: Box, cam: Camera, T: np.ndarray):
-    win = _box_pixel_window(b, cam, T)
+def _hit_box(best, o, D, b: Box, cam, T: np.ndarray):
+    win = _box_pixel_window(b, cam, T) if cam is not None else None
     if win is None:
         sl = (slice(None), slice(None))
     else:
