@@ -174,6 +174,32 @@ int denser_fuse_depth(denser_ctx* ctx, const float* depth, const denser_intrinsi
 int denser_integrate(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
                      const double T_gc[16], int32_t segment, void* stream, int32_t* n_new_out);
 
+/* ------------------------------------------------------------------ laser scans
+ * The projective update extends to laser sensors by updating only the voxels along
+ * each ray, from the sensor to mu behind the observed surface (Section III-A, after
+ * Eq. 1).  points: float32 [n_points][3] in the sensor frame (host or device memory);
+ * T_gs: 16 float64 (host), sensor -> global, rotation R and origin t.  A point is valid
+ * when finite, at range r = |p| > 0 and with floor((r + mu) / (s/2)) < 2^22; others are
+ * skipped.  Ray direction dg = R p / r, every float64 step in the oracle's order.
+ *
+ * denser_alloc_points: blocks holding a band sample at range r + n s/2, n = -N..N,
+ *   N = ceil(mu / (s/2)), range > 0, are allocated (the rule of denser_alloc_blocks along
+ *   the ray); new blocks are appended in ascending (segment, bz, by, bx) order.
+ * denser_fuse_points: every voxel of an allocated block of `segment` holding a ray sample
+ *   at range n s/2, n = 0..floor((r + mu)/(s/2)), counts once per ray; it observes
+ *   u_SDF = r - (c - t) . dg (c its centre) when u_SDF >= -mu.  The scan updates each
+ *   voxel once: w += n_obs, f = (w_old f_old + sum min(1, u_SDF/mu)) / w, the sum in
+ *   fixed point (multiples of 2^-30), so that the result does not depend on ray order.
+ *   Block sets and w are bit-exact with the oracle; f carries float32 rounding.
+ * denser_integrate_points: both, with one staging of host points.
+ * n_new_out (host, may be NULL): new blocks; when non-NULL the call waits. */
+int denser_alloc_points(denser_ctx* ctx, const float* points, int64_t n_points, const double T_gs[16],
+                        int32_t segment, void* stream, int32_t* n_new_out);
+int denser_fuse_points(denser_ctx* ctx, const float* points, int64_t n_points, const double T_gs[16],
+                       int32_t segment, void* stream);
+int denser_integrate_points(denser_ctx* ctx, const float* points, int64_t n_points, const double T_gs[16],
+                            int32_t segment, void* stream, int32_t* n_new_out);
+
 /* Regularisation (Section III-B/C): Chambolle-Pock iterations on the Omega-aware
  * TV-L2 energy over the allocated blocks, Omega = {w > 0}:
  *   p <- P(p + sigma grad_Omega u_bar),  P(q) = q / max(1, |q|_2)      (Eq. 3)

@@ -7,8 +7,9 @@ more detail; the readings taken here:
 
   L1  a scan is a set of points p in the sensor frame (float32) with a sensor->global
       pose T (float64, rotation R, origin t); a point is valid when finite with range
-      r = |p| > 0.  Its ray has the unit direction d = p / r, dg = R d in the global
-      frame, and starts at t;
+      r = |p| > 0 and M = floor((r + mu)/h) < 2^22 (a range limit of about 200 km at
+      10 cm voxels that keeps every ray's walk bounded).  Its ray has the unit
+      direction d = p / r, dg = R d in the global frame, and starts at t;
   L2  allocation follows reading R1 along the ray: a block is allocated when it holds
       a band sample at range rho = r + n h, n = -N..N, rho > 0 (h = s/2,
       N = ceil(mu/h)), at g = dg rho + t;
@@ -46,7 +47,7 @@ from .denser_oracle import BLOCK, BLOCK_VOXELS, SparseGrid, band_samples
 FIX = 2.0 ** 30  # fixed-point scale of the per-scan sums (L5)
 
 
-def ray_setup(points, T):
+def ray_setup(points, T, params=None):
     """(valid [n], r [n], dg [n, 3], t [3]) of a scan (L1), float64 in the stated order."""
     P = np.asarray(points, dtype=np.float32).astype(np.float64).reshape(-1, 3)
     T = np.asarray(T, dtype=np.float64)
@@ -55,6 +56,8 @@ def ray_setup(points, T):
     with np.errstate(invalid="ignore", divide="ignore"):
         r = np.sqrt((x * x + y * y) + z * z)
         valid = np.isfinite(r) & (r > 0)
+        if params is not None:
+            valid &= np.floor((r + params.mu) / (0.5 * params.voxel_size)) < 2.0 ** 22
         d = np.stack([x / r, y / r, z / r], axis=1)
     dg = np.stack([(R[i, 0] * d[:, 0] + R[i, 1] * d[:, 1]) + R[i, 2] * d[:, 2] for i in range(3)], axis=1)
     return valid, r, dg, t
@@ -66,7 +69,7 @@ def scan_block_keys(points, T, params, segment: int = 0) -> set:
     h = 0.5 * s
     bs = 8.0 * s
     N = band_samples(params)
-    valid, r, dg, t = ray_setup(points, T)
+    valid, r, dg, t = ray_setup(points, T, params)
     r, dg = r[valid], dg[valid]
     keys = set()
     for n in range(-N, N + 1):
@@ -103,7 +106,7 @@ def scan_observations(grid: SparseGrid, points, T, segment: int = 0):
     """All (flat voxel index, u_TSDF) observations of a scan (L3, L4), ray by ray."""
     p = grid.params
     s = p.voxel_size
-    valid, r, dg, t = ray_setup(points, T)
+    valid, r, dg, t = ray_setup(points, T, p)
     flat_all, u_all = [], []
     for i in np.nonzero(valid)[0]:
         v = ray_voxels(r[i], dg[i], t, p)

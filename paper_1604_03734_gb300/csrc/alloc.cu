@@ -224,6 +224,114 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
     if (range_err) report(m.counters, kErrRange);
 }
 
+struct LaserAllocArgs {
+    double R[9], t[3];
+    double h, bs;   // sample spacing s/2, block size 8 s
+    double mu;
+    int Ti[3];      // floor(t / bs)
+    float tf[3];    // t / bs - Ti, in [0, 1)
+    float hf, ibs;  // h, 1/bs as float32
+    int N, seg;
+    long long n;    // points
+};
+
+// Band-sample keys of a laser point (allocation along the ray): samples at range
+// rho = r + n h, n = -N..N, rho > 0, key = floor((dg rho + t) / bs) per axis.  The ray
+// (r, dg) is set up in float64 in the oracle's order; each sample is evaluated in
+// float32 relative to floor(t / bs), q = tf + rho Dg with Dg = dg / bs, and certified
+// with one bound per ray and axis,
+//   |q - q_real| <= 2^-24 (5 rho_max |Dg| + |q| + 1)   (rounding of dg, 1/bs, the product,
+//                                                         r, h, rho, the fma and tf)
+//   e = 2^-20 rho_max |Dg| + 2^-21 (q_max + 1)         (at least 3 times that),
+// and rho itself against 0 with 2^-22 rho_max (twice its error); otherwise the float64
+// path decides.
+__global__ void __launch_bounds__(256) laser_keys_kernel(const float* __restrict__ pts, LaserAllocArgs a, DeviceMap m) {
+    const int lane = threadIdx.x & 31;
+    const float eps20 = 9.53674316e-7f, eps21 = 4.76837158e-7f, eps22 = 2.38418579e-7f;
+    bool range_err = false;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < a.n; base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        double r = 0.0, dg[3] = {0.0, 0.0, 0.0};
+        bool valid = i < a.n && laser_ray(a.R, __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2),
+                                          &r, dg);
+        // the range limit of fusion: M = floor((r + mu) / h) < 2^22
+        valid = valid && floor(__ddiv_rn(__dadd_rn(r, a.mu), a.h)) < 4194304.0;
+        float Dg[3] = {0.0f, 0.0f, 0.0f}, e[3] = {0.0f, 0.0f, 0.0f};
+        float rf = 0.0f, erho = 0.0f;
+        bool fast = false;
+        if (valid) {
+            rf = (float)r;
+            const float rmax = rf + (float)a.N * a.hf;
+            erho = eps22 * rmax + 1e-30f;
+            fast = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Dg[k] = (float)dg[k] * a.ibs;
+                const float qm = fmaxf(fabsf(fmaf(fmaxf(rf - (float)a.N * a.hf, 0.0f), Dg[k], a.tf[k])),
+                                       fabsf(fmaf(rmax, Dg[k], a.tf[k])));
+                fast = fast && qm < 2097152.0f;
+                e[k] = fmaf(eps20, rmax * fabsf(Dg[k]), eps21 * (qm + 1.0f));
+            }
+        }
+        RayKeys rk;
+        unsigned long long last = kEmptyKey;
+        float nf = (float)(-a.N);
+        for (int n = -a.N; valid && n <= a.N; ++n, nf += 1.0f) {
+            unsigned long long key = kEmptyKey;
+            bool decided = false;
+            if (fast) {
+                const float rho = fmaf(nf, a.hf, rf);
+                if (rho < -erho) continue;  // behind the sensor for certain
+                if (rho > erho) {
+                    bool ok = true;
+                    int kk[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float q = fmaf(rho, Dg[k], a.tf[k]);
+                        const float tq = __fadd_rn(q, 12582912.0f);
+                        const float nq = tq - 12582912.0f;
+                        const bool down = nq > q;
+                        const float fr = q - (down ? nq - 1.0f : nq);
+                        ok = ok && fr >= e[k] && 1.0f - fr > e[k];
+                        kk[k] = __float_as_int(tq) - 0x4B400000 - (down ? 1 : 0);
+                    }
+                    if (ok) {
+                        const int b0 = a.Ti[0] + kk[0], b1 = a.Ti[1] + kk[1], b2 = a.Ti[2] + kk[2];
+                        if (!key_in_range(a.seg, b0, b1, b2)) {
+                            range_err = true;
+                            continue;
+                        }
+                        key = pack_key(a.seg, b0, b1, b2);
+                        decided = true;
+                    }
+                }
+            }
+            if (!decided) {
+                const double rho = __dadd_rn(r, __dmul_rn((double)n, a.h));
+                if (!(rho > 0.0)) continue;
+                double kb[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) kb[k] = floor(__ddiv_rn(__dadd_rn(__dmul_rn(dg[k], rho), a.t[k]), a.bs));
+                if (!(kb[0] >= -kCoordBias && kb[0] < kCoordBias && kb[1] >= -kCoordBias && kb[1] < kCoordBias &&
+                      kb[2] >= -kCoordBias && kb[2] < kCoordBias)) {
+                    range_err = true;
+                    continue;
+                }
+                key = pack_key(a.seg, (int32_t)kb[0], (int32_t)kb[1], (int32_t)kb[2]);
+            }
+            if (key == last) continue;
+            last = key;
+            if (rk.count == 4) {
+                hash_insert(m, rk.k0), hash_insert(m, rk.k1), hash_insert(m, rk.k2), hash_insert(m, rk.k3);
+                rk.count = 0;
+            }
+            rk.push(key);
+        }
+        warp_insert(m, rk, lane);
+    }
+    if (range_err) report(m.counters, kErrRange);
+}
+
 // Sorts (key, val) pairs in place in chunks of kSortChunk (bitonic network in shared
 // memory over the next power of two >= the chunk's count).  *count may exceed
 // capacity; only the first `capacity` pairs exist.
@@ -403,6 +511,8 @@ ZeroRegions all_regions(denser_ctx* c, int* nreg) {
 
 }  // namespace
 
+int finish_alloc(denser_ctx* c, cudaStream_t s);
+
 int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, const double* T, int32_t segment,
                  cudaStream_t s) {
     AllocArgs a;
@@ -432,6 +542,13 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
     a.seg = segment;
     const int npix = a.W * a.H;
     alloc_keys_kernel<<<grid_for(c->sm_count, npix, 256, 8), 256, 0, s>>>(depth, a, c->d);
+    c->launches += 1;
+    return finish_alloc(c, s);
+}
+
+// The inserted keys of one allocation call become blocks: sorted (chunks, then ranks
+// across chunks), zeroed, counted.
+int finish_alloc(denser_ctx* c, cudaStream_t s) {
     const int chunks = (int)((c->d.max_new + kSortChunk - 1) / kSortChunk);
     sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->d.new_keys, c->d.new_slots, c->d.counters + kNumNew,
                                                (int)c->d.max_new);
@@ -440,10 +557,36 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
     ZeroRegions z = all_regions(c, &nreg);
     zero_blocks_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d, z, nreg, 1, 0, 0);
     commit_kernel<<<1, 1, 0, s>>>(c->d);
-    c->launches += 5;
+    c->launches += 4;
     c->nbr_valid_blocks = -1;
     c->order_valid_blocks = -1;
     return cuda_check(c, cudaGetLastError(), "allocation kernels");
+}
+
+int launch_alloc_points(denser_ctx* c, const float* pts, int64_t n, const double* T, int32_t segment,
+                        cudaStream_t s) {
+    LaserAllocArgs a;
+    a.h = 0.5 * c->prm.voxel_size;
+    a.bs = 8.0 * c->prm.voxel_size;
+    for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) a.R[3 * r + q] = T[4 * r + q];
+        a.t[r] = T[4 * r + 3];
+        const double tb = a.t[r] / a.bs;
+        const double ti = floor(tb);
+        a.Ti[r] = (int)std::max(-2.0 * kCoordBias, std::min(2.0 * kCoordBias, ti));
+        a.tf[r] = (float)(tb - (double)a.Ti[r]);
+    }
+    a.N = (int)ceil(c->prm.mu / a.h - 1e-9);
+    a.mu = c->prm.mu;
+    a.hf = (float)a.h;
+    a.ibs = (float)(1.0 / a.bs);
+    a.seg = segment;
+    a.n = n;
+    if (n > 0) {
+        laser_keys_kernel<<<grid_for(c->sm_count, n, 256, 8), 256, 0, s>>>(pts, a, c->d);
+        c->launches += 1;
+    }
+    return finish_alloc(c, s);
 }
 
 int launch_load_blocks(denser_ctx* c, const int32_t* coords_dev, int64_t n, int64_t base, cudaStream_t s) {

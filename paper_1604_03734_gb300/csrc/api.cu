@@ -228,6 +228,8 @@ void free_all(denser_ctx* c) {
         if (c->dstage_free[i]) cudaEventDestroy(c->dstage_free[i]);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->laser_acc) cudaFree(c->laser_acc);
+    if (c->laser_touched) cudaFree(c->laser_touched);
 }
 
 }  // namespace
@@ -290,6 +292,7 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
         c->dstage_copied[i] = nullptr, c->dstage_free[i] = nullptr;
     }
     c->dstage_next = 0;
+    c->laser_acc = nullptr, c->laser_touched = nullptr;
     c->ctl_i = nullptr, c->ctl_d = nullptr, c->h_ctl_i = nullptr, c->h_ctl_d = nullptr;
     c->loop.valid = false;
     c->elem_size = p.precision == DENSER_FP32 ? 4 : 2;
@@ -450,6 +453,46 @@ int denser_integrate(denser_ctx* c, const float* depth, const denser_intrinsics*
         }
         return DENSER_OK;
     });
+}
+
+// Laser scans: points float32 [n][3] in the sensor frame, host or device memory.
+static int points_call(denser_ctx* c, const float* points, int64_t n_points, const double T_gs[16], int32_t segment,
+                void* stream, int32_t* n_new_out, bool alloc, bool fuse, const char* what) {
+    return guarded(c, [&]() -> int {
+        if (n_points < 0 || n_points > (1ll << 28) || (n_points > 0 && !points) || !valid_pose(T_gs) || segment < 0 ||
+            segment > kMaxSegment)
+            return set_error(c, DENSER_ERR_INVALID_ARG, std::string(what) + ": bad points, count, pose or segment");
+        cudaStream_t s = (cudaStream_t)stream;
+        const float* dp = nullptr;
+        int slot = -1, rc;
+        if (n_points > 0 && (rc = stage_depth(c, points, (size_t)n_points * 12, s, &dp, &slot))) return rc;
+        rc = DENSER_OK;
+        if (alloc) rc = launch_alloc_points(c, dp, n_points, T_gs, segment, s);
+        if (!rc && fuse) rc = launch_fuse_points(c, dp, n_points, T_gs, segment, s);
+        const int rr = release_depth(c, slot, s);
+        if (rc || (rc = rr)) return rc;
+        if (n_new_out) {
+            rc = read_counters(c, s);
+            *n_new_out = c->h_counters[kLastNew];
+            return rc;
+        }
+        return DENSER_OK;
+    });
+}
+
+int denser_alloc_points(denser_ctx* c, const float* points, int64_t n_points, const double T_gs[16], int32_t segment,
+                        void* stream, int32_t* n_new_out) {
+    return points_call(c, points, n_points, T_gs, segment, stream, n_new_out, true, false, "alloc_points");
+}
+
+int denser_fuse_points(denser_ctx* c, const float* points, int64_t n_points, const double T_gs[16], int32_t segment,
+                       void* stream) {
+    return points_call(c, points, n_points, T_gs, segment, stream, nullptr, false, true, "fuse_points");
+}
+
+int denser_integrate_points(denser_ctx* c, const float* points, int64_t n_points, const double T_gs[16],
+                            int32_t segment, void* stream, int32_t* n_new_out) {
+    return points_call(c, points, n_points, T_gs, segment, stream, n_new_out, true, true, "integrate_points");
 }
 
 int denser_regularize(denser_ctx* c, int32_t max_iters, double gap_tol, int32_t start, void* stream,

@@ -137,6 +137,10 @@ struct denser_ctx {
     cudaEvent_t dstage_copied[2];  // recorded on copy_stream after the copy into dstage[i]
     cudaEvent_t dstage_free[2];    // recorded on the call's stream after the kernels reading dstage[i]
     int dstage_next;
+    // laser fusion: per-voxel packed accumulators (count << 48 plus a fixed-point sum)
+    // and per-block touched flags, allocated on first use
+    unsigned long long* laser_acc;
+    uint8_t* laser_touched;
     void* hstage;              // pinned host staging for host outputs
     size_t hstage_bytes;
     uint8_t* omega_bytes;      // extract scratch
@@ -192,6 +196,8 @@ int launch_convert_state(denser_ctx* c, const void* src, float* dst, int64_t n, 
                          cudaStream_t s);
 int launch_surface(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long long* tri_ids, int64_t capacity,
                    cudaStream_t s);
+int launch_alloc_points(denser_ctx* c, const float* pts, int64_t n, const double* T, int32_t segment, cudaStream_t s);
+int launch_fuse_points(denser_ctx* c, const float* pts, int64_t n, const double* T, int32_t segment, cudaStream_t s);
 int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s);
 int launch_sort_pairs(denser_ctx* c, unsigned long long* keys, uint32_t* vals, const int32_t* count, int capacity,
                       cudaStream_t s);
@@ -244,6 +250,23 @@ __device__ inline int floor_small(float v) {
     const float t = __fadd_rn(v, 12582912.0f);
     const int n = __float_as_int(t) - 0x4B400000;
     return (t - 12582912.0f) > v ? n - 1 : n;
+}
+
+// Ray of a laser point p (sensor frame) under a sensor->global rotation R (row-major):
+// range r = sqrt((x*x + y*y) + z*z), unit direction d = p / r and its global direction
+// dg = R d, each row summed left to right, every float64 operation rounded on its own
+// (the _rn intrinsics keep fused multiply-adds out).  Returns false for a point that is
+// not finite or at range 0.
+__device__ inline bool laser_ray(const double* R, float px, float py, float pz, double* r, double* dg) {
+    const double x = px, y = py, z = pz;
+    const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+    if (!(isfinite(rr) && rr > 0.0)) return false;
+    const double d0 = __ddiv_rn(x, rr), d1 = __ddiv_rn(y, rr), d2 = __ddiv_rn(z, rr);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        dg[i] = __dadd_rn(__dadd_rn(__dmul_rn(R[3 * i], d0), __dmul_rn(R[3 * i + 1], d1)), __dmul_rn(R[3 * i + 2], d2));
+    *r = rr;
+    return true;
 }
 
 inline int grid_for(int sm_count, long long work, int threads, int per_sm) {

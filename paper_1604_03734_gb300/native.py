@@ -29,6 +29,7 @@ DENSER_FP32, DENSER_FP16, DENSER_BF16 = 0, 1, 2
 # every symbol include/denser.h declares
 EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_reset",
            "denser_last_error", "denser_sync", "denser_alloc_blocks", "denser_fuse_depth", "denser_integrate",
+           "denser_alloc_points", "denser_fuse_points", "denser_integrate_points",
            "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual", "denser_extract_surface",
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
            "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc",
@@ -93,6 +94,9 @@ def lib():
             "denser_alloc_blocks": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp, P(_i32)]),
             "denser_fuse_depth": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp]),
             "denser_integrate": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp, P(_i32)]),
+            "denser_alloc_points": (_i32, [_vp, _vp, _i64, P(_dbl), _i32, _vp, P(_i32)]),
+            "denser_fuse_points": (_i32, [_vp, _vp, _i64, P(_dbl), _i32, _vp]),
+            "denser_integrate_points": (_i32, [_vp, _vp, _i64, P(_dbl), _i32, _vp, P(_i32)]),
             "denser_regularize": (_i32, [_vp, _i32, _dbl, _i32, _vp, P(denser_reg_stats)]),
             "denser_energy": (_i32, [_vp, P(_dbl), P(_dbl), _vp]),
             "denser_extract": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, P(_i64), _vp]),
@@ -228,6 +232,33 @@ def denser_integrate(ctx, depth, K: denser_intrinsics, T_gc, segment=0, stream=N
     n = _i32(0)
     _check(ctx, lib().denser_integrate(ctx, _ptr(depth, np.float32), ctypes.byref(K), tp, segment,
                                        _stream(stream), ctypes.byref(n) if count else None))
+    return n.value if count else None
+
+
+def _npoints(points):
+    return 0 if points is None else int(points.shape[0])
+
+
+def denser_alloc_points(ctx, points, T_gs, segment=0, stream=None, count=False):
+    """Allocation along a laser scan's rays; points float32 [n, 3] (sensor frame)."""
+    keep, tp = _pose(T_gs)
+    n = _i32(0)
+    _check(ctx, lib().denser_alloc_points(ctx, _ptr(points, np.float32), _npoints(points), tp, segment,
+                                          _stream(stream), ctypes.byref(n) if count else None))
+    return n.value if count else None
+
+
+def denser_fuse_points(ctx, points, T_gs, segment=0, stream=None):
+    keep, tp = _pose(T_gs)
+    return _check(ctx, lib().denser_fuse_points(ctx, _ptr(points, np.float32), _npoints(points), tp, segment,
+                                                _stream(stream)))
+
+
+def denser_integrate_points(ctx, points, T_gs, segment=0, stream=None, count=False):
+    keep, tp = _pose(T_gs)
+    n = _i32(0)
+    _check(ctx, lib().denser_integrate_points(ctx, _ptr(points, np.float32), _npoints(points), tp, segment,
+                                              _stream(stream), ctypes.byref(n) if count else None))
     return n.value if count else None
 
 

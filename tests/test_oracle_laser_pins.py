@@ -191,7 +191,8 @@ def test_allocation_band_axis_aligned():
 
 def test_invalid_points_are_skipped():
     g = box_grid((-2, -2, -1), (2, 2, 6))
-    pts = np.array([[np.nan, 0, 1], [0, 0, 0], [np.inf, 1, 1]], np.float32)
+    # NaN, zero range, infinite, and beyond the 2^22-sample range limit (about 210 km)
+    pts = np.array([[np.nan, 0, 1], [0, 0, 0], [np.inf, 1, 1], [0, 0, 3.0e5]], np.float32)
     assert L.alloc_scan(O.SparseGrid(O.Params()), pts, T0) == 0
     cnt = L.fuse_scan(g, pts, T0)
     assert cnt.sum() == 0 and np.all(g.w == 0)
