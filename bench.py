@@ -198,6 +198,7 @@ def main():
     ap.add_argument("--schedule", default=None, help="sweep_kernel,order,ctas_per_sm,use_graph (default: the library's)")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start time-to-gap comparison")
     ap.add_argument("--no-surface", action="store_true", help="skip the surface-extraction measurement")
+    ap.add_argument("--no-laser", action="store_true", help="skip the laser-scan fusion measurement")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -356,6 +357,44 @@ def main():
                    "l2": "256 MB written before each call"}
         del tp, ti, bf, flush
 
+    # laser ray fusion (a separate map, outside the step): 64-beam x 2000-azimuth scans
+    # every 5 m along the same street, allocation + march + finalize per scan
+    laser = None
+    if not args.no_laser:
+        from synth.scenes import Lidar
+        lid = Lidar()
+        lframes = list(range(0, args.frames, 10))
+        pts = [torch.from_numpy(np.ascontiguousarray(scene.lidar_scan(k, lid))).to(dev) for k in lframes]
+        ml = N.DenserMap(device=local, max_blocks=1 << 17, hash_slots=1 << 20)
+
+        def laser_pass():
+            N.denser_reset(ml.ctx, stream)
+            for p, k in zip(pts, lframes):
+                N.denser_integrate_points(ml.ctx, p, poses[k], 0, stream)
+
+        laser_pass()
+        torch.cuda.synchronize()
+        snap = ml.snapshot()
+        obs = float(snap["w"].sum())
+        reps, tot = 3, 0.0
+        for _ in range(reps):
+            l0e, l1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0e.record(stream)
+            laser_pass()
+            l1e.record(stream)
+            torch.cuda.synchronize()
+            tot += l0e.elapsed_time(l1e)
+        lms = tot / reps
+        rays = sum(int(p.shape[0]) for p in pts)
+        lbytes = 12 * rays + 16 * obs
+        laser = {"scans": len(pts), "rays_per_scan": int(pts[0].shape[0]), "ms_per_scan": lms / len(pts),
+                 "rays_per_s": rays / (lms / 1e3), "observations_per_s": obs / (lms / 1e3),
+                 "blocks": int(len(snap["coords"])), "achieved_gbs": lbytes / (lms / 1e3) / 1e9,
+                 "frac_of_measured_hbm": lbytes / (lms / 1e3) / 1e9 / hbm,
+                 "bytes": "12 B per ray (point) + 16 B per voxel observation (64-bit accumulator read and write)"}
+        ml.close()
+        del pts
+
     cpu = None
     if not args.no_cpu_baseline:
         n = 3
@@ -376,7 +415,7 @@ def main():
                    "l2": f"working set {bpv * nvox / 1e9:.2f} GB per sweep > 129 MB L2, no flush",
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),
                    "pd_share_of_step": sweep_ms / args.steps / step_ms,
-                   "time_to_gap_1e-4_warm_vs_plain": ttg, "surface_extraction": surface},
+                   "time_to_gap_1e-4_warm_vs_plain": ttg, "surface_extraction": surface, "laser_fusion": laser},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": measured_traffic(kernel_name, args.precision, nvox),
                      "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": kernel_name,

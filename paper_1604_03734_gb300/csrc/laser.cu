@@ -52,7 +52,7 @@ __device__ __forceinline__ int floor_rel(float q, float e, bool* ok) {
 __global__ void __launch_bounds__(128) laser_march_kernel(const float* __restrict__ pts, MarchArgs a, DeviceMap m,
                                                           unsigned long long* __restrict__ acc,
                                                           uint8_t* __restrict__ touched) {
-    const float eps19 = 1.90734863e-6f, eps20 = 9.53674316e-7f, eps21 = 4.76837158e-7f;
+    const float eps19 = 1.90734863e-6f, eps20 = 9.53674316e-7f, eps22 = 2.38418579e-7f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n;
          i += (long long)gridDim.x * blockDim.x) {
         double r, dg[3];
@@ -60,18 +60,21 @@ __global__ void __launch_bounds__(128) laser_march_kernel(const float* __restric
         const double Md = floor(__ddiv_rn(__dadd_rn(r, a.mu), a.h));
         if (!(Md < 4194304.0)) continue;  // range beyond 2^22 samples: not a valid point
         const int M = (int)Md;
-        // q = t/s + n (h/s) dg relative to Tv, h/s = 1/2 exactly; per-axis bound
-        //   |q - q_real| <= 2^-24 (2 M |Dh| + |q| + 1)  (rounding of Dh, the fma, tf),
-        //   e = 2^-21 (2 M |Dh| + 2 + M |Dh|) covers it at least 4 times.
-        float Dh[3], e[3], Dg[3];
+        // q = t/s + n (h/s) dg relative to Tv, h/s = 1/2 exactly, with the step held as a
+        // float32 pair Dh + Dl: q = fma(n, Dh, fma(n, Dl, tf)).  Per-axis bound
+        //   |q - q_real| <= 2^-24 (|q| + 2) + 2^-48 n |Dh|  (the two fmas, tf, the pair),
+        //   e = 2^-22 (M |Dh| + 3) covers it at least 4 times.
+        float Dh[3], Dl[3], e[3], Dg[3];
         bool fast = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             Dg[k] = (float)dg[k];
-            Dh[k] = (float)(0.5 * dg[k]);
+            const double half = 0.5 * dg[k];
+            Dh[k] = (float)half;
+            Dl[k] = (float)(half - (double)Dh[k]);
             const float span = (float)M * fabsf(Dh[k]);
             fast = fast && span < 2097152.0f;
-            e[k] = eps21 * (3.0f * span + 2.0f);
+            e[k] = eps22 * (span + 3.0f);
         }
         // the hit point in voxel units relative to Tv, P = r dg / s + (t / s - Tv), as a
         // float32 pair hi + lo: the signed distance of a voxel is then a short vector
@@ -90,9 +93,9 @@ __global__ void __launch_bounds__(128) laser_march_kernel(const float* __restric
             int k0, k1, k2;
             bool ok = fast;
             if (ok) {
-                k0 = floor_rel(fmaf(nf, Dh[0], a.tf[0]), e[0], &ok);
-                k1 = floor_rel(fmaf(nf, Dh[1], a.tf[1]), e[1], &ok);
-                k2 = floor_rel(fmaf(nf, Dh[2], a.tf[2]), e[2], &ok);
+                k0 = floor_rel(fmaf(nf, Dh[0], fmaf(nf, Dl[0], a.tf[0])), e[0], &ok);
+                k1 = floor_rel(fmaf(nf, Dh[1], fmaf(nf, Dl[1], a.tf[1])), e[1], &ok);
+                k2 = floor_rel(fmaf(nf, Dh[2], fmaf(nf, Dl[2], a.tf[2])), e[2], &ok);
             }
             if (!ok) {
                 const double rho = __dmul_rn((double)n, a.h);

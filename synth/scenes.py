@@ -170,7 +170,52 @@ class Scene:
         valid = (best <= lidar.r_max) & ~drop
         rho = np.where(valid, best + rng_noise, np.nan)
         pts = (ds * rho[None]).reshape(3, -1).T
-        return pts.astype(np.float32)
+        return np.ascontiguousarray(pts, dtype=np.float32)
+
+    # ---------------------------------------------------------------- stereo
+    def _cast(self, T, D):
+        best = np.full(D.shape[1:], np.inf)
+        for r in self.rects:
+            _hit_rect(best, T[:3, 3], D, r)
+        for b in self.boxes:
+            _hit_box(best, T[:3, 3], D, b, None, T)
+        for f in self.facades:
+            _hit_facade(best, T[:3, 3], D, f)
+        return best
+
+    def intensity(self, T: np.ndarray, rng=None, noise: float = 0.01) -> np.ndarray:
+        """Grey image [H, W] float32 in [0, 1] seen from pose T: surfaces carry a fixed
+        value-noise texture of their world position (lattice 0.1 m, trilinear), so that
+        every view of a point sees the same value; rays with no hit within d_max see a
+        smooth sky gradient.  Additive N(0, noise) pixel noise from ``rng``."""
+        c = self.camera
+        R, o = T[:3, :3], T[:3, 3]
+        D = np.einsum("ij,jhw->ihw", R, self._rays())
+        lam = self._cast(T, D)
+        hit = lam <= self.d_max
+        P = o[:, None, None] + D * np.where(hit, lam, 0.0)[None]
+        img = texture_value(P.reshape(3, -1).T).reshape(c.height, c.width)
+        sky = 0.85 + 0.1 * (np.arange(c.height)[:, None] / c.height) * np.ones((1, c.width))
+        img = np.where(hit, img, sky)
+        if rng is not None and noise > 0:
+            img = img + rng.standard_normal(img.shape) * noise
+        return np.clip(img, 0.0, 1.0).astype(np.float32)
+
+    def stereo_pair(self, frame: int, baseline: float = 0.54, noise: float = 0.01):
+        """(I_left, I_right, d_right, T_right): a rectified pair whose right camera sits at
+        the pose of ``frame`` and whose left camera is ``baseline`` metres along its -x
+        axis; the true disparity on the right image is f * baseline / z (0 where the
+        right view sees nothing), so that I_left(x + d) = I_right(x).  Noise from
+        PCG64([seed, 3, frame])."""
+        TR = self.poses[frame]
+        TL = TR.copy()
+        TL[:3, 3] = TR[:3, 3] - baseline * TR[:3, 0]
+        rng = np.random.Generator(np.random.PCG64([self.seed, 3, frame]))
+        IL = self.intensity(TL, rng, noise)
+        IR = self.intensity(TR, rng, noise)
+        z = self.render_clean(frame)
+        d = np.where(z > 0, self.camera.fx * baseline / np.where(z > 0, z, 1.0), 0.0).astype(np.float32)
+        return IL, IR, d, TR
 
     def depth_maps(self, frames=None) -> np.ndarray:
         """Depth maps [n, H, W] float32; frame k draws its noise from PCG64([seed, 1, k])."""
@@ -182,6 +227,38 @@ class Scene:
             rng = np.random.Generator(np.random.PCG64([self.seed, 1, k]))
             out[i] = self.render(k, rng)
         return out
+
+
+# ---------------------------------------------------------------- texture
+def _lattice_hash(i, j, k):
+    """Deterministic values in [0, 1) on an integer lattice (a 64-bit integer mix)."""
+    h = (i.astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15)) ^ (j.astype(np.uint64) * np.uint64(0xC2B2AE3D27D4EB4F)) \
+        ^ (k.astype(np.uint64) * np.uint64(0x165667B19E3779F9))
+    h ^= h >> np.uint64(29)
+    h *= np.uint64(0xBF58476D1CE4E5B9)
+    h ^= h >> np.uint64(32)
+    return (h >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+
+
+def texture_value(P: np.ndarray, cell: float = 0.1) -> np.ndarray:
+    """Value noise of world points P [n, 3]: trilinear interpolation of lattice values,
+    two octaves (cells of 0.1 m and 0.4 m), in [0, 1]."""
+    out = np.zeros(len(P))
+    for scale, wgt in ((cell, 0.6), (4 * cell, 0.4)):
+        q = P / scale
+        b = np.floor(q)
+        f = q - b
+        b = b.astype(np.int64)
+        acc = np.zeros(len(P))
+        for dx in (0, 1):
+            for dy in (0, 1):
+                for dz in (0, 1):
+                    wv = (f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1]) * \
+                         (f[:, 2] if dz else 1 - f[:, 2])
+                    with np.errstate(over="ignore"):
+                        acc += wv * _lattice_hash(b[:, 0] + dx, b[:, 1] + dy, b[:, 2] + dz)
+        out += wgt * acc
+    return out
 
 
 # ---------------------------------------------------------------- primitives
