@@ -200,6 +200,62 @@ int denser_fuse_points(denser_ctx* ctx, const float* points, int64_t n_points, c
 int denser_integrate_points(denser_ctx* ctx, const float* points, int64_t n_points, const double T_gs[16],
                             int32_t segment, void* stream, int32_t* n_new_out);
 
+/* ------------------------------------------------------------------ stereo depth maps
+ * Depth-map estimation from a rectified pair (Section IV): a Census Transform Signature
+ * data term (IV-A) and an affine TGV regulariser shaped by an image-driven diffusion
+ * tensor (IV-B, IV-C).  The paper fixes no window, range or optimiser schedule; here:
+ * I_R is the reference (rho compares I_L(x + d, y) with I_R(x, y)), a 9 x 7 Census
+ * window (62 bits, edge pixels repeated), cost = Hamming / 62 (1 off the image),
+ * T = I + (exp(-gamma |grad I_R|^beta) - 1) n n^T, and the data term decoupled by an
+ * auxiliary field a: `outer` times an exhaustive integer a-step (argmin over delta in
+ * [0, max_disp) of lambda C + (d - delta)^2 / (2 theta), float32, ties to the smaller
+ * delta) then `inner` Chambolle-Pock iterations on the TGV-L2 problem, theta shrinking
+ * by theta_decay.  Images are float32 [height][width] in [0, 1]; every pointer of these
+ * calls is device memory (host pointers are DENSER_ERR_INVALID_ARG); width, height >= 2.
+ * They need no context, enqueue on `stream` and do not wait. */
+typedef struct {
+    int32_t max_disp;                 /* disparities 0 .. max_disp - 1 */
+    float lambda, alpha1, alpha2;     /* Table I: 0.5, 1.0, 5.0 */
+    float beta, gamma;                /* Table I: 1.0, 4.0 */
+    float theta0, theta_decay;        /* coupling schedule: 2.0, 0.5 */
+    int32_t outer, inner;             /* 8 a-steps, 80 primal-dual iterations after each */
+} denser_stereo_params;
+
+void denser_stereo_default_params(denser_stereo_params* p);
+
+/* 62-bit Census signatures sig uint64 [h][w] of img (bit b: the b-th window pixel in
+ * row-major order, the centre skipped, is darker than the centre). */
+int denser_census(const float* img, int32_t width, int32_t height, uint64_t* sig, void* stream);
+
+/* Diffusion tensor of img as three planes float32 [3][h][w]: t00, t01 (= t10), t11. */
+int denser_diffusion_tensor(const float* img, int32_t width, int32_t height, float gamma, float beta,
+                            float* tensor, void* stream);
+
+/* a-step: a = argmin_delta lambda Hamming/62 + (d - delta)^2 / (2 theta) per pixel
+ * (a float32 [h][w] holds integers); theta <= 0 or infinite drops the coupling; a may
+ * alias d. */
+int denser_disparity_assign(const uint64_t* sig_left, const uint64_t* sig_right, int32_t width,
+                            int32_t height, int32_t max_disp, float lambda, double theta,
+                            const float* d, float* a, void* stream);
+
+/* `iters` primal-dual iterations of the d-step on state float32 [12][h][w]: d, d_bar,
+ * w1, w2, w_bar1, w_bar2, p1, p2, q11, q12, q21, q22 (in that plane order). */
+int denser_tgv_iterate(const float* a, const float* tensor, int32_t width, int32_t height, float alpha1,
+                       float alpha2, double theta, int32_t iters, float* state, void* stream);
+
+/* Bytes of workspace denser_stereo_estimate needs for a width x height pair. */
+size_t denser_stereo_workspace_size(int32_t width, int32_t height);
+
+/* The whole estimate: disparity float32 [h][w] on I_R's grid. */
+int denser_stereo_estimate(const float* img_left, const float* img_right, int32_t width, int32_t height,
+                           const denser_stereo_params* params, void* workspace, size_t workspace_bytes,
+                           float* disparity, void* stream);
+
+/* depth = fx * baseline / disparity where disparity > min_disp, else 0 (invalid), the
+ * depth-map input of denser_alloc_blocks / denser_fuse_depth / denser_integrate. */
+int denser_disparity_to_depth(const float* disparity, int32_t width, int32_t height, float fx, float baseline,
+                              float min_disp, float* depth, void* stream);
+
 /* Regularisation (Section III-B/C): Chambolle-Pock iterations on the Omega-aware
  * TV-L2 energy over the allocated blocks, Omega = {w > 0}:
  *   p <- P(p + sigma grad_Omega u_bar),  P(q) = q / max(1, |q|_2)      (Eq. 3)

@@ -10,10 +10,12 @@ taken here:
   D1  rectified pair, intensities in [0, 1]; the reference image is I_R and
       rho(d, x, y) compares I_L(x + d, y) with I_R(x, y) (Section IV-A), so the
       disparity lives on I_R's grid, d >= 0, depth z = f B / d;
-  D2  Census window 5 x 5: a 24-bit signature, bit b (row-major over the window,
-      the centre skipped) set when that neighbour is darker than the centre; pixels
-      beyond the image repeat the edge;
-  D3  data cost C(x, y, delta) = Hamming(sig_L(x + delta, y), sig_R(x, y)) / 24 for
+  D2  Census window 9 x 7 (width x height): a 62-bit signature, bit b (row-major over
+      the window, the centre skipped) set when that neighbour is darker than the
+      centre; pixels beyond the image repeat the edge.  (A 5 x 5 window, 24 bits, left
+      a third of the street pair's pixels more than 3 px off after regularisation:
+      too few bits to tell 256 candidate disparities apart);
+  D3  data cost C(x, y, delta) = Hamming(sig_L(x + delta, y), sig_R(x, y)) / 62 for
       integer delta in [0, D); 1 where x + delta falls off the image;
   D4  T = exp(-gamma |grad I|^beta) n n^T + n_perp n_perp^T with n = grad I / |grad I|
       (= I + (e - 1) n n^T), the identity where grad I = 0; grad I of the reference
@@ -42,7 +44,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-BITS = 24  # 5 x 5 window without its centre
+RX, RY = 4, 3  # Census window half-width and half-height: 9 x 7
+BITS = (2 * RX + 1) * (2 * RY + 1) - 1  # 62, the centre skipped
 
 
 @dataclass(frozen=True)
@@ -63,26 +66,26 @@ class StereoParams:
 
 # ----------------------------------------------------------------- Census (D2, D3)
 def census(I) -> np.ndarray:
-    """24-bit Census signatures [H, W] (uint32) of image I."""
+    """62-bit Census signatures [H, W] (uint64) of image I."""
     I = np.asarray(I, dtype=np.float32)
     H, W = I.shape
     ys = np.arange(H)[:, None]
     xs = np.arange(W)[None, :]
-    sig = np.zeros((H, W), dtype=np.uint32)
+    sig = np.zeros((H, W), dtype=np.uint64)
     b = 0
-    for dy in range(-2, 3):
-        for dx in range(-2, 3):
+    for dy in range(-RY, RY + 1):
+        for dx in range(-RX, RX + 1):
             if dx == 0 and dy == 0:
                 continue
             nb = I[np.clip(ys + dy, 0, H - 1), np.clip(xs + dx, 0, W - 1)]
-            sig |= (nb < I).astype(np.uint32) << np.uint32(b)
+            sig |= (nb < I).astype(np.uint64) << np.uint64(b)
             b += 1
     return sig
 
 
 def popcount(x) -> np.ndarray:
-    x = np.asarray(x, dtype=np.uint32)
-    return np.unpackbits(x.view(np.uint8).reshape(x.shape + (4,)), axis=-1).sum(axis=-1).astype(np.int64)
+    x = np.asarray(x, dtype=np.uint64)
+    return np.unpackbits(x.view(np.uint8).reshape(x.shape + (8,)), axis=-1).sum(axis=-1).astype(np.int64)
 
 
 def hamming_volume(sigL, sigR, D) -> np.ndarray:
@@ -142,8 +145,22 @@ def apply_T(T, v):
 def assign(hvol, d, lam, theta) -> np.ndarray:
     """a-step: argmin over delta of lam h/BITS + (d - delta)^2 / (2 theta), float32 in the
     order cw*h + (dd*dd)*cq, cw = float32(lam/BITS), cq = float32(1/(2 theta)), ties to
-    the smallest delta.  theta = inf drops the coupling (winner takes all)."""
-    D = hvol.shape[0]
+    the smallest delta.  theta = inf drops the coupling (winner takes all).  hvol is the
+    Hamming volume [D, H, W], or a pair (sig_L, sig_R, D) to compute it delta by delta."""
+    if isinstance(hvol, tuple):
+        sigL, sigR, D = hvol
+        H, W = sigR.shape
+
+        def h_of(k):
+            h = np.full((H, W), BITS, dtype=np.int64)
+            if k < W:
+                h[:, : W - k] = popcount(sigL[:, k:] ^ sigR[:, : W - k])
+            return h
+    else:
+        D = hvol.shape[0]
+
+        def h_of(k):
+            return hvol[k]
     cw = np.float32(lam / BITS)
     cq = np.float32(0.0 if np.isinf(theta) else 1.0 / (2.0 * theta))
     d32 = np.asarray(d, dtype=np.float32)
@@ -151,7 +168,7 @@ def assign(hvol, d, lam, theta) -> np.ndarray:
     arg = np.zeros(d32.shape, dtype=np.int64)
     for k in range(D):
         dd = d32 - np.float32(k)
-        e = hvol[k].astype(np.float32) * cw + (dd * dd) * cq
+        e = h_of(k).astype(np.float32) * cw + (dd * dd) * cq
         better = e < best
         best = np.where(better, e, best)
         arg = np.where(better, k, arg)
@@ -206,7 +223,7 @@ def estimate(IL, IR, prm: StereoParams = StereoParams(), trace=None):
     """Disparity map on I_R's grid (D1-D8).  ``trace`` (a list) receives (theta, a, d)
     after every outer step."""
     sL, sR = census(IL), census(IR)
-    hvol = hamming_volume(sL, sR, prm.max_disp)
+    hvol = (sL, sR, prm.max_disp)
     T = diffusion_tensor(IR, prm.gamma, prm.beta)
     d0 = assign(hvol, np.zeros(IR.shape), prm.lam, np.inf)
     st = TGVState(d0)

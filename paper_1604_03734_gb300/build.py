@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libdenser.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["alloc.cu", "fuse.cu", "regularize.cu", "api.cu", "noalloc.cu", "net.cu", "surface.cu", "laser.cu"]
+SOURCES = ["alloc.cu", "fuse.cu", "regularize.cu", "api.cu", "noalloc.cu", "net.cu", "surface.cu", "laser.cu", "stereo.cu"]
 
 
 def _nvcc() -> str:

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <string>
 
+#include <initializer_list>
+
 #include "common.cuh"
 
 using namespace denser;
@@ -493,6 +495,99 @@ int denser_fuse_points(denser_ctx* c, const float* points, int64_t n_points, con
 int denser_integrate_points(denser_ctx* c, const float* points, int64_t n_points, const double T_gs[16],
                             int32_t segment, void* stream, int32_t* n_new_out) {
     return points_call(c, points, n_points, T_gs, segment, stream, n_new_out, true, true, "integrate_points");
+}
+
+// ------------------------------------------------------------------ stereo
+static bool dev_all(std::initializer_list<const void*> ps) {
+    for (const void* p : ps)
+        if (!p || !is_device_ptr(p)) return false;
+    return true;
+}
+
+static bool stereo_size_ok(int32_t W, int32_t H) {
+    return W >= 2 && H >= 2 && (int64_t)W * H < (1ll << 30);
+}
+
+void denser_stereo_default_params(denser_stereo_params* p) {
+    if (!p) return;
+    p->max_disp = 128;
+    p->lambda = 0.5f, p->alpha1 = 1.0f, p->alpha2 = 5.0f;
+    p->beta = 1.0f, p->gamma = 4.0f;
+    p->theta0 = 2.0f, p->theta_decay = 0.5f;
+    p->outer = 8, p->inner = 80;
+}
+
+int denser_census(const float* img, int32_t W, int32_t H, uint64_t* sig, void* stream) {
+    if (!stereo_size_ok(W, H) || !dev_all({img, sig})) return DENSER_ERR_INVALID_ARG;
+    return stereo_census(img, W, H, (unsigned long long*)sig, (cudaStream_t)stream);
+}
+
+int denser_diffusion_tensor(const float* img, int32_t W, int32_t H, float gamma, float beta, float* T, void* stream) {
+    if (!stereo_size_ok(W, H) || !dev_all({img, T}) || !(gamma >= 0) || !(beta > 0)) return DENSER_ERR_INVALID_ARG;
+    return stereo_tensor(img, W, H, gamma, beta, T, (cudaStream_t)stream);
+}
+
+int denser_disparity_assign(const uint64_t* sigL, const uint64_t* sigR, int32_t W, int32_t H, int32_t D, float lambda,
+                            double theta, const float* d, float* a, void* stream) {
+    if (!stereo_size_ok(W, H) || D < 1 || D > 4096 || !dev_all({sigL, sigR, d, a}) || !(lambda >= 0))
+        return DENSER_ERR_INVALID_ARG;
+    return stereo_assign((const unsigned long long*)sigL, (const unsigned long long*)sigR, W, H, D, lambda, theta, d,
+                         a, (cudaStream_t)stream);
+}
+
+int denser_tgv_iterate(const float* a, const float* T, int32_t W, int32_t H, float alpha1, float alpha2, double theta,
+                       int32_t iters, float* state, void* stream) {
+    if (!stereo_size_ok(W, H) || iters < 0 || !(alpha1 > 0) || !(alpha2 > 0) || !(theta > 0) ||
+        !dev_all({a, T, state}))
+        return DENSER_ERR_INVALID_ARG;
+    return stereo_tgv(a, T, W, H, alpha1, alpha2, theta, iters, state, (cudaStream_t)stream);
+}
+
+size_t denser_stereo_workspace_size(int32_t W, int32_t H) {
+    if (!stereo_size_ok(W, H)) return 0;
+    // sig_L, sig_R (8 bytes a pixel), tensor (3), a, state (12) float planes
+    return (size_t)W * H * (16 + 4 * 16);
+}
+
+int denser_stereo_estimate(const float* IL, const float* IR, int32_t W, int32_t H, const denser_stereo_params* p,
+                           void* ws, size_t ws_bytes, float* disparity, void* stream) {
+    if (!stereo_size_ok(W, H) || !p || p->max_disp < 1 || p->max_disp > 4096 || p->outer < 0 || p->inner < 0 ||
+        !(p->theta0 > 0) || !(p->theta_decay > 0) || !(p->alpha1 > 0) || !(p->alpha2 > 0) || !(p->lambda >= 0) ||
+        !(p->gamma >= 0) || !(p->beta > 0) || ws_bytes < denser_stereo_workspace_size(W, H) ||
+        !dev_all({IL, IR, ws, disparity}))
+        return DENSER_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)W * H;
+    unsigned long long* sigL = (unsigned long long*)ws;
+    unsigned long long* sigR = sigL + n;
+    float* T = (float*)(sigR + n);
+    float* a = T + 3 * n;
+    float* state = a + n;
+    int rc;
+    if ((rc = stereo_census(IL, W, H, sigL, s)) || (rc = stereo_census(IR, W, H, sigR, s)) ||
+        (rc = stereo_tensor(IR, W, H, p->gamma, p->beta, T, s)))
+        return rc;
+    if (cudaMemsetAsync(a, 0, n * 4, s) != cudaSuccess) return DENSER_ERR_CUDA;
+    // start: winner takes all (no coupling), w = p = q = 0
+    if ((rc = stereo_assign(sigL, sigR, W, H, p->max_disp, p->lambda, 0.0, a, a, s)) ||
+        (rc = stereo_init_state(state, a, W, H, s)))
+        return rc;
+    double theta = p->theta0;
+    for (int k = 0; k < p->outer; ++k) {
+        if ((rc = stereo_assign(sigL, sigR, W, H, p->max_disp, p->lambda, theta, state, a, s)) ||
+            (rc = stereo_tgv(a, T, W, H, p->alpha1, p->alpha2, theta, p->inner, state, s)))
+            return rc;
+        theta *= p->theta_decay;
+    }
+    return cudaMemcpyAsync(disparity, state, n * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? DENSER_OK
+                                                                                               : DENSER_ERR_CUDA;
+}
+
+int denser_disparity_to_depth(const float* disp, int32_t W, int32_t H, float fx, float baseline, float min_disp,
+                              float* depth, void* stream) {
+    if (!stereo_size_ok(W, H) || !(fx > 0) || !(baseline > 0) || !(min_disp >= 0) || !dev_all({disp, depth}))
+        return DENSER_ERR_INVALID_ARG;
+    return stereo_depth(disp, W, H, fx * baseline, min_disp, depth, (cudaStream_t)stream);
 }
 
 int denser_regularize(denser_ctx* c, int32_t max_iters, double gap_tol, int32_t start, void* stream,

@@ -197,6 +197,14 @@ int launch_convert_state(denser_ctx* c, const void* src, float* dst, int64_t n, 
 int launch_surface(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long long* tri_ids, int64_t capacity,
                    cudaStream_t s);
 int launch_alloc_points(denser_ctx* c, const float* pts, int64_t n, const double* T, int32_t segment, cudaStream_t s);
+int stereo_census(const float* img, int W, int H, unsigned long long* sig, cudaStream_t s);
+int stereo_tensor(const float* img, int W, int H, float gamma, float beta, float* T, cudaStream_t s);
+int stereo_assign(const unsigned long long* sigL, const unsigned long long* sigR, int W, int H, int D, float lambda,
+                  double theta, const float* d, float* a, cudaStream_t s);
+int stereo_tgv(const float* a, const float* T, int W, int H, float alpha1, float alpha2, double theta, int iters,
+               float* state, cudaStream_t s);
+int stereo_init_state(float* state, const float* d0, int W, int H, cudaStream_t s);
+int stereo_depth(const float* disp, int W, int H, float fb, float min_disp, float* depth, cudaStream_t s);
 int launch_fuse_points(denser_ctx* c, const float* pts, int64_t n, const double* T, int32_t segment, cudaStream_t s);
 int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s);
 int launch_sort_pairs(denser_ctx* c, unsigned long long* keys, uint32_t* vals, const int32_t* count, int capacity,

@@ -34,7 +34,10 @@ EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_r
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
            "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc",
            "denser_net_gather", "denser_net_targets", "denser_net_apply", "denser_conv3", "denser_conv3_wgrad",
-           "denser_relu_backward", "denser_net_loss", "denser_adam", "denser_pack_weights")
+           "denser_relu_backward", "denser_net_loss", "denser_adam", "denser_pack_weights",
+           "denser_stereo_default_params", "denser_census", "denser_diffusion_tensor", "denser_disparity_assign",
+           "denser_tgv_iterate", "denser_stereo_workspace_size", "denser_stereo_estimate",
+           "denser_disparity_to_depth")
 
 
 class denser_params(ctypes.Structure):
@@ -64,6 +67,13 @@ class denser_reg_stats(ctypes.Structure):
 class denser_schedule(ctypes.Structure):
     _fields_ = [("sweep_kernel", ctypes.c_int32), ("order", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32)]
+
+
+class denser_stereo_params(ctypes.Structure):
+    _fields_ = [("max_disp", ctypes.c_int32), ("lambda_", ctypes.c_float), ("alpha1", ctypes.c_float),
+                ("alpha2", ctypes.c_float), ("beta", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("theta0", ctypes.c_float), ("theta_decay", ctypes.c_float), ("outer", ctypes.c_int32),
+                ("inner", ctypes.c_int32)]
 
 
 class DenserError(RuntimeError):
@@ -119,6 +129,17 @@ def lib():
             "denser_adam": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, _i32, _vp]),
             "denser_pack_weights": (_i32, [_vp, _vp, _vp, _vp]),
+            "denser_stereo_default_params": (None, [P(denser_stereo_params)]),
+            "denser_census": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+            "denser_diffusion_tensor": (_i32, [_vp, _i32, _i32, ctypes.c_float, ctypes.c_float, _vp, _vp]),
+            "denser_disparity_assign": (_i32, [_vp, _vp, _i32, _i32, _i32, ctypes.c_float, _dbl, _vp, _vp, _vp]),
+            "denser_tgv_iterate": (_i32, [_vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, _dbl, _i32, _vp,
+                                          _vp]),
+            "denser_stereo_workspace_size": (ctypes.c_size_t, [_i32, _i32]),
+            "denser_stereo_estimate": (_i32, [_vp, _vp, _i32, _i32, P(denser_stereo_params), _vp, ctypes.c_size_t,
+                                              _vp, _vp]),
+            "denser_disparity_to_depth": (_i32, [_vp, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                                 _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -404,6 +425,59 @@ def denser_adam(w, grad, m, v, count, lr, beta1, beta2, eps, step, stream=None):
 
 def denser_pack_weights(w32, wf, wb, stream=None):
     _ok(lib().denser_pack_weights(_tptr(w32), _tptr(wf), _tptr(wb), _stream(stream)), "denser_pack_weights")
+
+
+# ------------------------------------------------------------ stereo
+def denser_stereo_default_params(**overrides) -> denser_stereo_params:
+    p = denser_stereo_params()
+    lib().denser_stereo_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+def _hw(img):
+    return int(img.shape[1]), int(img.shape[0])
+
+
+def denser_census(img, sig, stream=None):
+    W, H = _hw(img)
+    _ok(lib().denser_census(_tptr(img), W, H, _tptr(sig), _stream(stream)), "denser_census")
+
+
+def denser_diffusion_tensor(img, tensor, gamma=4.0, beta=1.0, stream=None):
+    W, H = _hw(img)
+    _ok(lib().denser_diffusion_tensor(_tptr(img), W, H, float(gamma), float(beta), _tptr(tensor), _stream(stream)),
+        "denser_diffusion_tensor")
+
+
+def denser_disparity_assign(sig_left, sig_right, max_disp, lam, theta, d, a, stream=None):
+    W, H = _hw(sig_right)
+    _ok(lib().denser_disparity_assign(_tptr(sig_left), _tptr(sig_right), W, H, int(max_disp), float(lam),
+                                      float(theta), _tptr(d), _tptr(a), _stream(stream)), "denser_disparity_assign")
+
+
+def denser_tgv_iterate(a, tensor, alpha1, alpha2, theta, iters, state, stream=None):
+    W, H = _hw(a)
+    _ok(lib().denser_tgv_iterate(_tptr(a), _tptr(tensor), W, H, float(alpha1), float(alpha2), float(theta),
+                                 int(iters), _tptr(state), _stream(stream)), "denser_tgv_iterate")
+
+
+def denser_stereo_workspace_size(width, height) -> int:
+    return int(lib().denser_stereo_workspace_size(int(width), int(height)))
+
+
+def denser_stereo_estimate(img_left, img_right, params, workspace, disparity, stream=None):
+    W, H = _hw(img_right)
+    nbytes = workspace.numel() * workspace.element_size()
+    _ok(lib().denser_stereo_estimate(_tptr(img_left), _tptr(img_right), W, H, ctypes.byref(params), _tptr(workspace),
+                                     nbytes, _tptr(disparity), _stream(stream)), "denser_stereo_estimate")
+
+
+def denser_disparity_to_depth(disparity, fx, baseline, min_disp, depth, stream=None):
+    W, H = _hw(disparity)
+    _ok(lib().denser_disparity_to_depth(_tptr(disparity), W, H, float(fx), float(baseline), float(min_disp),
+                                        _tptr(depth), _stream(stream)), "denser_disparity_to_depth")
 
 
 # ------------------------------------------------------------ convenience

@@ -184,17 +184,20 @@ class Scene:
         return best
 
     def intensity(self, T: np.ndarray, rng=None, noise: float = 0.01) -> np.ndarray:
-        """Grey image [H, W] float32 in [0, 1] seen from pose T: surfaces carry a fixed
-        value-noise texture of their world position (lattice 0.1 m, trilinear), so that
-        every view of a point sees the same value; rays with no hit within d_max see a
-        smooth sky gradient.  Additive N(0, noise) pixel noise from ``rng``."""
+        """Grey image [H, W] float32 in [0, 1] seen from pose T: surfaces carry a fixed,
+        band-limited value-noise texture of their world position (octaves 0.0125 - 0.4 m,
+        those finer than 4 pixels faded out), so that nearby views of a point see the same
+        value; rays with no hit within d_max see a smooth sky gradient.  Additive
+        N(0, noise) pixel noise from ``rng``."""
         c = self.camera
         R, o = T[:3, :3], T[:3, 3]
         D = np.einsum("ij,jhw->ihw", R, self._rays())
         lam = self._cast(T, D)
         hit = lam <= self.d_max
         P = o[:, None, None] + D * np.where(hit, lam, 0.0)[None]
-        img = texture_value(P.reshape(3, -1).T).reshape(c.height, c.width)
+        # metres per pixel at the hit (lam is the camera-frame depth: D has z = 1)
+        fp = np.where(hit, lam, 1.0) / c.fx
+        img = texture_value(P.reshape(3, -1).T, fp.reshape(-1)).reshape(c.height, c.width)
         sky = 0.85 + 0.1 * (np.arange(c.height)[:, None] / c.height) * np.ones((1, c.width))
         img = np.where(hit, img, sky)
         if rng is not None and noise > 0:
@@ -240,11 +243,17 @@ def _lattice_hash(i, j, k):
     return (h >> np.uint64(11)).astype(np.float64) / float(1 << 53)
 
 
-def texture_value(P: np.ndarray, cell: float = 0.1) -> np.ndarray:
-    """Value noise of world points P [n, 3]: trilinear interpolation of lattice values,
-    two octaves (cells of 0.1 m and 0.4 m), in [0, 1]."""
+def texture_value(P: np.ndarray, footprint=None, cell: float = 0.1) -> np.ndarray:
+    """Band-limited value noise of world points P [n, 3]: trilinear interpolation of
+    lattice values over octaves of 0.0125 .. 0.4 m, in [0, 1].  ``footprint`` [n] (metres
+    per pixel at each point) fades out the octaves finer than 4 pixels, so that nearby
+    views of a point sample the same, alias-free texture and close surfaces keep detail."""
     out = np.zeros(len(P))
-    for scale, wgt in ((cell, 0.6), (4 * cell, 0.4)):
+    total = np.zeros(len(P))
+    fp = np.zeros(len(P)) if footprint is None else np.asarray(footprint, dtype=np.float64)
+    for scale in (cell / 8, cell / 4, cell / 2, cell, 2 * cell, 4 * cell):
+        wgt = np.clip((scale / np.maximum(fp, 1e-12) - 2.0) / 2.0, 0.0, 1.0) if footprint is not None else \
+            np.ones(len(P))
         q = P / scale
         b = np.floor(q)
         f = q - b
@@ -258,7 +267,8 @@ def texture_value(P: np.ndarray, cell: float = 0.1) -> np.ndarray:
                     with np.errstate(over="ignore"):
                         acc += wv * _lattice_hash(b[:, 0] + dx, b[:, 1] + dy, b[:, 2] + dz)
         out += wgt * acc
-    return out
+        total += wgt
+    return np.where(total > 0, out / np.maximum(total, 1e-12), 0.5)
 
 
 # ---------------------------------------------------------------- primitives

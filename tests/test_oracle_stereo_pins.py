@@ -1,6 +1,6 @@
 """Pins of the stereo oracle (oracle/stereo_oracle.py) to facts that do not come from it:
 
-* Census signatures against a bit-by-bit loop, invariance under a monotone change of
+* Census signatures (9 x 7 window) against a bit-by-bit loop, invariance under a monotone change of
   intensity (the property Section IV-A names), zero for a flat window;
 * Hamming costs: zero at the true shift of an exactly shifted pair, popcount against
   Python's bit count;
@@ -32,8 +32,8 @@ def test_census_bit_by_bit_and_invariance():
     for y in range(H):
         for x in range(W):
             bits, b = 0, 0
-            for dy in range(-2, 3):
-                for dx in range(-2, 3):
+            for dy in range(-3, 4):
+                for dx in range(-4, 5):
                     if dx == 0 and dy == 0:
                         continue
                     yy, xx = min(max(y + dy, 0), H - 1), min(max(x + dx, 0), W - 1)
@@ -44,6 +44,7 @@ def test_census_bit_by_bit_and_invariance():
     J = (I.astype(np.float64) ** 2 * 0.7 + 0.2 * I + 0.05).astype(np.float32)  # increasing on [0, 1]
     assert np.array_equal(S.census(J), sig)
     assert np.all(S.census(np.full((5, 6), 0.3, np.float32)) == 0)
+    assert S.BITS == 62
 
 
 def test_hamming_zero_at_the_true_shift():
@@ -54,10 +55,10 @@ def test_hamming_zero_at_the_true_shift():
     IL[:, shift:] = IR[:, :-shift]           # I_L(x + shift) = I_R(x)
     IL[:, :shift] = rng.random((12, shift))
     h = S.hamming_volume(S.census(IL), S.census(IR), 16)
-    inner = (slice(2, -2), slice(2 + 0, 40 - shift - 2))
+    inner = (slice(3, -3), slice(4, 40 - shift - 4))
     assert np.all(h[shift][inner] == 0)
     assert np.all(h[:, :, -1][1:] == S.BITS)  # off the image for delta >= 1 at the last column
-    x = rng.integers(0, 1 << 24, size=50, dtype=np.uint32)
+    x = rng.integers(0, 1 << 62, size=50, dtype=np.uint64)
     assert np.array_equal(S.popcount(x), [bin(int(v)).count("1") for v in x])
 
 
@@ -96,7 +97,7 @@ def test_diffusion_tensor_eigenpairs():
 
 def test_assign_limits():
     rng = np.random.default_rng(4)
-    h = rng.integers(0, 25, size=(20, 5, 6))
+    h = rng.integers(0, S.BITS + 1, size=(20, 5, 6))
     a = S.assign(h, rng.random((5, 6)) * 19, 0.5, np.inf)
     np.testing.assert_array_equal(a, np.argmin(h, axis=0))
     d = np.array([[3.2, 7.5, 0.49, 12.51, 18.0]])
@@ -175,7 +176,7 @@ def test_integer_shift_is_recovered():
     IL = smooth_texture(rng, (24, 64))
     IL[:, shift:] = IR[:, :-shift]
     d = S.estimate(IL, IR, S.StereoParams(max_disp=24))
-    inner = np.abs(d[3:-3, 3:64 - shift - 3] - shift)
+    inner = np.abs(d[4:-4, 5:64 - shift - 5] - shift)
     assert np.median(inner) < 0.01 and (inner < 0.05).mean() > 0.99, (np.median(inner), (inner < 0.05).mean())
 
 
@@ -185,4 +186,4 @@ def test_synthetic_street_pair_against_ground_truth():
     d = S.estimate(IL, IR, S.StereoParams(max_disp=32))
     v = dt > 0
     err = np.abs(d - dt)[v]
-    assert np.median(err) < 0.02 and (err > 3).mean() < 0.06, (np.median(err), (err > 3).mean())
+    assert np.median(err) < 0.02 and (err > 3).mean() < 0.03, (np.median(err), (err > 3).mean())
