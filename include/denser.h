@@ -238,8 +238,9 @@ int denser_disparity_assign(const uint64_t* sig_left, const uint64_t* sig_right,
                             int32_t height, int32_t max_disp, float lambda, double theta,
                             const float* d, float* a, void* stream);
 
-/* `iters` primal-dual iterations of the d-step on state float32 [12][h][w]: d, d_bar,
- * w1, w2, w_bar1, w_bar2, p1, p2, q11, q12, q21, q22 (in that plane order). */
+/* `iters` primal-dual iterations of the d-step on state float32 [24][h][w]: the first 12
+ * planes hold d, d_bar, w1, w2, w_bar1, w_bar2, p1, p2, q11, q12, q21, q22 (in that
+ * order) on entry and on return; the last 12 are working space. */
 int denser_tgv_iterate(const float* a, const float* tensor, int32_t width, int32_t height, float alpha1,
                        float alpha2, double theta, int32_t iters, float* state, void* stream);
 

@@ -545,8 +545,8 @@ int denser_tgv_iterate(const float* a, const float* T, int32_t W, int32_t H, flo
 
 size_t denser_stereo_workspace_size(int32_t W, int32_t H) {
     if (!stereo_size_ok(W, H)) return 0;
-    // sig_L, sig_R (8 bytes a pixel), tensor (3), a, state (12) float planes
-    return (size_t)W * H * (16 + 4 * 16);
+    // sig_L, sig_R (8 bytes a pixel), tensor (3), a, state (2 x 12) float planes
+    return (size_t)W * H * (16 + 4 * 28);
 }
 
 int denser_stereo_estimate(const float* IL, const float* IR, int32_t W, int32_t H, const denser_stereo_params* p,

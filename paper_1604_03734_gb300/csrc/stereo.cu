@@ -15,9 +15,9 @@
 //   * forward differences, zero across the last column / row; div = -grad^T.
 //
 // Kernels: census, tensor, assign (one thread per pixel, the row's left signatures
-// staged in shared memory), and per primal-dual iteration a dual kernel (p, q) and a
-// primal kernel (d, w and their over-relaxed copies).  All buffers are device memory
-// in planes of H x W floats (row-major).
+// staged in shared memory), and one fused kernel per primal-dual iteration (the dual
+// step on a tile and its halo in shared memory, then the primal step).  All buffers are
+// device memory in planes of H x W floats (row-major).
 #include "common.cuh"
 
 namespace denser {
@@ -103,71 +103,97 @@ __global__ void __launch_bounds__(128) assign_kernel(const unsigned long long* _
 // State planes of the d-step.
 enum Plane { kD = 0, kDb, kW1, kW2, kWb1, kWb2, kP1, kP2, kQ11, kQ12, kQ21, kQ22, kPlanes };
 
-// Dual step: p <- P_alpha1(p + sigma (T grad d_bar - w_bar)), q <- P_alpha2(q + sigma grad w_bar).
-__global__ void tgv_dual_kernel(float* __restrict__ S, const float* __restrict__ T, int W, int H, float sigma,
-                                float alpha1, float alpha2) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const size_t n = (size_t)W * H, i = (size_t)y * W + x;
-    const bool hx = x + 1 < W, hy = y + 1 < H;
-    const float* db = S + kDb * n;
-    const float* wb1 = S + kWb1 * n;
-    const float* wb2 = S + kWb2 * n;
-    const float gx = hx ? db[i + 1] - db[i] : 0.0f, gy = hy ? db[i + W] - db[i] : 0.0f;
-    const float t00 = T[i], t01 = T[n + i], t11 = T[2 * n + i];
-    float p1 = S[kP1 * n + i] + sigma * ((t00 * gx + t01 * gy) - wb1[i]);
-    float p2 = S[kP2 * n + i] + sigma * ((t01 * gx + t11 * gy) - wb2[i]);
-    const float sp = fmaxf(1.0f, sqrtf(p1 * p1 + p2 * p2) / alpha1);
-    S[kP1 * n + i] = p1 / sp;
-    S[kP2 * n + i] = p2 / sp;
-    const float g11 = hx ? wb1[i + 1] - wb1[i] : 0.0f, g12 = hy ? wb1[i + W] - wb1[i] : 0.0f;
-    const float g21 = hx ? wb2[i + 1] - wb2[i] : 0.0f, g22 = hy ? wb2[i + W] - wb2[i] : 0.0f;
-    float q11 = S[kQ11 * n + i] + sigma * g11, q12 = S[kQ12 * n + i] + sigma * g12;
-    float q21 = S[kQ21 * n + i] + sigma * g21, q22 = S[kQ22 * n + i] + sigma * g22;
-    const float sq = fmaxf(1.0f, sqrtf(q11 * q11 + q12 * q12 + q21 * q21 + q22 * q22) / alpha2);
-    S[kQ11 * n + i] = q11 / sq;
-    S[kQ12 * n + i] = q12 / sq;
-    S[kQ21 * n + i] = q21 / sq;
-    S[kQ22 * n + i] = q22 / sq;
-}
-
 // (div v)(x, y) of a field v given at x - 1, x (for the x part) and y - 1, y.
 __device__ __forceinline__ float div_x(int x, int W, float v, float vm) {
     return (x == 0 ? v : (x == W - 1 ? -vm : v - vm));
 }
 
-// Primal step: d <- prox(d + tau div(T p)), w <- w + tau (p + div q); over-relaxation.
-__global__ void tgv_primal_kernel(float* __restrict__ S, const float* __restrict__ T, const float* __restrict__ a,
-                                  int W, int H, float tau, float tau_theta) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const size_t n = (size_t)W * H, i = (size_t)y * W + x;
-    const float* P1 = S + kP1 * n;
-    const float* P2 = S + kP2 * n;
-    // T p at the pixel and its -x, -y neighbours (T is symmetric)
-    const float tp1 = T[i] * P1[i] + T[n + i] * P2[i];
-    const float tp2 = T[n + i] * P1[i] + T[2 * n + i] * P2[i];
-    float tp1m = 0.0f, tp2m = 0.0f;
-    if (x > 0) tp1m = T[i - 1] * P1[i - 1] + T[n + i - 1] * P2[i - 1];
-    if (y > 0) tp2m = T[n + i - W] * P1[i - W] + T[2 * n + i - W] * P2[i - W];
-    const float divTp = div_x(x, W, tp1, tp1m) + div_x(y, H, tp2, tp2m);
-    const float d_old = S[kD * n + i];
+// One primal-dual iteration in one kernel.  A 32 x 8 tile stages d_bar and w_bar on
+// its region plus a halo (-1 .. +1), takes the dual step on the tile and its -x / -y
+// halo (the halo's duals are recomputed, identically, by the neighbouring tiles that
+// own them), then the primal step on the tile.  Neighbours are read from Si and every
+// plane written to So, so the call ping-pongs two state copies.
+constexpr int kTX = 32, kTY = 8;
+__global__ void __launch_bounds__(256) tgv_fused_kernel(const float* __restrict__ Si, float* __restrict__ So,
+                                                        const float* __restrict__ T, const float* __restrict__ a,
+                                                        int W, int H, float sigma, float tau, float tau_theta,
+                                                        float alpha1, float alpha2) {
+    __shared__ float sdb[kTY + 2][kTX + 2], sw1[kTY + 2][kTX + 2], sw2[kTY + 2][kTX + 2];
+    __shared__ float st0[kTY + 1][kTX + 1], st1[kTY + 1][kTX + 1], st2[kTY + 1][kTX + 1];
+    __shared__ float sp1[kTY + 1][kTX + 1], sp2[kTY + 1][kTX + 1];
+    __shared__ float sq11[kTY + 1][kTX + 1], sq12[kTY + 1][kTX + 1], sq21[kTY + 1][kTX + 1], sq22[kTY + 1][kTX + 1];
+    const size_t n = (size_t)W * H;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, tid = threadIdx.x;
+    // d_bar, w_bar on [x0 - 1, x0 + kTX] x [y0 - 1, y0 + kTY]
+    for (int k = tid; k < (kTY + 2) * (kTX + 2); k += 256) {
+        const int ry = k / (kTX + 2), rx = k % (kTX + 2);
+        const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
+        float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const size_t i = (size_t)gy * W + gx;
+            v0 = Si[kDb * n + i], v1 = Si[kWb1 * n + i], v2 = Si[kWb2 * n + i];
+        }
+        sdb[ry][rx] = v0, sw1[ry][rx] = v1, sw2[ry][rx] = v2;
+    }
+    __syncthreads();
+    // dual step on [x0 - 1, x0 + kTX - 1] x [y0 - 1, y0 + kTY - 1]
+    for (int k = tid; k < (kTY + 1) * (kTX + 1); k += 256) {
+        const int ry = k / (kTX + 1), rx = k % (kTX + 1);
+        const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
+        float t0 = 1.0f, t1 = 0.0f, t2 = 1.0f, p1 = 0.0f, p2 = 0.0f, q11 = 0.0f, q12 = 0.0f, q21 = 0.0f, q22 = 0.0f;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const size_t i = (size_t)gy * W + gx;
+            const bool hx = gx + 1 < W, hy = gy + 1 < H;
+            const float db = sdb[ry][rx];
+            const float gxd = hx ? sdb[ry][rx + 1] - db : 0.0f, gyd = hy ? sdb[ry + 1][rx] - db : 0.0f;
+            t0 = T[i], t1 = T[n + i], t2 = T[2 * n + i];
+            p1 = Si[kP1 * n + i] + sigma * ((t0 * gxd + t1 * gyd) - sw1[ry][rx]);
+            p2 = Si[kP2 * n + i] + sigma * ((t1 * gxd + t2 * gyd) - sw2[ry][rx]);
+            const float sp = fmaxf(1.0f, sqrtf(p1 * p1 + p2 * p2) / alpha1);
+            p1 /= sp, p2 /= sp;
+            const float w1 = sw1[ry][rx], w2 = sw2[ry][rx];
+            const float g11 = hx ? sw1[ry][rx + 1] - w1 : 0.0f, g12 = hy ? sw1[ry + 1][rx] - w1 : 0.0f;
+            const float g21 = hx ? sw2[ry][rx + 1] - w2 : 0.0f, g22 = hy ? sw2[ry + 1][rx] - w2 : 0.0f;
+            q11 = Si[kQ11 * n + i] + sigma * g11, q12 = Si[kQ12 * n + i] + sigma * g12;
+            q21 = Si[kQ21 * n + i] + sigma * g21, q22 = Si[kQ22 * n + i] + sigma * g22;
+            const float sq = fmaxf(1.0f, sqrtf(q11 * q11 + q12 * q12 + q21 * q21 + q22 * q22) / alpha2);
+            q11 /= sq, q12 /= sq, q21 /= sq, q22 /= sq;
+        }
+        st0[ry][rx] = t0, st1[ry][rx] = t1, st2[ry][rx] = t2;
+        sp1[ry][rx] = p1, sp2[ry][rx] = p2;
+        sq11[ry][rx] = q11, sq12[ry][rx] = q12, sq21[ry][rx] = q21, sq22[ry][rx] = q22;
+    }
+    __syncthreads();
+    // primal step on the tile
+    const int rx = (tid & (kTX - 1)) + 1, ry = tid / kTX + 1;
+    const int gx = x0 + rx - 1, gy = y0 + ry - 1;
+    if (gx >= W || gy >= H) return;
+    const size_t i = (size_t)gy * W + gx;
+    const float tp1 = st0[ry][rx] * sp1[ry][rx] + st1[ry][rx] * sp2[ry][rx];
+    const float tp2 = st1[ry][rx] * sp1[ry][rx] + st2[ry][rx] * sp2[ry][rx];
+    const float tp1m = gx > 0 ? st0[ry][rx - 1] * sp1[ry][rx - 1] + st1[ry][rx - 1] * sp2[ry][rx - 1] : 0.0f;
+    const float tp2m = gy > 0 ? st1[ry - 1][rx] * sp1[ry - 1][rx] + st2[ry - 1][rx] * sp2[ry - 1][rx] : 0.0f;
+    const float divTp = div_x(gx, W, tp1, tp1m) + div_x(gy, H, tp2, tp2m);
+    const float d_old = Si[kD * n + i];
     const float d_new = (d_old + tau * divTp + tau_theta * a[i]) / (1.0f + tau_theta);
-    // div q per component (q[i][0] pairs with d/dx, q[i][1] with d/dy)
-    const float* Q11 = S + kQ11 * n;
-    const float* Q12 = S + kQ12 * n;
-    const float* Q21 = S + kQ21 * n;
-    const float* Q22 = S + kQ22 * n;
-    const float dq1 = div_x(x, W, Q11[i], x > 0 ? Q11[i - 1] : 0.0f) + div_x(y, H, Q12[i], y > 0 ? Q12[i - W] : 0.0f);
-    const float dq2 = div_x(x, W, Q21[i], x > 0 ? Q21[i - 1] : 0.0f) + div_x(y, H, Q22[i], y > 0 ? Q22[i - W] : 0.0f);
-    const float w1o = S[kW1 * n + i], w2o = S[kW2 * n + i];
-    const float w1 = w1o + tau * (P1[i] + dq1), w2 = w2o + tau * (P2[i] + dq2);
-    S[kD * n + i] = d_new;
-    S[kDb * n + i] = 2.0f * d_new - d_old;
-    S[kW1 * n + i] = w1;
-    S[kW2 * n + i] = w2;
-    S[kWb1 * n + i] = 2.0f * w1 - w1o;
-    S[kWb2 * n + i] = 2.0f * w2 - w2o;
+    const float dq1 = div_x(gx, W, sq11[ry][rx], gx > 0 ? sq11[ry][rx - 1] : 0.0f) +
+                      div_x(gy, H, sq12[ry][rx], gy > 0 ? sq12[ry - 1][rx] : 0.0f);
+    const float dq2 = div_x(gx, W, sq21[ry][rx], gx > 0 ? sq21[ry][rx - 1] : 0.0f) +
+                      div_x(gy, H, sq22[ry][rx], gy > 0 ? sq22[ry - 1][rx] : 0.0f);
+    const float w1o = Si[kW1 * n + i], w2o = Si[kW2 * n + i];
+    const float w1 = w1o + tau * (sp1[ry][rx] + dq1), w2 = w2o + tau * (sp2[ry][rx] + dq2);
+    So[kD * n + i] = d_new;
+    So[kDb * n + i] = 2.0f * d_new - d_old;
+    So[kW1 * n + i] = w1;
+    So[kW2 * n + i] = w2;
+    So[kWb1 * n + i] = 2.0f * w1 - w1o;
+    So[kWb2 * n + i] = 2.0f * w2 - w2o;
+    So[kP1 * n + i] = sp1[ry][rx];
+    So[kP2 * n + i] = sp2[ry][rx];
+    So[kQ11 * n + i] = sq11[ry][rx];
+    So[kQ12 * n + i] = sq12[ry][rx];
+    So[kQ21 * n + i] = sq21[ry][rx];
+    So[kQ22 * n + i] = sq22[ry][rx];
 }
 
 __global__ void init_state_kernel(float* __restrict__ S, const float* __restrict__ d0, size_t n) {
@@ -211,13 +237,23 @@ int stereo_assign(const unsigned long long* sigL, const unsigned long long* sigR
     return cudaGetLastError() == cudaSuccess ? DENSER_OK : DENSER_ERR_CUDA;
 }
 
+// state: 2 x 12 planes; the first copy holds the state on entry and on return, the
+// second is the ping-pong partner of the fused kernel.
 int stereo_tgv(const float* a, const float* T, int W, int H, float alpha1, float alpha2, double theta, int iters,
                float* state, cudaStream_t s) {
     const float tau = (float)(1.0 / sqrt(12.0));
-    const dim3 grid((W + 127) / 128, H);
+    const size_t plane = (size_t)W * H;
+    float* A = state;
+    float* B = state + kPlanes * plane;
+    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
     for (int k = 0; k < iters; ++k) {
-        tgv_dual_kernel<<<grid, 128, 0, s>>>(state, T, W, H, tau, alpha1, alpha2);
-        tgv_primal_kernel<<<grid, 128, 0, s>>>(state, T, a, W, H, tau, (float)(tau / theta));
+        const bool even = (k & 1) == 0;
+        tgv_fused_kernel<<<grid, 256, 0, s>>>(even ? A : B, even ? B : A, T, a, W, H, tau, tau, (float)(tau / theta),
+                                              alpha1, alpha2);
+    }
+    if (iters & 1) {
+        if (cudaMemcpyAsync(A, B, kPlanes * plane * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return DENSER_ERR_CUDA;
     }
     return cudaGetLastError() == cudaSuccess ? DENSER_OK : DENSER_ERR_CUDA;
 }

@@ -81,10 +81,12 @@ def test_tgv_iterations(tiny_pair):
     Tref = S.diffusion_tensor(IR, 4.0, 1.0)
     st = S.TGVState(a)
     S.tgv_iterate(st, a, Tref, 1.0, 1.0, 5.0, 200)
-    state = torch.zeros((12,) + IR.shape, device="cuda")
+    state = torch.zeros((24,) + IR.shape, device="cuda")
     state[0] = dev(a)
     state[1] = dev(a)
-    N.denser_tgv_iterate(dev(a), T, 1.0, 5.0, 1.0, 200, state)
+    N.denser_tgv_iterate(dev(a), T, 1.0, 5.0, 1.0, 150, state)
+    N.denser_tgv_iterate(dev(a), T, 1.0, 5.0, 1.0, 49, state)  # an odd count ends in the first copy too
+    N.denser_tgv_iterate(dev(a), T, 1.0, 5.0, 1.0, 1, state)
     got = state.cpu().numpy().astype(np.float64)
     scale = np.abs(a).max()
     assert np.max(np.abs(got[0] - st.d)) <= 1e-4 * scale
