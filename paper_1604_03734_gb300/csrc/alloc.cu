@@ -125,6 +125,101 @@ __device__ inline void warp_insert(const DeviceMap& m, const RayKeys& rk, int la
     }
 }
 
+// Certified floor of axis coordinate q = fma(z, D, tf) of band sample nf (z = fma(nf, h,
+// d), exactly as the per-sample path evaluates it); *ok is cleared when the bound e does
+// not decide the floor.
+__device__ __forceinline__ int band_floor(float dv, float nf, float hf, float D, float tf, float e, bool* ok) {
+    const float q = fmaf(fmaf(nf, hf, dv), D, tf);
+    const float tq = __fadd_rn(q, 12582912.0f);  // nearest integer + 1.5 2^23
+    const float nq = tq - 12582912.0f;
+    const bool down = nq > q;
+    const float fr = q - (down ? nq - 1.0f : nq);  // q - floor(q), exact
+    *ok = *ok && fr >= e && 1.0f - fr > e;
+    return __float_as_int(tq) - 0x4B400000 - (down ? 1 : 0);
+}
+
+__device__ __forceinline__ void push_key(const DeviceMap& m, RayKeys& rk, unsigned long long key) {
+    if (rk.count == 4) {  // more keys than registers: insert what is held (divergent, rare)
+        hash_insert(m, rk.k0), hash_insert(m, rk.k1), hash_insert(m, rk.k2), hash_insert(m, rk.k3);
+        rk.count = 0;
+    }
+    rk.push(key);
+}
+
+// The distinct block keys of a ray's band without visiting every sample.  The real
+// coordinate q is linear in the sample index n, so each axis's floors are monotone along
+// the band: the floors at both ends, and for each axis that changes the first sample of
+// each new floor (estimated from the line, then confirmed by certified floors on both
+// sides), give every key in sample order.  Returns false, having pushed nothing, when a
+// floor is not certified, the nearest sample is not certainly in front of the camera, or
+// an axis changes more than twice; the per-sample path then takes the ray.
+__device__ bool band_keys_by_events(const AllocArgs& a, float dv, const float* D, const float* e, float ez,
+                                    const DeviceMap& m, RayKeys& rk, bool* range_err) {
+    const int N = a.N;
+    if (!(fmaf((float)(-N), a.hf, dv) > ez)) return false;
+    bool ok = true;
+    int klo[3], khi[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        klo[r] = band_floor(dv, (float)(-N), a.hf, D[r], a.tf[r], e[r], &ok);
+        khi[r] = band_floor(dv, (float)N, a.hf, D[r], a.tf[r], e[r], &ok);
+    }
+    if (!ok) return false;
+    int ev_n[6], ev_r[6], ev_v[6];
+    int ne = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int span = khi[r] - klo[r];
+        if (span == 0) continue;
+        if (span > 2 || span < -2) return false;
+        const int step = span > 0 ? 1 : -1;
+        const float q0 = fmaf(dv, D[r], a.tf[r]);
+        const float slope = a.hf * D[r];
+        for (int v = klo[r] + step; v != khi[r] + step; v += step) {
+            // increasing: the first n with q >= v; decreasing: the first n with q < v + 1
+            const float est = ((step > 0 ? (float)v : (float)(v + 1)) - q0) / slope;
+            int nc = step > 0 ? (int)ceilf(fminf(fmaxf(est, -1.0e6f), 1.0e6f))
+                               : (int)floorf(fminf(fmaxf(est, -1.0e6f), 1.0e6f)) + 1;
+            nc = min(max(nc, -N + 1), N);
+            for (int tries = 0;; ++tries) {
+                bool ok2 = true;
+                const int fa = band_floor(dv, (float)(nc - 1), a.hf, D[r], a.tf[r], e[r], &ok2);
+                const int fb = band_floor(dv, (float)nc, a.hf, D[r], a.tf[r], e[r], &ok2);
+                if (!ok2 || tries > 2) return false;
+                const bool at_b = step > 0 ? fb >= v : fb <= v;
+                const bool at_a = step > 0 ? fa >= v : fa <= v;
+                if (at_b && !at_a) break;
+                if (!at_b) {
+                    if (nc >= N) return false;
+                    ++nc;
+                } else {
+                    if (nc <= -N + 1) return false;
+                    --nc;
+                }
+            }
+            ev_n[ne] = nc, ev_r[ne] = r, ev_v[ne] = v;
+            ++ne;
+        }
+    }
+    // events in sample order (insertion sort of at most six)
+    for (int i = 1; i < ne; ++i)
+        for (int j = i; j > 0 && ev_n[j - 1] > ev_n[j]; --j) {
+            const int tn = ev_n[j], tr = ev_r[j], tv = ev_v[j];
+            ev_n[j] = ev_n[j - 1], ev_r[j] = ev_r[j - 1], ev_v[j] = ev_v[j - 1];
+            ev_n[j - 1] = tn, ev_r[j - 1] = tr, ev_v[j - 1] = tv;
+        }
+    int k[3] = {klo[0], klo[1], klo[2]};
+    for (int i = 0;;) {
+        const int b0 = a.Ti[0] + k[0], b1 = a.Ti[1] + k[1], b2 = a.Ti[2] + k[2];
+        if (key_in_range(a.seg, b0, b1, b2)) push_key(m, rk, pack_key(a.seg, b0, b1, b2));
+        else *range_err = true;
+        if (i >= ne) break;
+        const int n = ev_n[i];
+        for (; i < ne && ev_n[i] == n; ++i) k[ev_r[i]] = ev_v[i];
+    }
+    return true;
+}
+
 // Keys of every valid pixel's band samples (reading R1), inserted into the hash.
 //
 // The key of a sample is floor(t/bs + z D) per axis, D = R (u/fx, v/fy, 1) / bs the
@@ -143,11 +238,13 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
     const float eps = 9.53674316e-7f;  // 2^-20
     const float kMagic = 12582912.0f;  // 1.5 2^23: v + kMagic holds the integer nearest v for |v| < 2^22
     bool range_err = false;
+    float dmax = 0.0f;  // largest valid depth seen by this thread
     // The loop bound is warp-uniform so every lane reaches the warp collectives.
     for (int base = blockIdx.x * blockDim.x; base < npix; base += gridDim.x * blockDim.x) {
         const int pix = base + (int)threadIdx.x;
         float dv = pix < npix ? __ldg(depth + pix) : 0.0f;
         const bool valid = pix < npix && isfinite(dv) && dv > 0.0f;
+        if (valid) dmax = fmaxf(dmax, dv);
         const int y = (int)__umul64hi((unsigned long long)(unsigned)pix, a.w_magic), x = pix - y * a.W;
         float D[3] = {0.0f, 0.0f, 0.0f}, e[3] = {0.0f, 0.0f, 0.0f};
         float ez = 0.0f;
@@ -170,12 +267,14 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
             }
         }
         // the distinct block keys of this ray's band samples, in sample order (consecutive
-        // samples mostly share a block), inserted a warp round at a time once collected
+        // samples mostly share a block), inserted a warp round at a time once collected;
+        // first from the band's ends and floor changes, else sample by sample
         RayKeys rk;
+        const bool done = valid && fast && band_keys_by_events(a, dv, D, e, ez, m, rk, &range_err);
         unsigned long long last = kEmptyKey;
         int l0 = INT_MIN, l1 = 0, l2 = 0;  // last certified floor triple (INT_MIN: none)
         float nf = (float)(-a.N);
-        for (int n = -a.N; valid && n <= a.N; ++n, nf += 1.0f) {
+        for (int n = -a.N; valid && !done && n <= a.N; ++n, nf += 1.0f) {
             unsigned long long key = kEmptyKey;
             bool decided = false;
             if (fast) {
@@ -213,15 +312,13 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
             }
             if (key == kEmptyKey || key == last) continue;
             last = key;
-            if (rk.count == 4) {  // a very oblique ray: insert what it holds (divergent, rare)
-                hash_insert(m, rk.k0), hash_insert(m, rk.k1), hash_insert(m, rk.k2), hash_insert(m, rk.k3);
-                rk.count = 0;
-            }
-            rk.push(key);
+            push_key(m, rk, key);
         }
         warp_insert(m, rk, lane);
     }
     if (range_err) report(m.counters, kErrRange);
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if (lane == 0 && dmax > 0.0f) atomicMax(m.counters + kDepthMaxBits, __float_as_int(dmax));
 }
 
 struct LaserAllocArgs {
@@ -541,6 +638,9 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
     a.w_magic = ~0ull / (unsigned long long)a.W + 1ull;
     a.seg = segment;
     const int npix = a.W * a.H;
+    // the fusion of the same map reads the visible count and the largest valid depth
+    // that this pass records (zeroed first)
+    cudaMemsetAsync(c->d.counters + kNumVisible, 0, 2 * sizeof(int32_t), s);
     alloc_keys_kernel<<<grid_for(c->sm_count, npix, 256, 8), 256, 0, s>>>(depth, a, c->d);
     c->launches += 1;
     return finish_alloc(c, s);

@@ -445,7 +445,7 @@ int denser_integrate(denser_ctx* c, const float* depth, const denser_intrinsics*
         int rc = stage_depth(c, depth, (size_t)K->width * K->height * 4, s, &dd, &slot);
         if (rc) return rc;
         rc = launch_alloc(c, dd, K, T_gc, segment, s);
-        if (!rc) rc = launch_fuse(c, dd, K, T_gc, segment, s);
+        if (!rc) rc = launch_fuse(c, dd, K, T_gc, segment, s, true);
         const int rr = release_depth(c, slot, s);
         if (rc || (rc = rr)) return rc;
         if (n_new_out) {

@@ -185,8 +185,10 @@ namespace denser {
 // Launchers implemented in the .cu files (all enqueue on `s`).
 int launch_alloc(denser_ctx* c, const float* depth_dev, const denser_intrinsics* K, const double* T,
                  int32_t segment, cudaStream_t s);
+// depth_max_ready: the preceding allocation of the same depth map already reset the
+// visible count and recorded the largest valid depth (denser_integrate).
 int launch_fuse(denser_ctx* c, const float* depth_dev, const denser_intrinsics* K, const double* T,
-                int32_t segment, cudaStream_t s);
+                int32_t segment, cudaStream_t s, bool depth_max_ready = false);
 int launch_load_blocks(denser_ctx* c, const int32_t* coords_dev, int64_t n, int64_t base, cudaStream_t s);
 int launch_prepare_regularize(denser_ctx* c, int64_t n_blocks, bool rebuild_nbr, cudaStream_t s);
 int launch_sweep(denser_ctx* c, int64_t n_blocks, cudaStream_t s);

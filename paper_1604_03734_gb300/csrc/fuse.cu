@@ -30,6 +30,8 @@ struct FuseArgs {
     double radius;       // bounding-sphere radius of a block's voxel centres, padded
     float M[9];          // s R^T: camera-frame step per local voxel index (float32)
     float fxf, fyf, cxf, cyf, muf, sf, Wf, Hf;
+    float Rif[9], tif[3];  // R^T and -R^T t as float32 (the culling test)
+    float planef[4][3], tabs;  // side planes as float32; |t|_1 of -R^T t
     int W, H, seg;
 };
 
@@ -80,7 +82,7 @@ __global__ void cull_kernel(DeviceMap m, FuseArgs a) {
     const int nb = m.counters[kNumBlocks];
     const int dbits = m.counters[kDepthMaxBits];
     if (dbits == 0) return;  // no valid pixel: nothing can change
-    const double far = (double)__int_as_float(dbits) + a.mu;
+    const float farf = (float)((double)__int_as_float(dbits) + a.mu) * (1.0f + 1.0e-6f) + 1.0e-6f;
     const int lane = threadIdx.x & 31;
     // warp-uniform loop bound: every lane reaches the ballot
     for (int base = blockIdx.x * blockDim.x; base < nb; base += gridDim.x * blockDim.x) {
@@ -90,14 +92,22 @@ __global__ void cull_kernel(DeviceMap m, FuseArgs a) {
         if (b < nb) {
             const int4 k = reinterpret_cast<const int4*>(m.coords)[b];
             if (k.x == a.seg) {
-                // centre of the block's voxel centres: voxel index 8 b + 3.5 -> (8 b + 4) s
-                double c[3];
-                to_camera(a, (8.0 * k.y + 4.0) * a.s, (8.0 * k.z + 4.0) * a.s, (8.0 * k.w + 4.0) * a.s, c);
-                const double r = a.radius;
-                keep = c[2] + r >= 0.0 && c[2] - r <= far;  // not all behind, not all beyond d + mu
+                // centre of the block's voxel centres: voxel index 8 b + 3.5 -> (8 b + 4) s.
+                // The test only skips blocks that no voxel of can be updated, so float32
+                // with a margin is enough: the float32 centre and plane distances are
+                // within 2^-21 (|g|_1 + |t|_1 + 1) of the exact ones, the margin is twice that.
+                const float gx = (float)(8 * k.y + 4) * a.sf, gy = (float)(8 * k.z + 4) * a.sf,
+                            gz = (float)(8 * k.w + 4) * a.sf;
+                float c[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    c[r] = fmaf(a.Rif[3 * r], gx, fmaf(a.Rif[3 * r + 1], gy, fmaf(a.Rif[3 * r + 2], gz, a.tif[r])));
+                const float r = (float)a.radius +
+                                9.53674316e-7f * (fabsf(gx) + fabsf(gy) + fabsf(gz) + a.tabs + 1.0f);
+                keep = c[2] + r >= 0.0f && c[2] - r <= farf;  // not all behind, not all beyond d + mu
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    keep &= a.plane[q][0] * c[0] + a.plane[q][1] * c[1] + a.plane[q][2] * c[2] >= -r;
+                    keep &= fmaf(a.planef[q][0], c[0], fmaf(a.planef[q][1], c[1], a.planef[q][2] * c[2])) >= -r;
                 if (keep) {
                     double c0[3];
                     to_camera(a, __dmul_rn(__dadd_rn((double)(8 * k.y), 0.5), a.s),
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
 }  // namespace
 
 int launch_fuse(denser_ctx* c, const float* depth, const denser_intrinsics* K, const double* T, int32_t segment,
-                cudaStream_t s) {
+                cudaStream_t s, bool depth_max_ready) {
     FuseArgs a;
     // inverse pose (R^T, -R^T t), each row summed left to right
     for (int r = 0; r < 3; ++r) {
@@ -283,12 +293,20 @@ int launch_fuse(denser_ctx* c, const float* depth, const denser_intrinsics* K, c
     a.fxf = (float)a.fx, a.fyf = (float)a.fy, a.cxf = (float)a.cx, a.cyf = (float)a.cy;
     a.muf = (float)a.mu, a.sf = (float)a.s;
     a.Wf = (float)a.W, a.Hf = (float)a.H;
-    cudaMemsetAsync(c->d.counters + kNumVisible, 0, 2 * sizeof(int32_t), s);
-    const int npix = a.W * a.H;
-    depth_max_kernel<<<grid_for(c->sm_count, (npix + 3) / 4, 256, 2), 256, 0, s>>>(depth, npix, c->d.counters);
+    a.tabs = 0.0f;
+    for (int e = 0; e < 9; ++e) a.Rif[e] = (float)a.Ri[e];
+    for (int e = 0; e < 3; ++e) a.tif[e] = (float)a.ti[e], a.tabs += (float)fabs(a.ti[e]);
+    for (int q = 0; q < 4; ++q)
+        for (int e = 0; e < 3; ++e) a.planef[q][e] = (float)a.plane[q][e];
+    if (!depth_max_ready) {
+        cudaMemsetAsync(c->d.counters + kNumVisible, 0, 2 * sizeof(int32_t), s);
+        const int npix = a.W * a.H;
+        depth_max_kernel<<<grid_for(c->sm_count, (npix + 3) / 4, 256, 2), 256, 0, s>>>(depth, npix, c->d.counters);
+        c->launches += 1;
+    }
     cull_kernel<<<grid_for(c->sm_count, c->d.max_blocks, 256, 4), 256, 0, s>>>(c->d, a);
     fuse_kernel<<<c->sm_count * 16, 128, 0, s>>>(depth, c->d, a);
-    c->launches += 3;
+    c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "fusion kernels");
 }
 
