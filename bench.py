@@ -422,8 +422,9 @@ def main():
                   "ms_per_depth_map": sms, "megapixels_per_s": Ws * Hs / (sms / 1e3) / 1e6,
                   "pd_bytes_per_pixel_iteration": 148,
                   "pd_algorithmic_gbs": 148.0 * Ws * Hs * pd_iters / (sms / 1e3) / 1e9,
-                  "note": "the 16 state planes (30 MB) stay in the 129 MB L2; the GB/s figure is a lower "
-                          "bound on the primal-dual kernels' rate (the whole estimate's time divides it)"}
+                  "note": "12 state planes ping-ponged (2 x 22 MB) plus tensor and a: about half the reads "
+                          "hit L2; the GB/s figure divides by the whole estimate's time, a lower bound on the "
+                          "primal-dual kernel's rate"}
         del ws, il, ir, disp
 
     cpu = None

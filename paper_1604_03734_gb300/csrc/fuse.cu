@@ -30,6 +30,7 @@ struct FuseArgs {
     double radius;       // bounding-sphere radius of a block's voxel centres, padded
     float M[9];          // s R^T: camera-frame step per local voxel index (float32)
     float fxf, fyf, cxf, cyf, muf, sf, Wf, Hf;
+    float imuf;            // 1 / mu as float32
     float Rif[9], tif[3];  // R^T and -R^T t as float32 (the culling test)
     float planef[4][3], tabs;  // side planes as float32; |t|_1 of -R^T t
     int W, H, seg;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
                         if (fabsf(us + a.muf) > eu) {
                             decided = 1;
                             upd = us >= -a.muf;
-                            ut = fminf(1.0f, us / a.muf);
+                            ut = fminf(1.0f, us * a.imuf);
                         }
                     }
                 }
@@ -249,7 +250,9 @@ __global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ dep
                                                8 * m.coords[4 * b + 3] + lz, &ut);
             if (upd) {
                 const float wn = wv[q] + 1.0f;
-                fv[q] = (ut + wv[q] * fv[q]) / wn;
+                // the running mean of Eq. 1 (f is compared with a tolerance, so the fast
+                // division's two ulps do not matter; the update decision is already taken)
+                fv[q] = __fdividef(fmaf(wv[q], fv[q], ut), wn);
                 wv[q] = wn;
                 any = true;
             }
@@ -292,6 +295,7 @@ int launch_fuse(denser_ctx* c, const float* depth, const denser_intrinsics* K, c
     for (int e = 0; e < 9; ++e) a.M[e] = (float)(a.Ri[e] * a.s);
     a.fxf = (float)a.fx, a.fyf = (float)a.fy, a.cxf = (float)a.cx, a.cyf = (float)a.cy;
     a.muf = (float)a.mu, a.sf = (float)a.s;
+    a.imuf = (float)(1.0 / a.mu);
     a.Wf = (float)a.W, a.Hf = (float)a.H;
     a.tabs = 0.0f;
     for (int e = 0; e < 9; ++e) a.Rif[e] = (float)a.Ri[e];
