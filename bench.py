@@ -127,10 +127,10 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def make_inputs(seed, frames=None):
+def make_inputs(seed, frames=None, length=100.0):
     from synth.scenes import street_scene
-    scene = street_scene(seed=seed)
-    depths = scene.depth_maps(frames)
+    scene = street_scene(seed=seed, length=length)
+    depths = scene.depth_maps(frames, workers=min(16, os.cpu_count() or 1) if length > 100.0 else 1)
     return scene, depths
 
 
@@ -192,7 +192,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="denser", choices=["denser", "reference"])
     ap.add_argument("--iters", type=int, default=200)
-    ap.add_argument("--frames", type=int, default=200)
+    ap.add_argument("--frames", type=int, default=None, help="depth maps fused per step (default: the whole street)")
+    ap.add_argument("--length", type=float, default=100.0, help="street length in metres (a pose every 0.5 m)")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default=None, help="sweep_kernel,order,ctas_per_sm,use_graph (default: the library's)")
@@ -206,6 +207,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.frames is None:
+        args.frames = int(round(args.length / 0.5))
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -222,7 +225,7 @@ def main():
     dev = torch.device("cuda", local)
 
     # inputs: each rank fuses its own street (independent problems: weak scaling)
-    scene, depths_np = make_inputs(seed=rank, frames=range(args.frames))
+    scene, depths_np = make_inputs(seed=rank, frames=range(args.frames), length=args.length)
     cam = scene.camera
     K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
     depths_host = torch.from_numpy(depths_np).pin_memory()
@@ -230,7 +233,10 @@ def main():
     poses = scene.poses[:args.frames]
     stream = torch.cuda.current_stream(dev)
 
-    m = N.DenserMap(device=local, max_blocks=1 << 17, hash_slots=1 << 20, precision=args.precision)
+    # pool and hash sized for the street: about 250 blocks per metre at 10 cm voxels
+    mb = 1 << max(17, int(np.ceil(np.log2(300 * args.length))))
+    m = N.DenserMap(device=local, max_blocks=mb, hash_slots=2 * mb if mb > (1 << 19) else 1 << 20,
+                    precision=args.precision)
     ctx = m.ctx
     if args.schedule:
         N.denser_set_schedule(ctx, *[int(v) for v in args.schedule.split(",")])
@@ -442,7 +448,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {0: "f32", 1: "f16-storage/f32", 2: "bf16-storage/f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames": args.frames, "iters": args.iters, "blocks": nb,
+        "config": {"workload": WORKLOAD if args.length == 100.0 else WORKLOAD.replace("100 m: 200", f"{args.length:g} m: {args.frames}"),
+                   "frames": args.frames, "iters": args.iters, "blocks": nb,
                    "voxels": nvox, "parallelism": f"{world} independent streets" if world > 1 else "1 GPU",
                    "l2": f"working set {bpv * nvox / 1e9:.2f} GB per sweep > 129 MB L2, no flush",
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),

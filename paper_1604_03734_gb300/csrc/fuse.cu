@@ -166,7 +166,7 @@ __device__ inline bool certified_floor(float v, float e, int* out) {
     return lo == floor_small(v + e);
 }
 
-__global__ void __launch_bounds__(128) fuse_kernel(const float* __restrict__ depth, DeviceMap m, FuseArgs a) {
+__global__ void __launch_bounds__(128, 8) fuse_kernel(const float* __restrict__ depth, DeviceMap m, FuseArgs a) {
     const int nv = m.counters[kNumVisible];
     const int t = threadIdx.x;
     const int l0 = 4 * t;

@@ -220,15 +220,26 @@ class Scene:
         d = np.where(z > 0, self.camera.fx * baseline / np.where(z > 0, z, 1.0), 0.0).astype(np.float32)
         return IL, IR, d, TR
 
-    def depth_maps(self, frames=None) -> np.ndarray:
-        """Depth maps [n, H, W] float32; frame k draws its noise from PCG64([seed, 1, k])."""
+    def depth_map(self, k: int) -> np.ndarray:
+        """Depth map of frame k; its noise comes from PCG64([seed, 1, k])."""
+        return self.render(k, np.random.Generator(np.random.PCG64([self.seed, 1, k])))
+
+    def depth_maps(self, frames=None, workers: int = 1) -> np.ndarray:
+        """Depth maps [n, H, W] float32; frame k draws its noise from PCG64([seed, 1, k]), so
+        the result does not depend on ``workers`` (> 1: that many processes, started with
+        'spawn' so that a parent which already uses a GPU is safe)."""
         n = len(self.poses)
         frames = list(range(n)) if frames is None else list(frames)
         c = self.camera
         out = np.zeros((len(frames), c.height, c.width), np.float32)
+        if workers > 1 and len(frames) > 1:
+            import multiprocessing as mp
+            with mp.get_context("spawn").Pool(workers) as pool:
+                for i, img in enumerate(pool.imap(self.depth_map, frames, chunksize=8)):
+                    out[i] = img
+            return out
         for i, k in enumerate(frames):
-            rng = np.random.Generator(np.random.PCG64([self.seed, 1, k]))
-            out[i] = self.render(k, rng)
+            out[i] = self.depth_map(k)
         return out
 
 
