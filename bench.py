@@ -184,6 +184,29 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- multi-rank
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks (timings: the job ends with its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    """x summed over all ranks (work units: every rank fuses and solves its own street)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -284,16 +307,14 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = N.denser_launch_count(ctx) - l0
-    step_ms = ev0.elapsed_time(ev1) / args.steps
+    step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
         dist.barrier()
 
     nvox = nb * 512
     updates = nvox * args.iters
-    value = updates * world / (step_ms / 1e3)
+    updates_all = sum_over_ranks(updates, world, dev)  # each rank's street has its own block count
+    value = updates_all / (step_ms / 1e3)
 
     # end to end: host depth maps (pinned) in, host results out, through the C ABI
     torch.cuda.synchronize()
@@ -306,11 +327,7 @@ def main():
         pipeline(depths_host, out_host)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)) / e2e_steps, world, dev)
     h2d = args.frames * cam.width * cam.height * 4   # each map staged once (allocation and fusion)
     d2h = nb * (16 + 512 * (4 + 4 + 1 + 4))
 
@@ -461,7 +478,7 @@ def main():
                      "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": kernel_name,
                      "peak_kind": peak_kind, "bytes_per_voxel": bpv,
                      "schedule": N.denser_get_schedule(ctx)},
-        "e2e": {"value": updates * world / (e2e_ms / 1e3), "unit": "voxel-updates/s",
+        "e2e": {"value": updates_all / (e2e_ms / 1e3), "unit": "voxel-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
