@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--frames", type=int, default=None, help="depth maps fused per step (default: the whole street)")
     ap.add_argument("--length", type=float, default=100.0, help="street length in metres (a pose every 0.5 m)")
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=16,
+                    help="depth maps per allocation + fusion launch (1: one denser_integrate call per map)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default=None, help="sweep_kernel,order,ctas_per_sm,use_graph (default: the library's)")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start time-to-gap comparison")
@@ -254,6 +256,7 @@ def main():
     depths_host = torch.from_numpy(depths_np).pin_memory()
     depths_dev = depths_host.to(dev)
     poses = scene.poses[:args.frames]
+    poses_arr = np.asarray(poses, dtype=np.float64)
     stream = torch.cuda.current_stream(dev)
 
     # pool and hash sized for the street: about 250 blocks per metre at 10 cm voxels
@@ -266,8 +269,13 @@ def main():
 
     def pipeline(depth_src, outs):
         N.denser_reset(ctx, stream)
-        for k in range(args.frames):
-            N.denser_integrate(ctx, depth_src[k], K, poses[k], 0, stream)
+        if args.batch > 1:
+            for first in range(0, args.frames, args.batch):
+                N.denser_integrate_batch(ctx, depth_src[first:first + args.batch], K,
+                                         poses_arr[first:first + args.batch], 0, stream)
+        else:
+            for k in range(args.frames):
+                N.denser_integrate(ctx, depth_src[k], K, poses[k], 0, stream)
         st = N.denser_regularize(ctx, args.iters, 0.0, 0, stream)
         N.denser_extract(ctx, outs["coords"], outs["f"], outs["w"], outs["omega"], outs["u"],
                          outs["cap"], stream)
@@ -466,7 +474,7 @@ def main():
         "dtype": {0: "f32", 1: "f16-storage/f32", 2: "bf16-storage/f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.length == 100.0 else WORKLOAD.replace("100 m: 200", f"{args.length:g} m: {args.frames}"),
-                   "frames": args.frames, "iters": args.iters, "blocks": nb,
+                   "frames": args.frames, "fusion_batch": args.batch, "iters": args.iters, "blocks": nb,
                    "voxels": nvox, "parallelism": f"{world} independent streets" if world > 1 else "1 GPU",
                    "l2": f"working set {bpv * nvox / 1e9:.2f} GB per sweep > 129 MB L2, no flush",
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),

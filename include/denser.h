@@ -174,6 +174,21 @@ int denser_fuse_depth(denser_ctx* ctx, const float* depth, const denser_intrinsi
 int denser_integrate(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
                      const double T_gc[16], int32_t segment, void* stream, int32_t* n_new_out);
 
+/* n_frames depth maps of one camera, in order: the same result as n_frames calls of
+ * denser_integrate (the same blocks, block indices, f and w, bit for bit), in one
+ * allocation pass and one fusion pass per DENSER_MAX_BATCH maps.  A block first
+ * reached by map i is indexed after every block first reached by an earlier map, as
+ * one call per map gives, and takes maps i, i+1, ... only; each voxel takes its maps
+ * in order, so the running mean of Eq. 1 sees the same operands.
+ * depths: float32 [n_frames][height][width], host or device memory (host maps are
+ * staged DENSER_MAX_BATCH at a time); T_gc: float64 [n_frames][16] in host memory.
+ * n_new_out (host, may be NULL): blocks added by the whole call; when non-NULL the
+ * call waits for the stream after each group of maps.  An error stops the call after
+ * the group it occurred in; the sticky device error is reported by denser_sync. */
+#define DENSER_MAX_BATCH 16
+int denser_integrate_batch(denser_ctx* ctx, const float* depths, int32_t n_frames, const denser_intrinsics* K,
+                           const double* T_gc, int32_t segment, void* stream, int32_t* n_new_out);
+
 /* ------------------------------------------------------------------ laser scans
  * The projective update extends to laser sensors by updating only the voxels along
  * each ray, from the sensor to mu behind the observed surface (Section III-A, after

@@ -1,15 +1,20 @@
 // Block allocation into the hashing voxel grid (Section III-A, "Fusing Data").
 //
-// One allocation call runs five kernels on the caller's stream, with every count
-// kept on the device (no host round trip):
-//   alloc_keys    one thread per pixel; the band samples of the pixel's ray give block
-//                 keys (float64, fixed operation order); warp peers with the same key
-//                 elect one leader (match.any) that inserts it by CAS into the open-
-//                 addressing table and appends it to the call's new-key list;
-//   sort_chunks   bitonic sort of the new keys, kSortChunk keys per CTA in shared memory;
+// One allocation call (one depth map, or a batch of up to kMaxBatch maps of one camera)
+// runs five kernels on the caller's stream, with every count kept on the device (no
+// host round trip):
+//   alloc_keys    one thread per pixel of every map; the band samples of the pixel's ray
+//                 give block keys (certified float32, else float64 in a fixed operation
+//                 order); warp peers with the same key elect one leader (match.any) that
+//                 inserts it by CAS into the open-addressing table, appends it to the
+//                 call's new-key list when it is new, and lowers the slot's birth (the
+//                 first map of the batch that reached the key) by an atomic min;
+//   sort_chunks   bitonic sort of the new keys by (birth, key), kSortChunk keys per CTA
+//                 in shared memory;
 //   rank_assign   global rank of each new key = its rank in its chunk plus a binary
 //                 search in every other chunk; block index = blocks so far + rank, which
-//                 makes indices independent of insertion order;
+//                 makes indices independent of insertion order and equal to those of one
+//                 call per map (that order is by map, then by key);
 //   pool_init     zero the new blocks' fields;
 //   commit        publish the new block count.
 #include <math.h>
@@ -22,35 +27,50 @@ namespace denser {
 
 namespace {
 
-struct AllocArgs {
-    double fx, fy, cx, cy;
-    double h;   // sample spacing s/2
-    double bs;  // block size 8 s
+// The pose of one depth map of the call.
+struct AllocFrame {
     double R[9];
     double t[3];
     int Ti[3];             // floor(t / bs)
     float tf[3];           // t / bs - Ti, in [0, 1)
+    float Rf[9];           // R as float32
+};
+
+struct AllocArgs {
+    double fx, fy, cx, cy;
+    double h;   // sample spacing s/2
+    double bs;  // block size 8 s
     float hf;              // h as float32
     float cx_hi, cx_lo, cy_hi, cy_lo;  // principal point as float32 hi + lo
     float nhf;             // N h as float32
     unsigned long long w_magic;  // ceil(2^64 / W): y = umulhi(pixel, w_magic) for pixel < 2^32
     float ifx, ify, ibs;   // 1/fx, 1/fy, 1/bs as float32
-    float Rf[9];           // R as float32
     int W, H, N, seg;
+    int n_frames;          // depth maps of the call, [n_frames][H][W] back to back
+    int tiles;             // 256-pixel tiles per map
+    AllocFrame fr[kMaxBatch];
 };
+
+constexpr unsigned long long kCoordMask = (1ull << (3 * kCoordBits)) - 1;  // a key without its segment
+constexpr int kBirthShift = 3 * kCoordBits;
 
 __device__ inline void report(int32_t* counters, int32_t bit) { atomicOr(counters + kErrorBits, bit); }
 
-// Inserts `key`; returns true if this call created it.
-__device__ bool hash_insert(const DeviceMap& m, unsigned long long key) {
+// Inserts `key`, reached by depth map `frame` of the call; returns true if this call
+// created it.
+__device__ bool hash_insert(const DeviceMap& m, unsigned long long key, int frame) {
     const uint32_t h = hash_key(key);
     for (int i = 0; i < kMaxProbe; ++i) {
         const uint32_t slot = (h + (uint32_t)i) & m.slot_mask;
         unsigned long long cur = __ldcg(m.hash_keys + slot);
-        if (cur == key) return false;
+        if (cur == key) {
+            atomicMin(m.hash_birth + slot, frame);
+            return false;
+        }
         if (cur == kEmptyKey) {
             cur = atomicCAS(m.hash_keys + slot, kEmptyKey, key);
             if (cur == kEmptyKey) {
+                atomicMin(m.hash_birth + slot, frame);
                 const int pos = atomicAdd(m.counters + kNumNew, 1);
                 if (pos < (int)m.max_new) {
                     m.new_keys[pos] = key;
@@ -60,7 +80,10 @@ __device__ bool hash_insert(const DeviceMap& m, unsigned long long key) {
                 }
                 return true;
             }
-            if (cur == key) return false;
+            if (cur == key) {
+                atomicMin(m.hash_birth + slot, frame);
+                return false;
+            }
         }
     }
     report(m.counters, kErrHashFull);
@@ -70,7 +93,8 @@ __device__ bool hash_insert(const DeviceMap& m, unsigned long long key) {
 // Block key of band sample n of pixel (x, y) with depth d, or kEmptyKey when z <= 0.
 // The float64 operations follow the oracle's order one by one; the _rn intrinsics keep
 // the compiler from contracting them into fused multiply-adds.
-__device__ __forceinline__ unsigned long long sample_key(const AllocArgs& a, int x, int y, double d, int n, bool* range_err) {
+__device__ __forceinline__ unsigned long long sample_key(const AllocArgs& a, const AllocFrame& fr, int x, int y, double d,
+                                                        int n, bool* range_err) {
     const double z = __dadd_rn(d, __dmul_rn((double)n, a.h));
     if (!(z > 0.0)) return kEmptyKey;
     const double uu = __dsub_rn(__dadd_rn((double)x, 0.5), a.cx);
@@ -82,8 +106,8 @@ __device__ __forceinline__ unsigned long long sample_key(const AllocArgs& a, int
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const double g = __dadd_rn(
-            __dadd_rn(__dadd_rn(__dmul_rn(a.R[3 * r + 0], X), __dmul_rn(a.R[3 * r + 1], Y)), __dmul_rn(a.R[3 * r + 2], Z)),
-            a.t[r]);
+            __dadd_rn(__dadd_rn(__dmul_rn(fr.R[3 * r + 0], X), __dmul_rn(fr.R[3 * r + 1], Y)), __dmul_rn(fr.R[3 * r + 2], Z)),
+            fr.t[r]);
         k[r] = floor(__ddiv_rn(g, a.bs));
     }
     if (!(k[0] >= -kCoordBias && k[0] < kCoordBias && k[1] >= -kCoordBias && k[1] < kCoordBias &&
@@ -113,14 +137,14 @@ struct RayKeys {
 
 // Inserts the pending keys of a warp: round after round every lane offers its next key,
 // lanes offering the same key elect one leader (match.any), and the leaders insert.
-__device__ inline void warp_insert(const DeviceMap& m, const RayKeys& rk, int lane) {
+__device__ inline void warp_insert(const DeviceMap& m, const RayKeys& rk, int lane, int frame) {
     for (int i = 0;; ++i) {
         const unsigned long long key = i < rk.count ? rk.at(i) : kEmptyKey;
         const unsigned active = __ballot_sync(0xffffffffu, key != kEmptyKey);
         if (!active) break;
         if (key != kEmptyKey) {
             const unsigned peers = __match_any_sync(active, key);
-            if (lane == __ffs(peers) - 1) hash_insert(m, key);
+            if (lane == __ffs(peers) - 1) hash_insert(m, key, frame);
         }
     }
 }
@@ -138,9 +162,10 @@ __device__ __forceinline__ int band_floor(float dv, float nf, float hf, float D,
     return __float_as_int(tq) - 0x4B400000 - (down ? 1 : 0);
 }
 
-__device__ __forceinline__ void push_key(const DeviceMap& m, RayKeys& rk, unsigned long long key) {
+__device__ __forceinline__ void push_key(const DeviceMap& m, RayKeys& rk, unsigned long long key, int frame) {
     if (rk.count == 4) {  // more keys than registers: insert what is held (divergent, rare)
-        hash_insert(m, rk.k0), hash_insert(m, rk.k1), hash_insert(m, rk.k2), hash_insert(m, rk.k3);
+        hash_insert(m, rk.k0, frame), hash_insert(m, rk.k1, frame), hash_insert(m, rk.k2, frame),
+            hash_insert(m, rk.k3, frame);
         rk.count = 0;
     }
     rk.push(key);
@@ -153,16 +178,16 @@ __device__ __forceinline__ void push_key(const DeviceMap& m, RayKeys& rk, unsign
 // sides), give every key in sample order.  Returns false, having pushed nothing, when a
 // floor is not certified, the nearest sample is not certainly in front of the camera, or
 // an axis changes more than twice; the per-sample path then takes the ray.
-__device__ bool band_keys_by_events(const AllocArgs& a, float dv, const float* D, const float* e, float ez,
-                                    const DeviceMap& m, RayKeys& rk, bool* range_err) {
+__device__ bool band_keys_by_events(const AllocArgs& a, const AllocFrame& fr, int frame, float dv, const float* D,
+                                    const float* e, float ez, const DeviceMap& m, RayKeys& rk, bool* range_err) {
     const int N = a.N;
     if (!(fmaf((float)(-N), a.hf, dv) > ez)) return false;
     bool ok = true;
     int klo[3], khi[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        klo[r] = band_floor(dv, (float)(-N), a.hf, D[r], a.tf[r], e[r], &ok);
-        khi[r] = band_floor(dv, (float)N, a.hf, D[r], a.tf[r], e[r], &ok);
+        klo[r] = band_floor(dv, (float)(-N), a.hf, D[r], fr.tf[r], e[r], &ok);
+        khi[r] = band_floor(dv, (float)N, a.hf, D[r], fr.tf[r], e[r], &ok);
     }
     if (!ok) return false;
     int ev_n[6], ev_r[6], ev_v[6];
@@ -173,7 +198,7 @@ __device__ bool band_keys_by_events(const AllocArgs& a, float dv, const float* D
         if (span == 0) continue;
         if (span > 2 || span < -2) return false;
         const int step = span > 0 ? 1 : -1;
-        const float q0 = fmaf(dv, D[r], a.tf[r]);
+        const float q0 = fmaf(dv, D[r], fr.tf[r]);
         const float slope = a.hf * D[r];
         for (int v = klo[r] + step; v != khi[r] + step; v += step) {
             // increasing: the first n with q >= v; decreasing: the first n with q < v + 1
@@ -183,8 +208,8 @@ __device__ bool band_keys_by_events(const AllocArgs& a, float dv, const float* D
             nc = min(max(nc, -N + 1), N);
             for (int tries = 0;; ++tries) {
                 bool ok2 = true;
-                const int fa = band_floor(dv, (float)(nc - 1), a.hf, D[r], a.tf[r], e[r], &ok2);
-                const int fb = band_floor(dv, (float)nc, a.hf, D[r], a.tf[r], e[r], &ok2);
+                const int fa = band_floor(dv, (float)(nc - 1), a.hf, D[r], fr.tf[r], e[r], &ok2);
+                const int fb = band_floor(dv, (float)nc, a.hf, D[r], fr.tf[r], e[r], &ok2);
                 if (!ok2 || tries > 2) return false;
                 const bool at_b = step > 0 ? fb >= v : fb <= v;
                 const bool at_a = step > 0 ? fa >= v : fa <= v;
@@ -210,8 +235,8 @@ __device__ bool band_keys_by_events(const AllocArgs& a, float dv, const float* D
         }
     int k[3] = {klo[0], klo[1], klo[2]};
     for (int i = 0;;) {
-        const int b0 = a.Ti[0] + k[0], b1 = a.Ti[1] + k[1], b2 = a.Ti[2] + k[2];
-        if (key_in_range(a.seg, b0, b1, b2)) push_key(m, rk, pack_key(a.seg, b0, b1, b2));
+        const int b0 = fr.Ti[0] + k[0], b1 = fr.Ti[1] + k[1], b2 = fr.Ti[2] + k[2];
+        if (key_in_range(a.seg, b0, b1, b2)) push_key(m, rk, pack_key(a.seg, b0, b1, b2), frame);
         else *range_err = true;
         if (i >= ne) break;
         const int n = ev_n[i];
@@ -232,17 +257,31 @@ __device__ bool band_keys_by_events(const AllocArgs& a, float dv, const float* D
 // (rounding of D, of z, of the fma and of t/bs), covered at least twice by
 //   e = 2.5 2^-21 DA (z_max + N h) + 2^-22 (q_max + 1),
 // q linear in z so that q_max = max |q| over the band's two ends.
+//
+// The grid strides over 256-pixel tiles of all the call's maps, a tile within one map,
+// so that each CTA step reads one pose.  Each map's largest valid depth goes to its
+// counter when a CTA leaves the map.
 __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict__ depth, AllocArgs a, DeviceMap m) {
     const int npix = a.W * a.H;
     const int lane = threadIdx.x & 31;
     const float eps = 9.53674316e-7f;  // 2^-20
     const float kMagic = 12582912.0f;  // 1.5 2^23: v + kMagic holds the integer nearest v for |v| < 2^22
     bool range_err = false;
-    float dmax = 0.0f;  // largest valid depth seen by this thread
-    // The loop bound is warp-uniform so every lane reaches the warp collectives.
-    for (int base = blockIdx.x * blockDim.x; base < npix; base += gridDim.x * blockDim.x) {
-        const int pix = base + (int)threadIdx.x;
-        float dv = pix < npix ? __ldg(depth + pix) : 0.0f;
+    float dmax = 0.0f;  // largest valid depth seen by this thread in map `dframe`
+    int dframe = -1;
+    const int n_tiles = a.n_frames * a.tiles;
+    // The loop bound is CTA-uniform so every lane reaches the warp collectives.
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int frame = tile / a.tiles;
+        if (frame != dframe) {
+            for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            if (lane == 0 && dmax > 0.0f) atomicMax(m.counters + kFrameDepthMax + dframe, __float_as_int(dmax));
+            dmax = 0.0f;
+            dframe = frame;
+        }
+        const AllocFrame& fr = a.fr[frame];
+        const int pix = (tile - frame * a.tiles) * 256 + (int)threadIdx.x;
+        float dv = pix < npix ? __ldg(depth + (size_t)frame * npix + pix) : 0.0f;
         const bool valid = pix < npix && isfinite(dv) && dv > 0.0f;
         if (valid) dmax = fmaxf(dmax, dv);
         const int y = (int)__umul64hi((unsigned long long)(unsigned)pix, a.w_magic), x = pix - y * a.W;
@@ -259,9 +298,9 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
             fast = true;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                D[r] = fmaf(a.Rf[3 * r], ax, fmaf(a.Rf[3 * r + 1], ay, a.Rf[3 * r + 2])) * a.ibs;
-                const float DA = (fabsf(a.Rf[3 * r] * ax) + fabsf(a.Rf[3 * r + 1] * ay) + fabsf(a.Rf[3 * r + 2])) * a.ibs;
-                const float qm = fmaxf(fabsf(fmaf(zmin, D[r], a.tf[r])), fabsf(fmaf(zmax, D[r], a.tf[r])));
+                D[r] = fmaf(fr.Rf[3 * r], ax, fmaf(fr.Rf[3 * r + 1], ay, fr.Rf[3 * r + 2])) * a.ibs;
+                const float DA = (fabsf(fr.Rf[3 * r] * ax) + fabsf(fr.Rf[3 * r + 1] * ay) + fabsf(fr.Rf[3 * r + 2])) * a.ibs;
+                const float qm = fmaxf(fabsf(fmaf(zmin, D[r], fr.tf[r])), fabsf(fmaf(zmax, D[r], fr.tf[r])));
                 fast = fast && qm < 2097152.0f;  // beyond 2^21 the float64 path reports the range
                 e[r] = fmaf(1.25f * eps, DA * (zmax + a.nhf), 0.25f * eps * (qm + 1.0f));
             }
@@ -270,7 +309,7 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
         // samples mostly share a block), inserted a warp round at a time once collected;
         // first from the band's ends and floor changes, else sample by sample
         RayKeys rk;
-        const bool done = valid && fast && band_keys_by_events(a, dv, D, e, ez, m, rk, &range_err);
+        const bool done = valid && fast && band_keys_by_events(a, fr, frame, dv, D, e, ez, m, rk, &range_err);
         unsigned long long last = kEmptyKey;
         int l0 = INT_MIN, l1 = 0, l2 = 0;  // last certified floor triple (INT_MIN: none)
         float nf = (float)(-a.N);
@@ -285,7 +324,7 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
                     int k[3];
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
-                        const float q = fmaf(z, D[r], a.tf[r]);
+                        const float q = fmaf(z, D[r], fr.tf[r]);
                         const float tq = __fadd_rn(q, kMagic);  // nearest integer n + kMagic
                         const float nq = tq - kMagic;
                         const bool down = nq > q;               // floor(q) = n - 1
@@ -296,7 +335,7 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
                     if (ok) {
                         if (k[0] == l0 && k[1] == l1 && k[2] == l2) continue;  // same block as before
                         l0 = k[0], l1 = k[1], l2 = k[2];
-                        const int b0 = a.Ti[0] + k[0], b1 = a.Ti[1] + k[1], b2 = a.Ti[2] + k[2];
+                        const int b0 = fr.Ti[0] + k[0], b1 = fr.Ti[1] + k[1], b2 = fr.Ti[2] + k[2];
                         if (!key_in_range(a.seg, b0, b1, b2)) {
                             range_err = true;
                             continue;
@@ -307,18 +346,18 @@ __global__ void __launch_bounds__(256) alloc_keys_kernel(const float* __restrict
                 }
             }
             if (!decided) {
-                key = sample_key(a, x, y, (double)dv, n, &range_err);
+                key = sample_key(a, fr, x, y, (double)dv, n, &range_err);
                 l0 = INT_MIN;
             }
             if (key == kEmptyKey || key == last) continue;
             last = key;
-            push_key(m, rk, key);
+            push_key(m, rk, key, frame);
         }
-        warp_insert(m, rk, lane);
+        warp_insert(m, rk, lane, frame);
     }
     if (range_err) report(m.counters, kErrRange);
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    if (lane == 0 && dmax > 0.0f) atomicMax(m.counters + kDepthMaxBits, __float_as_int(dmax));
+    if (lane == 0 && dmax > 0.0f) atomicMax(m.counters + kFrameDepthMax + dframe, __float_as_int(dmax));
 }
 
 struct LaserAllocArgs {
@@ -418,22 +457,21 @@ __global__ void __launch_bounds__(256) laser_keys_kernel(const float* __restrict
             }
             if (key == last) continue;
             last = key;
-            if (rk.count == 4) {
-                hash_insert(m, rk.k0), hash_insert(m, rk.k1), hash_insert(m, rk.k2), hash_insert(m, rk.k3);
-                rk.count = 0;
-            }
-            rk.push(key);
+            push_key(m, rk, key, 0);
         }
-        warp_insert(m, rk, lane);
+        warp_insert(m, rk, lane, 0);
     }
     if (range_err) report(m.counters, kErrRange);
 }
 
 // Sorts (key, val) pairs in place in chunks of kSortChunk (bitonic network in shared
 // memory over the next power of two >= the chunk's count).  *count may exceed
-// capacity; only the first `capacity` pairs exist.
+// capacity; only the first `capacity` pairs exist.  With `birth` (the allocation's new
+// keys, val = hash slot), each key's segment bits are first replaced by its slot's
+// birth, so that the keys sort by (birth, key) and are stored that way.
 __global__ void __launch_bounds__(1024) sort_chunks_kernel(unsigned long long* keys, uint32_t* vals,
-                                                           const int32_t* count, int capacity) {
+                                                           const int32_t* count, int capacity,
+                                                           const int32_t* __restrict__ birth) {
     __shared__ unsigned long long sk[kSortChunk];
     __shared__ uint32_t ss[kSortChunk];
     const int n = min(*count, capacity);
@@ -443,8 +481,14 @@ __global__ void __launch_bounds__(1024) sort_chunks_kernel(unsigned long long* k
     int size = 64;
     while (size < cnt) size <<= 1;
     for (int i = threadIdx.x; i < size; i += blockDim.x) {
-        sk[i] = i < cnt ? keys[base + i] : kEmptyKey;
-        ss[i] = i < cnt ? vals[base + i] : 0u;
+        unsigned long long k = kEmptyKey;
+        uint32_t v = 0u;
+        if (i < cnt) {
+            k = keys[base + i], v = vals[base + i];
+            if (birth) k = ((unsigned long long)birth[v] << kBirthShift) | (k & kCoordMask);
+        }
+        sk[i] = k;
+        ss[i] = v;
     }
     __syncthreads();
     for (int k = 2; k <= size; k <<= 1) {
@@ -504,13 +548,15 @@ __global__ void rank_assign_kernel(DeviceMap m) {
     const int n = min(m.counters[kNumNew], (int)m.max_new);
     const int nb = m.counters[kNumBlocks];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const unsigned long long key = m.new_keys[i];
+        // the list holds (birth, key without segment); the table holds the key itself
+        const unsigned long long sorted = m.new_keys[i];
         const long long idx = nb + global_rank(m.new_keys, n, i);
         const uint32_t slot = m.new_slots[i];
         if (idx < (long long)m.max_blocks) {
             int32_t s, x, y, z;
-            unpack_key(key, &s, &x, &y, &z);
+            unpack_key(m.hash_keys[slot], &s, &x, &y, &z);
             reinterpret_cast<int4*>(m.coords)[idx] = make_int4(s, x, y, z);
+            m.block_birth[idx] = (uint8_t)(sorted >> kBirthShift);
             m.hash_vals[slot] = (int32_t)idx;
         } else {
             m.hash_vals[slot] = -2;
@@ -610,27 +656,32 @@ ZeroRegions all_regions(denser_ctx* c, int* nreg) {
 
 int finish_alloc(denser_ctx* c, cudaStream_t s);
 
-int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, const double* T, int32_t segment,
-                 cudaStream_t s) {
+int launch_alloc(denser_ctx* c, const float* depth, int n_frames, const denser_intrinsics* K, const double* T,
+                 int32_t segment, cudaStream_t s) {
     AllocArgs a;
     a.fx = K->fx, a.fy = K->fy, a.cx = K->cx, a.cy = K->cy;
     a.h = 0.5 * c->prm.voxel_size;
     a.bs = 8.0 * c->prm.voxel_size;
-    for (int r = 0; r < 3; ++r) {
-        for (int q = 0; q < 3; ++q) a.R[3 * r + q] = T[4 * r + q];
-        a.t[r] = T[4 * r + 3];
-    }
     a.W = K->width, a.H = K->height;
     a.N = (int)ceil(c->prm.mu / a.h - 1e-9);
     a.ifx = (float)(1.0 / a.fx), a.ify = (float)(1.0 / a.fy), a.ibs = (float)(1.0 / a.bs);
     a.cx_hi = (float)a.cx, a.cx_lo = (float)(a.cx - (double)a.cx_hi);
     a.cy_hi = (float)a.cy, a.cy_lo = (float)(a.cy - (double)a.cy_hi);
-    for (int e = 0; e < 9; ++e) a.Rf[e] = (float)a.R[e];
-    for (int r = 0; r < 3; ++r) {
-        const double tb = a.t[r] / a.bs;
-        const double ti = floor(tb);
-        a.Ti[r] = (int)std::max(-2.0 * kCoordBias, std::min(2.0 * kCoordBias, ti));
-        a.tf[r] = (float)(tb - (double)a.Ti[r]);
+    a.n_frames = n_frames;
+    for (int i = 0; i < n_frames; ++i) {
+        AllocFrame& fr = a.fr[i];
+        const double* Ti = T + 16 * i;
+        for (int r = 0; r < 3; ++r) {
+            for (int q = 0; q < 3; ++q) fr.R[3 * r + q] = Ti[4 * r + q];
+            fr.t[r] = Ti[4 * r + 3];
+        }
+        for (int e = 0; e < 9; ++e) fr.Rf[e] = (float)fr.R[e];
+        for (int r = 0; r < 3; ++r) {
+            const double tb = fr.t[r] / a.bs;
+            const double ti = floor(tb);
+            fr.Ti[r] = (int)std::max(-2.0 * kCoordBias, std::min(2.0 * kCoordBias, ti));
+            fr.tf[r] = (float)(tb - (double)fr.Ti[r]);
+        }
     }
     a.hf = (float)a.h;
     a.nhf = (float)(a.N * a.h);
@@ -638,10 +689,12 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
     a.w_magic = ~0ull / (unsigned long long)a.W + 1ull;
     a.seg = segment;
     const int npix = a.W * a.H;
-    // the fusion of the same map reads the visible count and the largest valid depth
-    // that this pass records (zeroed first)
-    cudaMemsetAsync(c->d.counters + kNumVisible, 0, 2 * sizeof(int32_t), s);
-    alloc_keys_kernel<<<grid_for(c->sm_count, npix, 256, 8), 256, 0, s>>>(depth, a, c->d);
+    a.tiles = (npix + 255) / 256;
+    // the fusion of the same maps reads the visible count and the largest valid depths
+    // that this pass records (zeroed first, with the words between them)
+    cudaMemsetAsync(c->d.counters + kNumVisible, 0, (kCounterWords - kNumVisible) * sizeof(int32_t), s);
+    alloc_keys_kernel<<<grid_for(c->sm_count, (int64_t)n_frames * a.tiles * 256, 256, 8), 256, 0, s>>>(depth, a,
+                                                                                                        c->d);
     c->launches += 1;
     return finish_alloc(c, s);
 }
@@ -651,7 +704,7 @@ int launch_alloc(denser_ctx* c, const float* depth, const denser_intrinsics* K, 
 int finish_alloc(denser_ctx* c, cudaStream_t s) {
     const int chunks = (int)((c->d.max_new + kSortChunk - 1) / kSortChunk);
     sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->d.new_keys, c->d.new_slots, c->d.counters + kNumNew,
-                                               (int)c->d.max_new);
+                                               (int)c->d.max_new, c->d.hash_birth);
     rank_assign_kernel<<<grid_for(c->sm_count, c->d.max_new, 256, 4), 256, 0, s>>>(c->d);
     int nreg;
     ZeroRegions z = all_regions(c, &nreg);
@@ -708,7 +761,7 @@ int launch_block_order(denser_ctx* c, int64_t n_blocks, cudaStream_t s) {
     order_keys_kernel<<<grid_for(c->sm_count, n_blocks, 256, 8), 256, 0, s>>>(c->d.coords, cnt, c->order_keys,
                                                                               c->order_vals);
     const int chunks = (int)((n_blocks + kSortChunk - 1) / kSortChunk);
-    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->order_keys, c->order_vals, cnt, (int)c->d.max_blocks);
+    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->order_keys, c->order_vals, cnt, (int)c->d.max_blocks, nullptr);
     order_scatter_kernel<<<grid_for(c->sm_count, n_blocks, 256, 8), 256, 0, s>>>(c->order_keys, c->order_vals, cnt,
                                                                                  (int)c->d.max_blocks, c->order);
     c->launches += 3;

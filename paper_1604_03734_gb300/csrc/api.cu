@@ -211,9 +211,9 @@ int energy_now(denser_ctx* c, int64_t nb, cudaStream_t s, double* P, double* D) 
 }
 
 void free_all(denser_ctx* c) {
-    void* ptrs[] = {c->d.hash_keys, c->d.hash_vals, c->d.coords, c->d.f, c->d.w, c->d.u, c->d.ub[0], c->d.ub[1],
+    void* ptrs[] = {c->d.hash_keys, c->d.hash_vals, c->d.hash_birth, c->d.block_birth, c->d.coords, c->d.f, c->d.w, c->d.u, c->d.ub[0], c->d.ub[1],
                     c->d.p[0], c->d.p[1], c->d.omega_bits, c->d.nbr, c->d.counters, c->d.new_keys,
-                    c->d.new_slots, c->d.visible, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch,
+                    c->d.new_slots, c->d.visible, c->d.vis_org, c->d.partials, c->stage, c->omega_bytes, c->conv_scratch,
                     c->order, c->order_keys, c->order_vals, c->ctl_i, c->ctl_d, c->surf_counts,
                     c->surf_offsets, c->surf_scratch, c->surf_up, c->surf_list, c->surf_cursor};
     release_graph_loop(c);
@@ -306,11 +306,14 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->d.max_blocks = (uint32_t)mb;
     c->d.max_new = (uint32_t)max_new;
     c->d.slot_mask = p.hash_slots - 1;
+    c->d.org_frames = 1;  // grown to kMaxBatch by the first batched fusion
     struct Req {
         void** ptr;
         size_t bytes;
     } reqs[] = {{(void**)&c->d.hash_keys, (size_t)p.hash_slots * 8},
                 {(void**)&c->d.hash_vals, (size_t)p.hash_slots * 4},
+                {(void**)&c->d.hash_birth, (size_t)p.hash_slots * 4},
+                {(void**)&c->d.block_birth, mb},
                 {(void**)&c->d.coords, mb * 16},
                 {(void**)&c->d.f, nv * 4},
                 {(void**)&c->d.w, nv * 4},
@@ -321,10 +324,11 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
                 {(void**)&c->d.p[1], 3 * nv * c->elem_size},
                 {(void**)&c->d.omega_bits, mb * 64},
                 {(void**)&c->d.nbr, mb * kNeighbours * 4},
-                {(void**)&c->d.counters, kNumCounters * 4},
+                {(void**)&c->d.counters, kCounterWords * 4},
                 {(void**)&c->d.new_keys, max_new * 8},
                 {(void**)&c->d.new_slots, max_new * 4},
                 {(void**)&c->d.visible, mb * 32},
+                {(void**)&c->d.vis_org, mb * 32},
                 {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2) * 8},
                 {(void**)&c->order, mb * 4},
                 {(void**)&c->order_keys, mb * 8},
@@ -382,7 +386,9 @@ int denser_reset(denser_ctx* c, void* stream) {
             return rc;
         if ((rc = cuda_check(c, cudaMemsetAsync(c->d.hash_vals, 0xff, (size_t)c->prm.hash_slots * 4, s), "reset")))
             return rc;
-        if ((rc = cuda_check(c, cudaMemsetAsync(c->d.counters, 0, kNumCounters * 4, s), "reset"))) return rc;
+        if ((rc = cuda_check(c, cudaMemsetAsync(c->d.hash_birth, 0x7f, (size_t)c->prm.hash_slots * 4, s), "reset")))
+            return rc;
+        if ((rc = cuda_check(c, cudaMemsetAsync(c->d.counters, 0, kCounterWords * 4, s), "reset"))) return rc;
         c->cur = 0;
         c->nbr_valid_blocks = -1;
         c->order_valid_blocks = -1;
@@ -406,7 +412,7 @@ int denser_alloc_blocks(denser_ctx* c, const float* depth, const denser_intrinsi
         int slot;
         int rc = stage_depth(c, depth, (size_t)K->width * K->height * 4, s, &dd, &slot);
         if (rc) return rc;
-        rc = launch_alloc(c, dd, K, T_gc, segment, s);
+        rc = launch_alloc(c, dd, 1, K, T_gc, segment, s);
         const int rr = release_depth(c, slot, s);
         if (rc || (rc = rr)) return rc;
         if (n_new_out) {
@@ -428,7 +434,7 @@ int denser_fuse_depth(denser_ctx* c, const float* depth, const denser_intrinsics
         int slot;
         int rc = stage_depth(c, depth, (size_t)K->width * K->height * 4, s, &dd, &slot);
         if (rc) return rc;
-        rc = launch_fuse(c, dd, K, T_gc, segment, s);
+        rc = launch_fuse(c, dd, 1, K, T_gc, segment, s);
         const int rr = release_depth(c, slot, s);
         return rc ? rc : rr;
     });
@@ -444,8 +450,8 @@ int denser_integrate(denser_ctx* c, const float* depth, const denser_intrinsics*
         int slot;
         int rc = stage_depth(c, depth, (size_t)K->width * K->height * 4, s, &dd, &slot);
         if (rc) return rc;
-        rc = launch_alloc(c, dd, K, T_gc, segment, s);
-        if (!rc) rc = launch_fuse(c, dd, K, T_gc, segment, s, true);
+        rc = launch_alloc(c, dd, 1, K, T_gc, segment, s);
+        if (!rc) rc = launch_fuse(c, dd, 1, K, T_gc, segment, s, true);
         const int rr = release_depth(c, slot, s);
         if (rc || (rc = rr)) return rc;
         if (n_new_out) {
@@ -453,6 +459,38 @@ int denser_integrate(denser_ctx* c, const float* depth, const denser_intrinsics*
             *n_new_out = c->h_counters[kLastNew];
             return rc;
         }
+        return DENSER_OK;
+    });
+}
+
+int denser_integrate_batch(denser_ctx* c, const float* depths, int32_t n_frames, const denser_intrinsics* K,
+                           const double* T_gc, int32_t segment, void* stream, int32_t* n_new_out) {
+    return guarded(c, [&]() -> int {
+        if (!depths || n_frames < 1 || !T_gc || !valid_intrinsics(K) || segment < 0 || segment > kMaxSegment)
+            return set_error(c, DENSER_ERR_INVALID_ARG,
+                             "integrate_batch: bad depth maps, frame count, intrinsics, poses or segment");
+        for (int i = 0; i < n_frames; ++i)
+            if (!valid_pose(T_gc + 16 * (size_t)i))
+                return set_error(c, DENSER_ERR_INVALID_ARG, "integrate_batch: pose " + std::to_string(i) + " is not finite");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t map_floats = (size_t)K->width * K->height;
+        int64_t added = 0;
+        for (int first = 0; first < n_frames; first += kMaxBatch) {
+            const int n = std::min(kMaxBatch, n_frames - first);
+            const float* dd;
+            int slot;
+            int rc = stage_depth(c, depths + (size_t)first * map_floats, (size_t)n * map_floats * 4, s, &dd, &slot);
+            if (rc) return rc;
+            rc = launch_alloc(c, dd, n, K, T_gc + 16 * (size_t)first, segment, s);
+            if (!rc) rc = launch_fuse(c, dd, n, K, T_gc + 16 * (size_t)first, segment, s, true);
+            const int rr = release_depth(c, slot, s);
+            if (rc || (rc = rr)) return rc;
+            if (n_new_out) {
+                if ((rc = read_counters(c, s))) return rc;
+                added += c->h_counters[kLastNew];
+            }
+        }
+        if (n_new_out) *n_new_out = (int32_t)added;
         return DENSER_OK;
     });
 }

@@ -18,6 +18,7 @@ constexpr int kNeighbours = 12;
 constexpr int kMaxProbe = 512;             // linear-probe limit of the hash table
 constexpr int kSortChunk = 2048;           // keys sorted per CTA before the rank merge
 constexpr int kSweepThreads = 512;
+constexpr int kMaxBatch = 16;              // depth maps per batched allocation + fusion launch
 
 // ---------------------------------------------------------------- block keys
 // 64-bit key: bits 0-18 bx + 2^18, 19-37 by + 2^18, 38-56 bz + 2^18, 57-63 segment.
@@ -64,8 +65,9 @@ enum Counter {
     kLastNew = 2,      // blocks added by the last allocation call
     kErrorBits = 3,    // sticky error flags (ErrorBit)
     kNumVisible = 4,   // blocks selected for the running fusion call
-    kDepthMaxBits = 5, // max valid depth of the running fusion call (float bits)
-    kNumCounters = 8
+    kNumCounters = 8,  // words copied to the host
+    kFrameDepthMax = 8,  // [kMaxBatch] max valid depth per depth map of the running call (float bits)
+    kCounterWords = kFrameDepthMax + kMaxBatch
 };
 
 enum ErrorBit : int32_t {
@@ -96,6 +98,9 @@ template <> struct Store<__nv_bfloat16> {
 struct DeviceMap {
     unsigned long long* hash_keys;  // [slots]
     int32_t* hash_vals;             // [slots] block index; -1 pending, -2 rejected
+    int32_t* hash_birth;            // [slots] first depth map of the running batch that
+                                    // reached the slot's key (atomic min; 0x7f7f7f7f: none)
+    uint8_t* block_birth;           // [max_blocks] that depth map, for the blocks a batch added
     uint32_t slot_mask;
     int32_t* coords;                // [max_blocks][4] (segment, bx, by, bz)
     float* f;                       // [max_blocks][512]
@@ -108,7 +113,10 @@ struct DeviceMap {
     int32_t* counters;              // [kNumCounters]
     unsigned long long* new_keys;   // [max_new] inserted keys of the running call
     uint32_t* new_slots;            // [max_new]
-    int32_t* visible;               // [max_blocks] fusion work list (32-byte entries)
+    int32_t* visible;               // [max_blocks] fusion work list ({block, depth-map mask})
+    float* vis_org;                 // [max_blocks][org_frames][8] the listed blocks' camera-frame
+                                    // origins per depth map (float32 hi, lo, bound)
+    int32_t org_frames;             // depth maps per entry that vis_org holds
     double* partials;               // [kEnergyGrid][2] energy partial sums
     uint32_t max_blocks;
     uint32_t max_new;
@@ -183,12 +191,21 @@ struct denser_ctx {
 namespace denser {
 
 // Launchers implemented in the .cu files (all enqueue on `s`).
-int launch_alloc(denser_ctx* c, const float* depth_dev, const denser_intrinsics* K, const double* T,
+// Allocation for n_frames (1..kMaxBatch) depth maps of one camera, stored back to back
+// ([n_frames][H][W] float32), with poses T [n_frames][16]: one key pass over all of
+// them, then one sort / index / zero / commit.  New blocks are indexed in order of
+// (first depth map that reached them, key), the order that one call per depth map
+// gives.  The pass also records each map's largest valid depth and resets the fusion's
+// visible count.
+int launch_alloc(denser_ctx* c, const float* depth_dev, int n_frames, const denser_intrinsics* K, const double* T,
                  int32_t segment, cudaStream_t s);
-// depth_max_ready: the preceding allocation of the same depth map already reset the
-// visible count and recorded the largest valid depth (denser_integrate).
-int launch_fuse(denser_ctx* c, const float* depth_dev, const denser_intrinsics* K, const double* T,
-                int32_t segment, cudaStream_t s, bool depth_max_ready = false);
+// Fusion of the same n_frames depth maps: one culling pass and one fusion pass, each
+// voxel taking the maps in order.  after_alloc: launch_alloc of the same maps ran just
+// before (their depth maxima are recorded, and a block that the batch added is fused
+// only from the first map that allocated it on, as one call per map would); otherwise
+// the depth maxima are computed here and every allocated block takes every map.
+int launch_fuse(denser_ctx* c, const float* depth_dev, int n_frames, const denser_intrinsics* K, const double* T,
+                int32_t segment, cudaStream_t s, bool after_alloc = false);
 int launch_load_blocks(denser_ctx* c, const int32_t* coords_dev, int64_t n, int64_t base, cudaStream_t s);
 int launch_prepare_regularize(denser_ctx* c, int64_t n_blocks, bool rebuild_nbr, cudaStream_t s);
 int launch_sweep(denser_ctx* c, int64_t n_blocks, cudaStream_t s);

@@ -24,11 +24,13 @@ DENSER_ERR_TIMEOUT = -5
 DENSER_ERR_RANGE = -6
 DENSER_ERR_TOO_LARGE = -7
 DENSER_NOALLOC_MAX_BLOCKS = 16384
+DENSER_MAX_BATCH = 16
 DENSER_FP32, DENSER_FP16, DENSER_BF16 = 0, 1, 2
 
 # every symbol include/denser.h declares
 EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_reset",
            "denser_last_error", "denser_sync", "denser_alloc_blocks", "denser_fuse_depth", "denser_integrate",
+           "denser_integrate_batch",
            "denser_alloc_points", "denser_fuse_points", "denser_integrate_points",
            "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual", "denser_extract_surface",
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
@@ -104,6 +106,7 @@ def lib():
             "denser_alloc_blocks": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp, P(_i32)]),
             "denser_fuse_depth": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp]),
             "denser_integrate": (_i32, [_vp, _vp, P(denser_intrinsics), P(_dbl), _i32, _vp, P(_i32)]),
+            "denser_integrate_batch": (_i32, [_vp, _vp, _i32, P(denser_intrinsics), P(_dbl), _i32, _vp, P(_i32)]),
             "denser_alloc_points": (_i32, [_vp, _vp, _i64, P(_dbl), _i32, _vp, P(_i32)]),
             "denser_fuse_points": (_i32, [_vp, _vp, _i64, P(_dbl), _i32, _vp]),
             "denser_integrate_points": (_i32, [_vp, _vp, _i64, P(_dbl), _i32, _vp, P(_i32)]),
@@ -253,6 +256,21 @@ def denser_integrate(ctx, depth, K: denser_intrinsics, T_gc, segment=0, stream=N
     n = _i32(0)
     _check(ctx, lib().denser_integrate(ctx, _ptr(depth, np.float32), ctypes.byref(K), tp, segment,
                                        _stream(stream), ctypes.byref(n) if count else None))
+    return n.value if count else None
+
+
+def denser_integrate_batch(ctx, depths, K: denser_intrinsics, T_gc, segment=0, stream=None, count=False):
+    """Allocation and fusion of depth maps [n, H, W] in order (the result of n
+    denser_integrate calls) with poses [n, 4, 4]; returns the number of new blocks when
+    ``count`` (waits), else None."""
+    n_frames = int(depths.shape[0])
+    if tuple(depths.shape[1:]) != (K.height, K.width):
+        raise ValueError(f"depth maps {tuple(depths.shape)} do not match the camera's {K.height} x {K.width}")
+    tp_arr = np.ascontiguousarray(np.asarray(T_gc, dtype=np.float64).reshape(n_frames, 16))
+    n = _i32(0)
+    _check(ctx, lib().denser_integrate_batch(ctx, _ptr(depths, np.float32), n_frames, ctypes.byref(K),
+                                             tp_arr.ctypes.data_as(ctypes.POINTER(_dbl)), segment, _stream(stream),
+                                             ctypes.byref(n) if count else None))
     return n.value if count else None
 
 
