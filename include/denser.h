@@ -17,7 +17,9 @@
  *   - Per-voxel fields are stored block-major: field[block][512].  The dual field p
  *     is stored component-major: p[3][block][512].
  *   - Block indices: every allocation call appends its new blocks in ascending
- *     (segment, bz, by, bx) order, after all blocks allocated earlier.
+ *     (segment, bz, by, bx) order, after all blocks allocated earlier (a batched call,
+ *     denser_integrate_batch, orders them by the first depth map that reached them,
+ *     then by key: the order one call per map gives).
  *   - Depth maps are float32 [height][width]; a pixel is valid when finite and > 0.
  *
  * Pointers
@@ -108,14 +110,19 @@ typedef struct {
  * iterates; only speed differs (chosen by the autotuner).
  *   sweep_kernel  0: staged (each CTA loads a block, then computes it),
  *                 1: pipelined (cp.async prefetch of the next block while computing),
- *                 2: rows (one thread per 8-voxel x-row, vector loads; the default),
+ *                 2: rows (one thread per 8-voxel x-row, vector loads; the default for
+ *                    16-bit storage, with order 1 and ctas_per_sm 0),
  *                 3: rows with the next block's own fields prefetched by 1-D bulk copies
- *                    (TMA) into a double-buffered shared-memory stage
+ *                    (TMA) into a double-buffered shared-memory stage,
+ *                 4: rows with the halos (faces, edges, x halos) copied asynchronously
+ *                    (cp.async) straight into shared memory while the block's own rows
+ *                    load (float32 storage; 16-bit storage stages them as kernel 2); the
+ *                    default for float32 storage, with order 0 and ctas_per_sm 2
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)
  *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default); for
- *                 the row kernel it picks the register budget: 0/1 -> 8 CTAs of 64
- *                 threads per SM, 2 -> 10, 3 -> 12; for kernel 3 it caps CTAs at 2x this
+ *                 the row kernels (2, 4) it picks the register budget: 0/1 -> 8 CTAs of
+ *                 64 threads per SM, 2 -> 10, 3 -> 12; for kernel 3 it caps CTAs at 2x this
  *   use_graph     1: the iteration loop of denser_regularize runs as one CUDA graph: a
  *                 WHILE conditional node whose body is gap_every sweeps (10 when no gap
  *                 test is asked for) plus the FP64 gap evaluation, and whose condition is

@@ -281,9 +281,12 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->surf_items = 0;
     c->h_counters = nullptr, c->h_energy = nullptr;
     c->launches = 0;
-    c->sched.sweep_kernel = 2;
-    c->sched.order = 1;
-    c->sched.ctas_per_sm = 0;
+    // float32 storage: the row sweep with asynchronous halos, 10 CTAs per SM, blocks in
+    // index order; 16-bit storage: the row sweep, 8 CTAs per SM, blocks in key order
+    const bool f32 = p.precision == DENSER_FP32;
+    c->sched.sweep_kernel = f32 ? 4 : 2;
+    c->sched.order = f32 ? 0 : 1;
+    c->sched.ctas_per_sm = f32 ? 2 : 0;
     c->sched.use_graph = 1;
     c->order = nullptr, c->order_keys = nullptr, c->order_vals = nullptr;
     c->order_valid_blocks = -1;
@@ -992,7 +995,7 @@ int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const floa
 
 int denser_set_schedule(denser_ctx* c, const denser_schedule* sch) {
     if (!c || !sch) return DENSER_ERR_INVALID_ARG;
-    if (sch->sweep_kernel < 0 || sch->sweep_kernel > 3 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
+    if (sch->sweep_kernel < 0 || sch->sweep_kernel > 4 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
         sch->ctas_per_sm > 8 || sch->use_graph < 0 || sch->use_graph > 1)
         return set_error(c, DENSER_ERR_INVALID_ARG, "set_schedule: field out of range");
     c->sched = *sch;

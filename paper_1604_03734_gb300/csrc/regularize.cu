@@ -264,6 +264,16 @@ __device__ inline void cp_async4(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// The same with zero fill: nothing is read and the destination is zeroed when !valid
+// (src-size 0); gmem must still be a valid address.
+__device__ inline void cp_async16z(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ inline void cp_async4z(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
+}
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -483,6 +493,7 @@ struct __align__(16) RowTiles {
     float xhp[100];          // u_bar at x = 8 of each row
     float xhm[100];          // u_bar at x = -1 of each row
     float pxm[64];           // new p_x at x = -1 of each block row
+    float phm[3][64];        // old p at x = -1 of each block row (asynchronous staging)
     unsigned short om[100];  // Omega: bits 0-7 at x = 0..7, bit 8 at x = 8, bit 9 at x = -1
 };
 
@@ -584,10 +595,83 @@ __device__ inline void ld_row_smem(const T* p, float* v) {
     }
 }
 
+// Row of 8 floats of block n's field (two 16-byte copies); zeros when n < 0.
+__device__ inline void cp_row_z(float* dst, const float* field, int n, int row) {
+    const bool ok = n >= 0;
+    const float* src = ok ? field + (size_t)n * kBlockVoxels + 8 * row : field;
+    cp_async16z(dst, src, ok);
+    cp_async16z(dst + 4, ok ? src + 4 : field, ok);
+}
+
+// Voxel l of block n's field; zero when n < 0.
+__device__ inline void cp_voxel_z(float* dst, const float* field, int n, int l) {
+    cp_async4z(dst, n >= 0 ? field + (size_t)n * kBlockVoxels + l : field, n >= 0);
+}
+
+__device__ inline unsigned voxel_bit(const uint32_t* __restrict__ bits, int n, int l) {
+    return n >= 0 ? (__ldg(bits + (size_t)n * 16 + (l >> 5)) >> (l & 31)) & 1u : 0u;
+}
+
+// Asynchronous halo staging of row r (float32 storage): the x halos, the face and edge
+// rows and the old p behind the low faces go straight from L2 into the tiles (cp.async,
+// zeros for absent neighbours), so that their latency overlaps the loads of the block's
+// own rows.  Returns the Omega words of the tile rows the row fills: om[0] the x-halo
+// bits of its own row (bits 8 and 9), om[1] its y-face row, om[2] its z-face row, om[3]
+// its edge row.
+__device__ __forceinline__ void issue_row_halos(const SweepArgs<float>& a, RowTiles& s, int r, int ly, int lz,
+                                                const int* nb, unsigned* om) {
+    const float* ubs = a.ub_in;
+    const size_t ps = a.pstride;
+    const int rr = r10(ly, lz);
+    cp_voxel_z(&s.xhp[rr], ubs, nb[0], 8 * r);
+    cp_voxel_z(&s.xhm[rr], ubs, nb[3], 8 * r + 7);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cp_voxel_z(&s.phm[c][r], a.p_in + c * ps, nb[3], 8 * r + 7);
+    om[0] = (voxel_bit(a.bits, nb[0], 8 * r) << 8) | (voxel_bit(a.bits, nb[3], 8 * r + 7) << 9);
+    om[1] = om[2] = om[3] = 0u;
+    if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
+        const int d = r10(8, lz);
+        cp_row_z(s.ub[d], ubs, nb[1], 8 * lz);
+        cp_voxel_z(&s.xhm[d], ubs, nb[6], 8 * (8 * lz) + 7);
+        om[1] = (nb[1] >= 0 ? row_bits(a.bits, nb[1], 8 * lz) : 0u) | (voxel_bit(a.bits, nb[6], 8 * (8 * lz) + 7) << 9);
+    }
+    if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
+        const int d = r10(-1, lz);
+        cp_row_z(s.ub[d], ubs, nb[4], 7 + 8 * lz);
+        cp_voxel_z(&s.xhp[d], ubs, nb[8], 8 * (7 + 8 * lz));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cp_row_z(s.pfy[c][lz], a.p_in + c * ps, nb[4], 7 + 8 * lz);
+        om[1] = (nb[4] >= 0 ? row_bits(a.bits, nb[4], 7 + 8 * lz) : 0u) | (voxel_bit(a.bits, nb[8], 8 * (7 + 8 * lz)) << 8);
+    }
+    if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
+        const int d = r10(ly, 8);
+        cp_row_z(s.ub[d], ubs, nb[2], ly);
+        cp_voxel_z(&s.xhm[d], ubs, nb[7], 8 * ly + 7);
+        om[2] = (nb[2] >= 0 ? row_bits(a.bits, nb[2], ly) : 0u) | (voxel_bit(a.bits, nb[7], 8 * ly + 7) << 9);
+    }
+    if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
+        const int d = r10(ly, -1);
+        cp_row_z(s.ub[d], ubs, nb[5], ly + 56);
+        cp_voxel_z(&s.xhp[d], ubs, nb[10], 8 * (ly + 56));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cp_row_z(s.pfz[c][ly], a.p_in + c * ps, nb[5], ly + 56);
+        om[2] = (nb[5] >= 0 ? row_bits(a.bits, nb[5], ly + 56) : 0u) | (voxel_bit(a.bits, nb[10], 8 * (ly + 56)) << 8);
+    }
+    if (ly == 0 && lz == 7) {  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
+        cp_row_z(s.ub[r10(-1, 8)], ubs, nb[9], 7);
+        om[3] = nb[9] >= 0 ? row_bits(a.bits, nb[9], 7) : 0u;
+    }
+    if (ly == 7 && lz == 0) {  // edge row (8, -1) <- block (-z,+y) row (0, 7)
+        cp_row_z(s.ub[r10(8, -1)], ubs, nb[11], 56);
+        om[3] = nb[11] >= 0 ? row_bits(a.bits, nb[11], 56) : 0u;
+    }
+    cp_async_commit();
+}
+
 // One block of the row sweep: staging of the rows, faces and edges, the dual steps,
 // the primal step and the relaxation.  `stage` holds the block's own fields when they
 // were prefetched into shared memory (else they are read from global memory).
-template <typename T>
+template <typename T, bool ASYNC = false>
 __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, int b, int r, const char* stage,
                                            const int* nb) {
     const int ly = r & 7, lz = r >> 3;
@@ -595,6 +679,9 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
     const size_t ps = a.pstride;
     const size_t base = (size_t)b * kBlockVoxels + 8 * r;
     // ---------------------------------------------------------- staging
+    constexpr bool kAsync = ASYNC && sizeof(T) == 4;
+    unsigned hom[4] = {0u, 0u, 0u, 0u};
+    if constexpr (kAsync) issue_row_halos(reinterpret_cast<const SweepArgs<float>&>(a), s, r, ly, lz, nb, hom);
     float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
     unsigned om_r;
     if (stage) {  // this block's rows were brought into shared memory by the bulk copies
@@ -622,74 +709,88 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
     }
     // x halos of the row: u_bar and Omega at x = 8 and x = -1, old p at x = -1
     float hm0 = 0.0f, hm1 = 0.0f, hm2 = 0.0f;
-    {
-        unsigned bit;
-        const float xp = load_voxel<T>(a, nb[0], 8 * r, &bit);
-        om_r |= bit << 8;
-        const int n3 = nb[3];
-        const float xm = load_voxel<T>(a, n3, 8 * r + 7, &bit);
-        om_r |= bit << 9;
-        if (n3 >= 0) {
-            const size_t o3 = (size_t)n3 * kBlockVoxels + 8 * r + 7;
-            hm0 = Store<T>::ld(a.p_in + o3);
-            hm1 = Store<T>::ld(a.p_in + ps + o3);
-            hm2 = Store<T>::ld(a.p_in + 2 * ps + o3);
+    if constexpr (kAsync) {
+        om_r |= hom[0];  // the dual and primal steps read the row's bits from this register
+        sts_row(s.ub[rr], ub);
+        s.om[rr] = (unsigned short)om_r;
+        if (ly == 7) s.om[r10(8, lz)] = (unsigned short)hom[1];
+        if (ly == 0) s.om[r10(-1, lz)] = (unsigned short)hom[1];
+        if (lz == 7) s.om[r10(ly, 8)] = (unsigned short)hom[2];
+        if (lz == 0) s.om[r10(ly, -1)] = (unsigned short)hom[2];
+        if (ly == 0 && lz == 7) s.om[r10(-1, 8)] = (unsigned short)hom[3];
+        if (ly == 7 && lz == 0) s.om[r10(8, -1)] = (unsigned short)hom[3];
+        cp_async_wait_all();
+    } else {
+        {
+            unsigned bit;
+            const float xp = load_voxel<T>(a, nb[0], 8 * r, &bit);
+            om_r |= bit << 8;
+            const int n3 = nb[3];
+            const float xm = load_voxel<T>(a, n3, 8 * r + 7, &bit);
+            om_r |= bit << 9;
+            if (n3 >= 0) {
+                const size_t o3 = (size_t)n3 * kBlockVoxels + 8 * r + 7;
+                hm0 = Store<T>::ld(a.p_in + o3);
+                hm1 = Store<T>::ld(a.p_in + ps + o3);
+                hm2 = Store<T>::ld(a.p_in + 2 * ps + o3);
+            }
+            s.xhp[rr] = xp;
+            s.xhm[rr] = xm;
         }
-        s.xhp[rr] = xp;
-        s.xhm[rr] = xm;
-    }
-    sts_row(s.ub[rr], ub);
-    s.om[rr] = (unsigned short)om_r;
-    // faces and edges
-    if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
-        const int d = r10(8, lz);
-        unsigned om = load_face_row<T>(a, nb[1], 8 * lz, s.ub[d]), bit;
-        s.xhm[d] = load_voxel<T>(a, nb[6], 8 * (8 * lz) + 7, &bit);
-        s.om[d] = (unsigned short)(om | (bit << 9));
-    }
-    if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
-        const int d = r10(-1, lz);
-        const int n4 = nb[4];
-        unsigned om = load_face_row<T>(a, n4, 7 + 8 * lz, s.ub[d]), bit;
-        s.xhp[d] = load_voxel<T>(a, nb[8], 8 * (7 + 8 * lz), &bit);
-        s.om[d] = (unsigned short)(om | (bit << 8));
-        float q[8];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (n4 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n4 * kBlockVoxels + 8 * (7 + 8 * lz), q);
-            else
-#pragma unroll
-                for (int i = 0; i < 8; ++i) q[i] = 0.0f;
-            sts_row(s.pfy[c][lz], q);
+        sts_row(s.ub[rr], ub);
+        s.om[rr] = (unsigned short)om_r;
+        // faces and edges
+        if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
+            const int d = r10(8, lz);
+            unsigned om = load_face_row<T>(a, nb[1], 8 * lz, s.ub[d]), bit;
+            s.xhm[d] = load_voxel<T>(a, nb[6], 8 * (8 * lz) + 7, &bit);
+            s.om[d] = (unsigned short)(om | (bit << 9));
         }
-    }
-    if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
-        const int d = r10(ly, 8);
-        unsigned om = load_face_row<T>(a, nb[2], ly, s.ub[d]), bit;
-        s.xhm[d] = load_voxel<T>(a, nb[7], 8 * ly + 7, &bit);
-        s.om[d] = (unsigned short)(om | (bit << 9));
-    }
-    if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
-        const int d = r10(ly, -1);
-        const int n5 = nb[5];
-        unsigned om = load_face_row<T>(a, n5, ly + 56, s.ub[d]), bit;
-        s.xhp[d] = load_voxel<T>(a, nb[10], 8 * (ly + 56), &bit);
-        s.om[d] = (unsigned short)(om | (bit << 8));
-        float q[8];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (n5 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n5 * kBlockVoxels + 8 * (ly + 56), q);
-            else
-#pragma unroll
-                for (int i = 0; i < 8; ++i) q[i] = 0.0f;
-            sts_row(s.pfz[c][ly], q);
+        if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
+            const int d = r10(-1, lz);
+            const int n4 = nb[4];
+            unsigned om = load_face_row<T>(a, n4, 7 + 8 * lz, s.ub[d]), bit;
+            s.xhp[d] = load_voxel<T>(a, nb[8], 8 * (7 + 8 * lz), &bit);
+            s.om[d] = (unsigned short)(om | (bit << 8));
+            float q[8];
+    #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (n4 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n4 * kBlockVoxels + 8 * (7 + 8 * lz), q);
+                else
+    #pragma unroll
+                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+                sts_row(s.pfy[c][lz], q);
+            }
         }
+        if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
+            const int d = r10(ly, 8);
+            unsigned om = load_face_row<T>(a, nb[2], ly, s.ub[d]), bit;
+            s.xhm[d] = load_voxel<T>(a, nb[7], 8 * ly + 7, &bit);
+            s.om[d] = (unsigned short)(om | (bit << 9));
+        }
+        if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
+            const int d = r10(ly, -1);
+            const int n5 = nb[5];
+            unsigned om = load_face_row<T>(a, n5, ly + 56, s.ub[d]), bit;
+            s.xhp[d] = load_voxel<T>(a, nb[10], 8 * (ly + 56), &bit);
+            s.om[d] = (unsigned short)(om | (bit << 8));
+            float q[8];
+    #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (n5 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n5 * kBlockVoxels + 8 * (ly + 56), q);
+                else
+    #pragma unroll
+                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+                sts_row(s.pfz[c][ly], q);
+            }
+        }
+        if (ly == 0 && lz == 7)  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
+            s.om[r10(-1, 8)] = (unsigned short)load_face_row<T>(a, nb[9], 7, s.ub[r10(-1, 8)]);
+        if (ly == 7 && lz == 0)  // edge row (8, -1) <- block (-z,+y) row (0, 7)
+            s.om[r10(8, -1)] = (unsigned short)load_face_row<T>(a, nb[11], 56, s.ub[r10(8, -1)]);
     }
-    if (ly == 0 && lz == 7)  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
-        s.om[r10(-1, 8)] = (unsigned short)load_face_row<T>(a, nb[9], 7, s.ub[r10(-1, 8)]);
-    if (ly == 7 && lz == 0)  // edge row (8, -1) <- block (-z,+y) row (0, 7)
-        s.om[r10(8, -1)] = (unsigned short)load_face_row<T>(a, nb[11], 56, s.ub[r10(8, -1)]);
     __syncthreads();
+    if constexpr (kAsync) hm0 = s.phm[0][r], hm1 = s.phm[1][r], hm2 = s.phm[2][r];
 
     // ------------------------------------------------------- dual steps
     {
@@ -785,7 +886,7 @@ __device__ inline void load_nbr_row(const int32_t* __restrict__ nbr, int b, int*
     out[6] = y.z, out[7] = y.w, out[8] = z.x, out[9] = z.y, out[10] = z.z, out[11] = z.w;
 }
 
-template <typename T, int MINB>
+template <typename T, int MINB, bool ASYNC = false>
 __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs<T> a) {
     __shared__ RowTiles s;
     const int G = gridDim.x;
@@ -803,7 +904,7 @@ __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs
             b_next = a.order ? __ldg(a.order + kn) : kn;
             load_nbr_row(a.nbr, b_next, nb_next);
         }
-        rows_block<T>(a, s, b, threadIdx.x, nullptr, nb);
+        rows_block<T, ASYNC>(a, s, b, threadIdx.x, nullptr, nb);
         __syncthreads();  // the tiles are rewritten for the next block
         b = b_next;
 #pragma unroll
@@ -894,7 +995,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) sweep_rows_tma_kernel(SweepArg
         const int b = block_at(k);
         int nb[kNeighbours];
         load_nbr_row(a.nbr, b, nb);
-        rows_block<T>(a, s, b, t, stages + h * L::kBytes, nb);
+        rows_block<T, true>(a, s, b, t, stages + h * L::kBytes, nb);
         __syncthreads();  // tiles and this stage half are reused
     }
 }
@@ -1063,6 +1164,24 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 8>, kRowThreads, 0);
                 sweep_rows_kernel<T, 8><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
                                           kRowThreads, 0, s>>>(a);
+        }
+    } else if (c->sched.sweep_kernel == 4) {
+        // row sweep with the halos staged asynchronously (float32 storage; 16-bit storage
+        // takes the synchronous staging)
+        // (ctas_per_sm 2: up to 10 resident CTAs per SM, 96 registers; 3: 12, 80 registers)
+        int per_sm = 0;
+        if (c->sched.ctas_per_sm == 3) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 12, true>, kRowThreads, 0);
+            sweep_rows_kernel<T, 12, true><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
+                                             kRowThreads, 0, s>>>(a);
+        } else if (c->sched.ctas_per_sm == 2) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 10, true>, kRowThreads, 0);
+            sweep_rows_kernel<T, 10, true><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
+                                             kRowThreads, 0, s>>>(a);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 8, true>, kRowThreads, 0);
+            sweep_rows_kernel<T, 8, true><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
+                                            kRowThreads, 0, s>>>(a);
         }
     } else if (c->sched.sweep_kernel == 3) {
         int per_sm = 0;
