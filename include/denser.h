@@ -110,14 +110,12 @@ typedef struct {
  * iterates; only speed differs (chosen by the autotuner).
  *   sweep_kernel  0: staged (each CTA loads a block, then computes it),
  *                 1: pipelined (cp.async prefetch of the next block while computing),
- *                 2: rows (one thread per 8-voxel x-row, vector loads; the default for
- *                    16-bit storage, with order 1 and ctas_per_sm 0),
+ *                 2: rows (one thread per 8-voxel x-row, vector loads),
  *                 3: rows with the next block's own fields prefetched by 1-D bulk copies
  *                    (TMA) into a double-buffered shared-memory stage,
  *                 4: rows with the halos (faces, edges, x halos) copied asynchronously
- *                    (cp.async) straight into shared memory while the block's own rows
- *                    load (float32 storage; 16-bit storage stages them as kernel 2); the
- *                    default for float32 storage, with order 0 and ctas_per_sm 2
+ *                    (cp.async) into shared memory while the block's own rows load; the
+ *                    default, with order 0 and ctas_per_sm 2
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)
  *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default); for

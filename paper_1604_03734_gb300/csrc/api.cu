@@ -281,12 +281,10 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->surf_items = 0;
     c->h_counters = nullptr, c->h_energy = nullptr;
     c->launches = 0;
-    // float32 storage: the row sweep with asynchronous halos, 10 CTAs per SM, blocks in
-    // index order; 16-bit storage: the row sweep, 8 CTAs per SM, blocks in key order
-    const bool f32 = p.precision == DENSER_FP32;
-    c->sched.sweep_kernel = f32 ? 4 : 2;
-    c->sched.order = f32 ? 0 : 1;
-    c->sched.ctas_per_sm = f32 ? 2 : 0;
+    // the row sweep with asynchronous halos, 10 CTAs per SM, blocks in index order
+    c->sched.sweep_kernel = 4;
+    c->sched.order = 0;
+    c->sched.ctas_per_sm = 2;
     c->sched.use_graph = 1;
     c->order = nullptr, c->order_keys = nullptr, c->order_vals = nullptr;
     c->order_valid_blocks = -1;

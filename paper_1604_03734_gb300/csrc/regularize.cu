@@ -595,77 +595,163 @@ __device__ inline void ld_row_smem(const T* p, float* v) {
     }
 }
 
-// Row of 8 floats of block n's field (two 16-byte copies); zeros when n < 0.
-__device__ inline void cp_row_z(float* dst, const float* field, int n, int row) {
+// Where the asynchronous halo copies land.  With float32 storage they land in the tiles
+// themselves.  With 16-bit storage they land here first, as stored (a row of 8 values;
+// for a single voxel the aligned 4-byte word that holds it, since cp.async moves at least
+// 4 bytes), and each thread converts what it copied into the tiles.
+template <typename T>
+struct __align__(16) HaloRaw {
+    T ub[100][8];
+    T pfy[3][8][8];
+    T pfz[3][8][8];
+    uint32_t xhp[100], xhm[100];
+    uint32_t phm[3][64];
+};
+template <>
+struct HaloRaw<float> {
+    int unused;
+};
+
+// Row `row` of block n's field (8 values: 32 or 16 bytes); zeros when n < 0.
+template <typename T>
+__device__ inline void cp_row_z(void* dst, const T* field, int n, int row) {
     const bool ok = n >= 0;
-    const float* src = ok ? field + (size_t)n * kBlockVoxels + 8 * row : field;
+    const T* src = ok ? field + (size_t)n * kBlockVoxels + 8 * row : field;
     cp_async16z(dst, src, ok);
-    cp_async16z(dst + 4, ok ? src + 4 : field, ok);
+    if constexpr (sizeof(T) == 4) cp_async16z(reinterpret_cast<char*>(dst) + 16, ok ? src + 4 : field, ok);
 }
 
-// Voxel l of block n's field; zero when n < 0.
-__device__ inline void cp_voxel_z(float* dst, const float* field, int n, int l) {
-    cp_async4z(dst, n >= 0 ? field + (size_t)n * kBlockVoxels + l : field, n >= 0);
+// Voxel l of block n's field (16-bit storage: the 4-byte word holding it); zero when n < 0.
+template <typename T>
+__device__ inline void cp_voxel_z(void* dst, const T* field, int n, int l) {
+    const int la = sizeof(T) == 4 ? l : (l & ~1);
+    cp_async4z(dst, n >= 0 ? field + (size_t)n * kBlockVoxels + la : field, n >= 0);
 }
 
 __device__ inline unsigned voxel_bit(const uint32_t* __restrict__ bits, int n, int l) {
     return n >= 0 ? (__ldg(bits + (size_t)n * 16 + (l >> 5)) >> (l & 31)) & 1u : 0u;
 }
 
-// Asynchronous halo staging of row r (float32 storage): the x halos, the face and edge
-// rows and the old p behind the low faces go straight from L2 into the tiles (cp.async,
-// zeros for absent neighbours), so that their latency overlaps the loads of the block's
-// own rows.  Returns the Omega words of the tile rows the row fills: om[0] the x-halo
-// bits of its own row (bits 8 and 9), om[1] its y-face row, om[2] its z-face row, om[3]
-// its edge row.
-__device__ __forceinline__ void issue_row_halos(const SweepArgs<float>& a, RowTiles& s, int r, int ly, int lz,
-                                                const int* nb, unsigned* om) {
-    const float* ubs = a.ub_in;
+// The value of a 16-bit voxel from the word that holds it (odd: the upper half).
+template <typename T>
+__device__ inline float word_half(uint32_t w, int odd) {
+    return Store<T>::ld(reinterpret_cast<const T*>(&w) + odd);
+}
+
+// Asynchronous halo staging of row r: the x halos, the face and edge rows and the old p
+// behind the low faces go straight from L2 into shared memory (cp.async, zeros for
+// absent neighbours), so that their latency overlaps the loads of the block's own rows.
+// Returns the Omega words of the tile rows the row fills: om[0] the x-halo bits of its
+// own row (bits 8 and 9), om[1] its y-face row, om[2] its z-face row, om[3] its edge row.
+// The x = 8 voxels sit at even offsets of their block, the x = -1 voxels at odd ones.
+template <typename T>
+__device__ __forceinline__ void issue_row_halos(const SweepArgs<T>& a, RowTiles& s, HaloRaw<T>& raw, int r, int ly,
+                                                int lz, const int* nb, unsigned* om) {
+    constexpr bool kF = sizeof(T) == 4;
+    const T* ubs = a.ub_in;
     const size_t ps = a.pstride;
     const int rr = r10(ly, lz);
-    cp_voxel_z(&s.xhp[rr], ubs, nb[0], 8 * r);
-    cp_voxel_z(&s.xhm[rr], ubs, nb[3], 8 * r + 7);
+    auto ub_row = [&](int d) -> void* { if constexpr (kF) return s.ub[d]; else return raw.ub[d]; };
+    auto xhp = [&](int d) -> void* { if constexpr (kF) return &s.xhp[d]; else return &raw.xhp[d]; };
+    auto xhm = [&](int d) -> void* { if constexpr (kF) return &s.xhm[d]; else return &raw.xhm[d]; };
+    cp_voxel_z<T>(xhp(rr), ubs, nb[0], 8 * r);
+    cp_voxel_z<T>(xhm(rr), ubs, nb[3], 8 * r + 7);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) cp_voxel_z(&s.phm[c][r], a.p_in + c * ps, nb[3], 8 * r + 7);
+    for (int c = 0; c < 3; ++c) {
+        void* dst;
+        if constexpr (kF) dst = &s.phm[c][r]; else dst = &raw.phm[c][r];
+        cp_voxel_z<T>(dst, a.p_in + c * ps, nb[3], 8 * r + 7);
+    }
     om[0] = (voxel_bit(a.bits, nb[0], 8 * r) << 8) | (voxel_bit(a.bits, nb[3], 8 * r + 7) << 9);
     om[1] = om[2] = om[3] = 0u;
     if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
         const int d = r10(8, lz);
-        cp_row_z(s.ub[d], ubs, nb[1], 8 * lz);
-        cp_voxel_z(&s.xhm[d], ubs, nb[6], 8 * (8 * lz) + 7);
+        cp_row_z<T>(ub_row(d), ubs, nb[1], 8 * lz);
+        cp_voxel_z<T>(xhm(d), ubs, nb[6], 8 * (8 * lz) + 7);
         om[1] = (nb[1] >= 0 ? row_bits(a.bits, nb[1], 8 * lz) : 0u) | (voxel_bit(a.bits, nb[6], 8 * (8 * lz) + 7) << 9);
     }
     if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
         const int d = r10(-1, lz);
-        cp_row_z(s.ub[d], ubs, nb[4], 7 + 8 * lz);
-        cp_voxel_z(&s.xhp[d], ubs, nb[8], 8 * (7 + 8 * lz));
+        cp_row_z<T>(ub_row(d), ubs, nb[4], 7 + 8 * lz);
+        cp_voxel_z<T>(xhp(d), ubs, nb[8], 8 * (7 + 8 * lz));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_row_z(s.pfy[c][lz], a.p_in + c * ps, nb[4], 7 + 8 * lz);
+        for (int c = 0; c < 3; ++c) {
+            void* dst;
+            if constexpr (kF) dst = s.pfy[c][lz]; else dst = raw.pfy[c][lz];
+            cp_row_z<T>(dst, a.p_in + c * ps, nb[4], 7 + 8 * lz);
+        }
         om[1] = (nb[4] >= 0 ? row_bits(a.bits, nb[4], 7 + 8 * lz) : 0u) | (voxel_bit(a.bits, nb[8], 8 * (7 + 8 * lz)) << 8);
     }
     if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
         const int d = r10(ly, 8);
-        cp_row_z(s.ub[d], ubs, nb[2], ly);
-        cp_voxel_z(&s.xhm[d], ubs, nb[7], 8 * ly + 7);
+        cp_row_z<T>(ub_row(d), ubs, nb[2], ly);
+        cp_voxel_z<T>(xhm(d), ubs, nb[7], 8 * ly + 7);
         om[2] = (nb[2] >= 0 ? row_bits(a.bits, nb[2], ly) : 0u) | (voxel_bit(a.bits, nb[7], 8 * ly + 7) << 9);
     }
     if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
         const int d = r10(ly, -1);
-        cp_row_z(s.ub[d], ubs, nb[5], ly + 56);
-        cp_voxel_z(&s.xhp[d], ubs, nb[10], 8 * (ly + 56));
+        cp_row_z<T>(ub_row(d), ubs, nb[5], ly + 56);
+        cp_voxel_z<T>(xhp(d), ubs, nb[10], 8 * (ly + 56));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_row_z(s.pfz[c][ly], a.p_in + c * ps, nb[5], ly + 56);
+        for (int c = 0; c < 3; ++c) {
+            void* dst;
+            if constexpr (kF) dst = s.pfz[c][ly]; else dst = raw.pfz[c][ly];
+            cp_row_z<T>(dst, a.p_in + c * ps, nb[5], ly + 56);
+        }
         om[2] = (nb[5] >= 0 ? row_bits(a.bits, nb[5], ly + 56) : 0u) | (voxel_bit(a.bits, nb[10], 8 * (ly + 56)) << 8);
     }
     if (ly == 0 && lz == 7) {  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
-        cp_row_z(s.ub[r10(-1, 8)], ubs, nb[9], 7);
+        cp_row_z<T>(ub_row(r10(-1, 8)), ubs, nb[9], 7);
         om[3] = nb[9] >= 0 ? row_bits(a.bits, nb[9], 7) : 0u;
     }
     if (ly == 7 && lz == 0) {  // edge row (8, -1) <- block (-z,+y) row (0, 7)
-        cp_row_z(s.ub[r10(8, -1)], ubs, nb[11], 56);
+        cp_row_z<T>(ub_row(r10(8, -1)), ubs, nb[11], 56);
         om[3] = nb[11] >= 0 ? row_bits(a.bits, nb[11], 56) : 0u;
     }
     cp_async_commit();
+}
+
+// 16-bit storage: converts the halo values row r copied (after its copies have landed)
+// into the float32 tiles.
+template <typename T>
+__device__ __forceinline__ void convert_row_halos(RowTiles& s, const HaloRaw<T>& raw, int r, int ly, int lz) {
+    const int rr = r10(ly, lz);
+    auto row = [&](float* dst, const T* src) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(src + i);
+        sts_row(dst, v);
+    };
+    s.xhp[rr] = word_half<T>(raw.xhp[rr], 0);
+    s.xhm[rr] = word_half<T>(raw.xhm[rr], 1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s.phm[c][r] = word_half<T>(raw.phm[c][r], 1);
+    if (ly == 7) {
+        const int d = r10(8, lz);
+        row(s.ub[d], raw.ub[d]);
+        s.xhm[d] = word_half<T>(raw.xhm[d], 1);
+    }
+    if (ly == 0) {
+        const int d = r10(-1, lz);
+        row(s.ub[d], raw.ub[d]);
+        s.xhp[d] = word_half<T>(raw.xhp[d], 0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) row(s.pfy[c][lz], raw.pfy[c][lz]);
+    }
+    if (lz == 7) {
+        const int d = r10(ly, 8);
+        row(s.ub[d], raw.ub[d]);
+        s.xhm[d] = word_half<T>(raw.xhm[d], 1);
+    }
+    if (lz == 0) {
+        const int d = r10(ly, -1);
+        row(s.ub[d], raw.ub[d]);
+        s.xhp[d] = word_half<T>(raw.xhp[d], 0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) row(s.pfz[c][ly], raw.pfz[c][ly]);
+    }
+    if (ly == 0 && lz == 7) row(s.ub[r10(-1, 8)], raw.ub[r10(-1, 8)]);
+    if (ly == 7 && lz == 0) row(s.ub[r10(8, -1)], raw.ub[r10(8, -1)]);
 }
 
 // One block of the row sweep: staging of the rows, faces and edges, the dual steps,
@@ -673,15 +759,15 @@ __device__ __forceinline__ void issue_row_halos(const SweepArgs<float>& a, RowTi
 // were prefetched into shared memory (else they are read from global memory).
 template <typename T, bool ASYNC = false>
 __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, int b, int r, const char* stage,
-                                           const int* nb) {
+                                           const int* nb, HaloRaw<T>* raw = nullptr) {
     const int ly = r & 7, lz = r >> 3;
     const int rr = r10(ly, lz);
     const size_t ps = a.pstride;
     const size_t base = (size_t)b * kBlockVoxels + 8 * r;
     // ---------------------------------------------------------- staging
-    constexpr bool kAsync = ASYNC && sizeof(T) == 4;
+    constexpr bool kAsync = ASYNC;
     unsigned hom[4] = {0u, 0u, 0u, 0u};
-    if constexpr (kAsync) issue_row_halos(reinterpret_cast<const SweepArgs<float>&>(a), s, r, ly, lz, nb, hom);
+    if constexpr (kAsync) issue_row_halos<T>(a, s, *raw, r, ly, lz, nb, hom);
     float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
     unsigned om_r;
     if (stage) {  // this block's rows were brought into shared memory by the bulk copies
@@ -720,6 +806,7 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
         if (ly == 0 && lz == 7) s.om[r10(-1, 8)] = (unsigned short)hom[3];
         if (ly == 7 && lz == 0) s.om[r10(8, -1)] = (unsigned short)hom[3];
         cp_async_wait_all();
+        if constexpr (sizeof(T) != 4) convert_row_halos<T>(s, *raw, r, ly, lz);
     } else {
         {
             unsigned bit;
@@ -889,6 +976,7 @@ __device__ inline void load_nbr_row(const int32_t* __restrict__ nbr, int b, int*
 template <typename T, int MINB, bool ASYNC = false>
 __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs<T> a) {
     __shared__ RowTiles s;
+    __shared__ HaloRaw<T> raw;
     const int G = gridDim.x;
     int k = blockIdx.x;
     if (k >= a.n_blocks) return;
@@ -904,7 +992,7 @@ __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs
             b_next = a.order ? __ldg(a.order + kn) : kn;
             load_nbr_row(a.nbr, b_next, nb_next);
         }
-        rows_block<T, ASYNC>(a, s, b, threadIdx.x, nullptr, nb);
+        rows_block<T, ASYNC>(a, s, b, threadIdx.x, nullptr, nb, &raw);
         __syncthreads();  // the tiles are rewritten for the next block
         b = b_next;
 #pragma unroll
@@ -966,6 +1054,7 @@ template <typename T>
 __global__ void __launch_bounds__(kRowThreads, 4) sweep_rows_tma_kernel(SweepArgs<T> a) {
     using L = RowStage<T>;
     __shared__ RowTiles s;
+    __shared__ HaloRaw<T> raw;
     __shared__ __align__(8) uint64_t bars[2];
     extern __shared__ __align__(128) char stages[];  // [2][L::kBytes]
     const int t = threadIdx.x;
@@ -995,7 +1084,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) sweep_rows_tma_kernel(SweepArg
         const int b = block_at(k);
         int nb[kNeighbours];
         load_nbr_row(a.nbr, b, nb);
-        rows_block<T, true>(a, s, b, t, stages + h * L::kBytes, nb);
+        rows_block<T, true>(a, s, b, t, stages + h * L::kBytes, nb, &raw);
         __syncthreads();  // tiles and this stage half are reused
     }
 }
@@ -1166,8 +1255,7 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
                                           kRowThreads, 0, s>>>(a);
         }
     } else if (c->sched.sweep_kernel == 4) {
-        // row sweep with the halos staged asynchronously (float32 storage; 16-bit storage
-        // takes the synchronous staging)
+        // row sweep with the halos staged asynchronously
         // (ctas_per_sm 2: up to 10 resident CTAs per SM, 96 registers; 3: 12, 80 registers)
         int per_sm = 0;
         if (c->sched.ctas_per_sm == 3) {
