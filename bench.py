@@ -16,6 +16,7 @@ workload (the first frames of the same street, as many iterations as frames).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -77,15 +78,32 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    """nvidia-smi clock/throttle samples every 200 ms.  The sampler is started before the
+    warm-up (so that nvidia-smi's own start-up does not fall into the timed region) and
+    the summary keeps the samples whose timestamps lie inside the timed region."""
 
     def __init__(self, index=0):
         self.proc = None
         self.path = None
         self.index = index
+        self.t0 = self.t1 = None
+
+    def wait_ready(self, timeout=5.0):
+        """Waits until the first sample is written (or the timeout)."""
+        t_end = time.time() + timeout
+        while self.proc is not None and time.time() < t_end:
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.05)
+
+    def start(self):
+        self.t0 = datetime.datetime.now()
+
+    def stop(self):
+        self.t1 = datetime.datetime.now()
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -109,25 +127,30 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not self.path or not os.path.exists(self.path):
             return None
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             [nm for nm, v in zip(names, parts[6:10]) if v.lower().startswith("active")]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        inside = [r for r in rows if self.t0 is not None and self.t1 is not None and self.t0 <= r[0] <= self.t1]
+        window = "timed region"
+        if not inside and rows and self.t0 is not None:
+            # a region shorter than the sampling period: the first sample after it began
+            after = [r for r in rows if r[0] >= self.t0]
+            inside, window = (after[:1] or rows[-1:]), "first sample after the start of the timed region"
+        if not inside:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        reasons = sorted({nm for r in inside for nm in r[3]})
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": float(max(r[2] for r in inside)),
+                "samples": len(inside), "window": window, "reasons": reasons}
 
 
 def make_inputs(seed, frames=None, length=100.0):
@@ -216,7 +239,7 @@ def sum_over_ranks(x: float, world: int, device=None) -> float:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="denser", choices=["denser", "reference"])
     ap.add_argument("--iters", type=int, default=200)
@@ -301,17 +324,19 @@ def main():
     out_dev = outputs(nb, dev)
     out_host = outputs(nb, torch.device("cpu"))
 
-    for _ in range(args.warmup):
-        pipeline(depths_dev, out_dev)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-
-    l0 = N.denser_launch_count(ctx)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sweep_ms, sweep_launches = 0.0, 0
     with ClockSampler(local) as clk:
+        clk.wait_ready()
+        for _ in range(args.warmup):
+            pipeline(depths_dev, out_dev)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+        l0 = N.denser_launch_count(ctx)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sweep_ms, sweep_launches = 0.0, 0
+        torch.cuda.synchronize()
+        clk.start()
         ev0.record(stream)
         for _ in range(args.steps):
             st = pipeline(depths_dev, out_dev)
@@ -319,6 +344,7 @@ def main():
             sweep_launches += st.sweep_launches
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.stop()
     launches = N.denser_launch_count(ctx) - l0
     step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     if world > 1:
