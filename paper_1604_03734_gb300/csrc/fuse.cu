@@ -10,6 +10,8 @@
 //               A culled (block, map) provably has no voxel that Eq. 1 would update.
 //               After a batched allocation a block that the batch added takes only the
 //               maps from the first one that allocated it on, as one call per map would;
+//   origin      the float64 camera-frame origin of each listed (block, map) pair, as a
+//               float32 hi/lo pair with its bound;
 //   fuse        one CTA per listed block, 128 threads x 4 consecutive voxels; f and w
 //               stay in registers while the block takes its maps in order, so they move
 //               once per call as float4.  Each integer decision (the pixel a voxel
@@ -163,18 +165,25 @@ __global__ void cull_kernel(DeviceMap m, FuseArgs a) {
         if (lane == 0 && ball) first = atomicAdd(m.counters + kNumVisible, __popc(ball));
         first = __shfl_sync(0xffffffffu, first, 0);
         if (mask) {
-            const int slot = first + __popc(ball & ((1u << lane) - 1));
             VisEntry e;
             e.b = b, e.mask = mask;
-            reinterpret_cast<VisEntry*>(m.visible)[slot] = e;
-            // the block's float64 origin in each map it takes
-            const int4 k = reinterpret_cast<const int4*>(m.coords)[b];
-            VisOrigin* o = reinterpret_cast<VisOrigin*>(m.vis_org) + (size_t)slot * a.n_frames;
-            for (uint32_t mm = mask; mm; mm &= mm - 1u) {
-                const int i = __ffs(mm) - 1;
-                o[i] = block_origin(a, a.fr[i], k);
-            }
+            reinterpret_cast<VisEntry*>(m.visible)[first + __popc(ball & ((1u << lane) - 1))] = e;
         }
+    }
+}
+
+// The float64 origin of every listed (block, map) pair, one thread per pair: the float64
+// pipe of this GPU is narrow, so the chains run side by side instead of one map after
+// another in the culling thread.
+__global__ void __launch_bounds__(256) origin_kernel(DeviceMap m, FuseArgs a) {
+    const long long n = (long long)m.counters[kNumVisible] * a.n_frames;
+    const VisEntry* __restrict__ vis = reinterpret_cast<const VisEntry*>(m.visible);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int kb = (int)(t / a.n_frames), i = (int)(t - (long long)kb * a.n_frames);
+        const VisEntry e = vis[kb];
+        if ((e.mask >> i) & 1u)
+            reinterpret_cast<VisOrigin*>(m.vis_org)[t] =
+                block_origin(a, a.fr[i], reinterpret_cast<const int4*>(m.coords)[e.b]);
     }
 }
 
@@ -379,8 +388,9 @@ int launch_fuse(denser_ctx* c, const float* depth, int n_frames, const denser_in
         c->d.org_frames = kMaxBatch;
     }
     cull_kernel<<<grid_for(c->sm_count, c->d.max_blocks, 256, 4), 256, 0, s>>>(c->d, a);
+    origin_kernel<<<grid_for(c->sm_count, (int64_t)c->d.max_blocks * n_frames, 256, 8), 256, 0, s>>>(c->d, a);
     fuse_kernel<<<c->sm_count * 16, 128, 0, s>>>(depth, c->d, a);
-    c->launches += 2;
+    c->launches += 3;
     return cuda_check(c, cudaGetLastError(), "fusion kernels");
 }
 
