@@ -43,6 +43,7 @@ def test_binding_loads_and_default_params(library):
 def test_null_context_is_rejected(library):
     L = native.lib()
     assert L.denser_sync(None, None) == native.DENSER_ERR_INVALID_ARG
+    assert L.denser_integrate_batch(None, None, 1, None, None, 0, None, None) == native.DENSER_ERR_INVALID_ARG
     assert L.denser_launch_count(None) == 0
     assert L.denser_last_error(None) == b"null context"
 
