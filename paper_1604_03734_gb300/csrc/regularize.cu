@@ -4,15 +4,21 @@
 //   omega_bits   Omega = {w > 0} packed 32 voxels per word (ballot per warp);
 //   neighbours   per block the indices of its 6 face and 6 (low, high) edge
 //                neighbours through the hash table (-1: unallocated = Omega-bar);
-// per iteration, one fused sweep:
-//   sweep        one CTA per 8^3 block (grid-stride), one thread per voxel.  The CTA
-//                stages u_bar on the block, its six faces and six edges, Omega on the
-//                same positions and p on the block and its three low faces in shared
-//                memory (the "block as a grid whose boundary conditions come from its
-//                neighbours' I_Omega", Section III-B).  It then takes the dual step on the
-//                block and on its low faces (the divergence needs p^{k+1} one voxel
-//                behind), synchronises, and takes the primal step and the relaxation.
-//                u_bar and p are ping-ponged across iterations; u is updated in place.
+// per iteration, one fused sweep.  Each CTA takes one 8^3 block at a time (grid-stride)
+// and stages what the block's stencil reads in shared memory: u_bar on the block, its six
+// faces and six edges, Omega on the same positions and p on its three low faces (the
+// "block as a grid whose boundary conditions come from its neighbours' I_Omega",
+// Section III-B).  It takes the dual step on the block and on its low faces (the
+// divergence needs p^{k+1} one voxel behind), synchronises, and takes the primal step
+// and the relaxation.  u_bar and p are ping-ponged across iterations; u is updated in
+// place.  Variants (the schedule picks one; all give bit-identical iterates):
+//   sweep_kernel           512 threads, one voxel per thread, stage then compute;
+//   sweep_pipe_kernel      the same with cp.async prefetch of the next block;
+//   sweep_rows_kernel      64 threads, one 8-voxel x-row per thread in registers; with
+//                          ASYNC (the default) the halos are copied by cp.async straight
+//                          into shared memory while the block's own rows load;
+//   sweep_rows_tma_kernel  the row kernel with the next block's own fields brought in by
+//                          1-D bulk copies (TMA) into a double-buffered stage.
 // and on demand:
 //   energy       FP64 primal P(u) and dual D(p) partial sums per CTA (fixed grid, fixed
 //                order: deterministic), then one CTA sums the partials.
