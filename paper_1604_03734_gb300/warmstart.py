@@ -4,7 +4,7 @@ A 4-layer 3^3 convolutional network (2 -> 16 -> 16 -> 16 -> 4 channels) reads a 
 block with its one-voxel halo (f and w / (w + 8) on 10^3 voxels) and predicts the
 block's converged (u, p_x, p_y, p_z).  Those predictions, masked to Omega and to the
 edges of Eq. 3 and projected onto |p| <= 1, replace the zero start of Section III-C;
-the plain primal-dual iteration then runs from there, so it stays the judge of the
+the plain primal-dual iteration then runs from there, so it stays the arbiter of the
 result (same fixed point, same gap test).
 
 Every product and update runs in the library's kernels (tensor-core BF16 convolutions
