@@ -5,6 +5,7 @@ configuration bench.py times, checked against the oracle on what it can compute:
     key the oracle finds for later frames present;
   * fusion: 48 sampled blocks fused by the oracle with every frame from the one that
     allocated them on (w bit-exact, f within 1e-4);
+  * the batched call the benchmark times (16 maps per launch): the same map, bit for bit;
   * regularisation: from the GPU state after 200 iterations, one more GPU iteration
     equals one oracle iteration on sampled blocks (the update of a block only reads
     its 26-neighbourhood), and the FP64 gap is non-negative.
@@ -74,6 +75,22 @@ def test_full_fusion_sampled_blocks(street):
     np.testing.assert_array_equal(snap["w"][sel], g.w.astype(np.float32))
     assert np.max(np.abs(snap["f"][sel] - g.f)) <= TOL
     assert g.w.sum() > 0
+
+
+def test_full_batched_fusion_equals_per_map(street):
+    """The benchmark's configuration: all 200 maps through denser_integrate_batch (16 per
+    launch) leave the per-map map above bit for bit (coords, f, w), so the oracle checks
+    above hold for it too."""
+    s, d, m, snap, news = street
+    cam = s.camera
+    K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    with N.DenserMap(max_blocks=1 << 17, hash_slots=1 << 20) as mb:
+        n_new = N.denser_integrate_batch(mb.ctx, torch.from_numpy(d).cuda(), K, np.asarray(s.poses[:len(d)]), 0,
+                                         count=True)
+        got = mb.snapshot()
+    assert n_new == news[-1]
+    for key in ("coords", "f", "w"):
+        np.testing.assert_array_equal(got[key], snap[key], err_msg=key)
 
 
 def test_full_regularize_step_consistency(street):
