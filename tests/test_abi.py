@@ -52,3 +52,17 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(native.denser_params) == 6 * 8 + 6 * 4
     assert ctypes.sizeof(native.denser_intrinsics) == 4 * 8 + 2 * 4
     assert ctypes.sizeof(native.denser_reg_stats) == 2 * 4 + 6 * 8 + 2 * 4 + 2 * 8
+
+
+def test_batch_binding_checks_shapes_without_a_gpu(library):
+    """The binding of denser_integrate_batch checks the maps' shape against the camera
+    before any call, and the library rejects a null context."""
+    import numpy as np
+    K = native.intrinsics(100.0, 100.0, 2.5, 2.0, 5, 4)
+    poses = np.stack([np.eye(4)] * 2)
+    with pytest.raises(ValueError):
+        native.denser_integrate_batch(None, np.zeros((2, 4, 4), np.float32), K, poses)
+    with pytest.raises(native.DenserError):
+        native.denser_integrate_batch(None, np.zeros((2, 4, 5), np.float32), K, poses)
+    with pytest.raises(ValueError):  # one pose per map
+        native.denser_integrate_batch(None, np.zeros((2, 4, 5), np.float32), K, poses[:1])
