@@ -179,9 +179,10 @@ int denser_fuse_depth(denser_ctx* ctx, const float* depth, const denser_intrinsi
 int denser_integrate(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
                      const double T_gc[16], int32_t segment, void* stream, int32_t* n_new_out);
 
-/* n_frames depth maps of one camera, in order: the same result as n_frames calls of
- * denser_integrate (the same blocks, block indices, f and w, bit for bit), in one
- * allocation pass and one fusion pass per DENSER_MAX_BATCH maps.  A block first
+/* Allocation and fusion (Section III-A, Eq. 1) of n_frames depth maps of one camera, in
+ * order: the same result as n_frames calls of denser_integrate (the same blocks, block
+ * indices, f and w, bit for bit), in one allocation pass and one fusion pass per
+ * DENSER_MAX_BATCH maps.  A block first
  * reached by map i is indexed after every block first reached by an earlier map, as
  * one call per map gives, and takes maps i, i+1, ... only; each voxel takes its maps
  * in order, so the running mean of Eq. 1 sees the same operands.
