@@ -226,8 +226,6 @@ int stereo_init_state(float* state, const float* d0, int W, int H, cudaStream_t 
 int stereo_depth(const float* disp, int W, int H, float fb, float min_disp, float* depth, cudaStream_t s);
 int launch_fuse_points(denser_ctx* c, const float* pts, int64_t n, const double* T, int32_t segment, cudaStream_t s);
 int launch_zero_state(denser_ctx* c, int64_t first_block, int64_t n_blocks, cudaStream_t s);
-int launch_sort_pairs(denser_ctx* c, unsigned long long* keys, uint32_t* vals, const int32_t* count, int capacity,
-                      cudaStream_t s);
 int launch_block_order(denser_ctx* c, int64_t n_blocks, cudaStream_t s);
 int configure_kernels(denser_ctx* c);
 int launch_graph_loop(denser_ctx* c, int64_t n_blocks, int k, bool with_gap, cudaStream_t s);
