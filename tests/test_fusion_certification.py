@@ -1,0 +1,202 @@
+"""Soundness of the fusion kernel's float32 certification, on the CPU.
+
+The fusion kernel (Section III-A, Eq. 1) takes each voxel's integer decisions (in front
+of the camera, inside the image, which pixel, u_SDF >= -mu) in float32 together with a
+forward error bound, and recomputes the voxel in float64 only when the bound cannot
+decide.  This test restates that float32 path in numpy (float32 operations round to
+nearest like the GPU's; fused multiply-adds are rounded once, exactly) and checks, on
+random poses far from the origin and on depth maps whose neighbouring pixels disagree
+(so that a wrong pixel shows), that every decision it certifies is the oracle's
+float64 decision, and that it leaves few voxels undecided.  No GPU.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import denser_oracle as O
+from tests.oracle_helpers import grid_from_blocks
+
+F32 = np.float32
+EPS22 = F32(2.0 ** -22)
+
+
+def fma32(a, b, c):
+    """float32 fma(a, b, c) rounded once: the product of two float32 values is exact in
+    float64; the sum's float64 rounding error is recovered exactly (two-sum), and only a
+    float64 sum that sits exactly halfway between two float32 values needs it."""
+    p = np.asarray(a, np.float64) * np.asarray(b, np.float64)
+    c = np.asarray(c, np.float64)
+    s = p + c
+    bp = s - c
+    err = (p - bp) + (c - (s - bp))
+    r = s.astype(F32)
+    lo = np.where(r.astype(np.float64) <= s, r, np.nextafter(r, F32(-np.inf)))
+    hi = np.nextafter(lo, F32(np.inf))
+    mid = (lo.astype(np.float64) + hi.astype(np.float64)) * 0.5
+    at_mid = (s == mid) & (err != 0)
+    return np.where(at_mid, np.where(err > 0, hi, lo), r).astype(F32)
+
+
+def rcp32(z):
+    """Correctly rounded float32 reciprocal (float64 quotient rounded to float32; a tie
+    would need 1/z within 2^-53 of a float32 midpoint, which a float32 z cannot give)."""
+    return (1.0 / np.asarray(z, np.float64)).astype(F32)
+
+
+def floor32(v):
+    return np.floor(np.asarray(v, F32)).astype(np.int64)
+
+
+def kernel_decisions(keys, depth, K, T, prm):
+    """The float32 path of the fusion kernel for every voxel of `keys`: (decided, update,
+    u_tsdf) per voxel, each [nb, 512]."""
+    s = prm.voxel_size
+    Ri, ti = O.pose_inverse(T)
+    keys = np.asarray(keys, np.int64)
+    nb = len(keys)
+    # the block's float64 origin as a float32 hi/lo pair with its bound
+    g = [(keys[:, a].astype(np.float64) * 8.0 + 0.5) * s for a in (1, 2, 3)]
+    c0 = [((Ri[r, 0] * g[0] + Ri[r, 1] * g[1]) + Ri[r, 2] * g[2]) + ti[r] for r in range(3)]
+    hi = [c.astype(F32) for c in c0]
+    lo = [(c0[r] - hi[r].astype(np.float64)).astype(F32) for r in range(3)]
+    amax = np.max(np.abs(np.stack(c0)), axis=0)
+    gmax = (8.0 * np.abs(keys[:, 1:]).sum(axis=1) + 24.0) * s
+    dl = np.ldexp(amax + gmax + np.abs(ti).sum() + 1.0, -44).astype(F32)[:, None]
+    M = (Ri * s).astype(F32).reshape(-1)
+    l = np.arange(512)
+    lxf, lyf, lzf = (l % 8).astype(F32), ((l // 8) % 8).astype(F32), (l // 64).astype(F32)
+    myz = [fma32(M[3 * r + 1], lyf, M[3 * r + 2] * lzf) for r in range(3)]
+    m = [fma32(M[3 * r], lxf, myz[r]) for r in range(3)]
+    x, y, z = [((hi[r][:, None] + m[r][None, :]) + lo[r][:, None]).astype(F32) for r in range(3)]
+    sf = F32(s)
+    s25 = F32(25.0) * sf
+    dx, dy, dz = [fma32(EPS22, (np.abs(v) + s25).astype(F32), dl) for v in (x, y, z)]
+    fxf, fyf, cxf, cyf = F32(K.fx), F32(K.fy), F32(K.cx), F32(K.cy)
+    muf, imuf = F32(prm.mu), F32(1.0 / prm.mu)
+    Wf, Hf = F32(K.width), F32(K.height)
+
+    decided = np.zeros((nb, 512), bool)
+    upd = np.zeros((nb, 512), bool)
+    ut = np.zeros((nb, 512), F32)
+    behind = (z + dz) <= 0
+    decided |= behind
+    front = (z - dz) > 0
+    with np.errstate(all="ignore"):
+        inv = rcp32(z)
+        rx, ry = (x * inv).astype(F32), (y * inv).astype(F32)
+        px, py = fma32(fxf, rx, cxf), fma32(fyf, ry, cyf)
+        iz = rcp32((z - dz).astype(F32))
+        ex = (fxf * (dx + np.abs(rx) * dz) * iz * F32(1.01) + EPS22 * (fxf * np.abs(rx) + np.abs(px) + np.abs(cxf))
+              + F32(1e-6)).astype(F32)
+        ey = (fyf * (dy + np.abs(ry) * dz) * iz * F32(1.01) + EPS22 * (fyf * np.abs(ry) + np.abs(py) + np.abs(cyf))
+              + F32(1e-6)).astype(F32)
+        outside = front & (((px + ex) < 0) | ((px - ex) >= Wf) | ((py + ey) < 0) | ((py - ey) >= Hf))
+        decided |= outside
+        small = (ex < F32(2.0 ** 20)) & (ey < F32(2.0 ** 20))
+        pxi, pyi = floor32(px - ex), floor32(py - ey)
+        pix_ok = front & ~outside & small & (pxi == floor32(px + ex)) & (pyi == floor32(py + ey))
+        d = depth[np.clip(pyi, 0, K.height - 1), np.clip(pxi, 0, K.width - 1)].astype(F32)
+        invalid = pix_ok & ~(np.isfinite(d) & (d > 0))
+        decided |= invalid
+        dh = (d - hi[2][:, None]).astype(F32)
+        us = ((dh - m[2][None, :]) - lo[2][:, None]).astype(F32)
+        eu = (EPS22 * (np.abs(dh) + np.abs(m[2][None, :]) + np.abs(us) + muf + s25) + dl + F32(1e-7)).astype(F32)
+        cert = pix_ok & ~invalid & (np.abs(us + muf) > eu)
+        decided |= cert
+        upd |= cert & (us >= -muf)
+        ut = np.where(cert, np.minimum(F32(1.0), us * imuf), ut).astype(F32)
+    return decided, upd, ut
+
+
+def random_pose(rng, far):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    R = np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                  [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                  [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = rng.uniform(-far, far, 3)
+    return T
+
+
+@pytest.mark.parametrize("seed,far", [(0, 5.0), (1, 300.0), (2, 2000.0)])
+def test_certified_decisions_are_the_oracles(seed, far):
+    rng = np.random.default_rng(seed)
+    prm = O.Params()
+    W, H = 173, 61
+    K = O.Intrinsics(float(rng.uniform(80, 400)), float(rng.uniform(80, 400)), float(rng.uniform(70, 100)),
+                     float(rng.uniform(25, 35)), W, H)
+    T = random_pose(rng, far)
+    # depth maps whose neighbouring pixels disagree, with invalid pixels of both kinds
+    depth = rng.uniform(0.5, 12.0, (H, W)).astype(F32)
+    depth[rng.random((H, W)) < 0.1] = 0.0
+    depth[rng.random((H, W)) < 0.05] = np.nan
+    # blocks around points in the viewing frustum (and some behind the camera)
+    n = 160
+    u, v = rng.uniform(-5, W + 5, n), rng.uniform(-5, H + 5, n)
+    zc = rng.uniform(-2.0, 13.0, n)
+    pc = np.stack([(u - K.cx) * zc / K.fx, (v - K.cy) * zc / K.fy, zc])
+    pg = T[:3, :3] @ pc + T[:3, 3:4]
+    keys = sorted({(0,) + tuple(int(b) for b in np.floor(pg[:, i] / (8 * prm.voxel_size))) for i in range(n)})
+    g = grid_from_blocks(keys)
+    want = O.fuse_depth(g, depth, K, T)
+    decided, upd, ut = kernel_decisions(keys, depth, K, T, prm)
+    assert decided.mean() > 0.97, decided.mean()
+    np.testing.assert_array_equal(upd[decided], want[decided])
+    both = decided & upd
+    assert both.sum() > 1000
+    assert np.max(np.abs(ut[both].astype(np.float64) - g.f[both])) <= 2e-6
+
+
+def _lattice_case():
+    """A camera on the voxel lattice: identity rotation, fx = fy = 100 px, principal point
+    on a pixel edge.  Voxel centres ((i + 0.5) s, ...) then project to rational pixel
+    coordinates, many of them exactly on a pixel edge in float64."""
+    prm = O.Params()
+    K = O.Intrinsics(100.0, 100.0, 80.0, 48.0, 160, 96)
+    keys = [(0, bx, by, bz) for bz in range(0, 3) for by in range(-2, 2) for bx in range(-3, 3)]
+    g = grid_from_blocks(keys)
+    C = g.coords()
+    l = np.arange(512)
+    s = prm.voxel_size
+    xc = ((C[:, 1:2] * 8 + l % 8) + 0.5) * s
+    yc = ((C[:, 2:3] * 8 + (l // 8) % 8) + 0.5) * s
+    zc = ((C[:, 3:4] * 8 + l // 64) + 0.5) * s
+    px = np.floor(K.fx * xc / zc + K.cx).astype(np.int64)
+    py = np.floor(K.fy * yc / zc + K.cy).astype(np.int64)
+    return prm, K, keys, g, zc, px, py
+
+
+def test_pixel_edges_are_deferred_or_right():
+    """Projections on pixel edges, against a checkerboard of valid and invalid pixels:
+    a pixel off by one in either direction flips the update."""
+    prm, K, keys, g, zc, px, py = _lattice_case()
+    yy, xx = np.mgrid[0:K.height, 0:K.width]
+    depth = np.where((xx + yy) % 2 == 0, F32(20.0), F32(0.0)).astype(F32)
+    want = O.fuse_depth(g, depth, K, np.eye(4))
+    decided, upd, ut = kernel_decisions(keys, depth, K, np.eye(4), prm)
+    assert 0.5 < decided.mean() < 1.0  # the edge cases are deferred to float64
+    assert want.sum() > 2000
+    np.testing.assert_array_equal(upd[decided], want[decided])
+
+
+def test_truncation_edges_are_deferred_or_right():
+    """Depths set to z - mu within a few float32 ulps put u_SDF on the truncation edge of
+    Eq. 1 (one voxel per pixel)."""
+    rng = np.random.default_rng(7)
+    prm, K, keys, g, zc, px, py = _lattice_case()
+    ok = (px >= 0) & (px < K.width) & (py >= 0) & (py < K.height)
+    depth = rng.uniform(0.3, 3.0, (K.height, K.width)).astype(F32)
+    sel = np.flatnonzero(ok.reshape(-1))
+    rng.shuffle(sel)
+    for f in sel:
+        b, v = divmod(int(f), 512)
+        depth[py[b, v], px[b, v]] = F32(zc[b, v] - prm.mu) + F32(rng.integers(-3, 4)) * F32(2.0 ** -22)
+    want = O.fuse_depth(g, depth, K, np.eye(4))
+    decided, upd, ut = kernel_decisions(keys, depth, K, np.eye(4), prm)
+    assert 0.5 < decided.mean() < 1.0
+    np.testing.assert_array_equal(upd[decided], want[decided])
+    both = decided & upd
+    assert np.max(np.abs(ut[both].astype(np.float64) - g.f[both])) <= 2e-6
