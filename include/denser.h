@@ -157,8 +157,10 @@ int denser_sync(denser_ctx* ctx, void* stream);
 
 /* Allocation (Section III-A, "Fusing Data"): every block that holds a sample of a
  * valid pixel's ray at depths z = d + n*s/2, n = -N..N, N = ceil(mu/(s/2)), z > 0,
- * is allocated (f = w = 0) if absent.  Sample positions and block keys are computed
- * in float64 in the order the oracle states (bit-exact block sets and indices).
+ * is allocated (f = w = 0) if absent.  Each block key is the floor of a float64
+ * expression written out in a fixed operation order; the kernel evaluates it in float32
+ * with a forward error bound and recomputes it in float64, in that order, wherever the
+ * bound cannot certify the floor, so block sets and indices are exact.
  * depth: float32 [height][width]; K: intrinsics; T_gc: 16 float64 (host memory);
  * segment: block-key segment.  n_new_out (host, may be NULL): number of new blocks;
  * when non-NULL the call waits for the stream. */
@@ -169,8 +171,11 @@ int denser_alloc_blocks(denser_ctx* ctx, const float* depth, const denser_intrin
 /* Projective fusion, Eq. 1 (Section III-A, steps 1-4): every allocated voxel of
  * `segment` is projected into the depth map (nearest pixel = floor of the
  * projection); where the pixel is valid and u_SDF = d - z_c >= -mu, w += 1 and
- * f = (min(1, u_SDF/mu) + w_old f_old) / w.  The update decision is taken in
- * float64 (bit-exact with the oracle); f is accumulated in float32. */
+ * f = (min(1, u_SDF/mu) + w_old f_old) / w.  The update decision (pixel index and
+ * the u_SDF >= -mu test) is that of the float64 expressions in a fixed operation
+ * order: the kernel takes it in float32 with a per-voxel error bound and recomputes it
+ * in float64 wherever the bound cannot certify it, so w is exact; f is accumulated in
+ * float32. */
 int denser_fuse_depth(denser_ctx* ctx, const float* depth, const denser_intrinsics* K,
                       const double T_gc[16], int32_t segment, void* stream);
 
@@ -280,8 +285,8 @@ int denser_disparity_to_depth(const float* disparity, int32_t width, int32_t hei
 
 /* Regularisation (Section III-B/C): Chambolle-Pock iterations on the Omega-aware
  * TV-L2 energy over the allocated blocks, Omega = {w > 0}:
- *   p <- P(p + sigma grad_Omega u_bar),  P(q) = q / max(1, |q|_2)      (Eq. 3)
- *   u <- (u + tau div_Omega p + tau lambda w f) / (1 + tau lambda w)  on Omega (Eq. 4)
+ *   p <- P(p + sigma grad_Omega u_bar),  P(q) = q / max(1, |q|_2)   (grad_Omega: Eq. 3)
+ *   u <- (u + tau div_Omega p + tau lambda w f) / (1 + tau lambda w) on Omega (div_Omega: Eq. 4)
  *   u_bar <- u + theta (u - u_old)
  * start: 0 = from p = u = u_bar = 0 (step 1), 1 = resume from the current state.
  * Runs max_iters iterations, or stops earlier once gap/|P| <= gap_tol (gap_tol > 0
@@ -421,9 +426,11 @@ int denser_pack_weights(const float* w32, void* wf, void* wb, void* stream);
  * latency-critical loop cannot take the device-wide synchronisation that cudaMalloc
  * and cudaFree may cause.  It computes the same P(u) and D(p) as denser_energy, but
  * from caller-owned buffers and with no context: coords int32 [n][4], f, w, u float32
- * [n][512] and p float32 [3][n][512], all in device memory, in the layouts that
- * denser_extract and denser_extract_dual write.  out (host or device memory) receives
- * {P, D}; with a host `out` the call waits for the stream.
+ * [n][512] and p float32 [3][n][512], all in device memory of the current device (or
+ * managed memory), in the layouts that denser_extract and denser_extract_dual write.
+ * coords must be 16-byte aligned and the float buffers 4-byte aligned.  out (host
+ * memory, or 8-byte aligned device memory of the current device) receives {P, D};
+ * with a host `out` the call waits for the stream.
  * Its only working memory is a fixed 2.2 MB array in device memory that every GPU which
  * loads the library holds until the process exits.  That size caps the map at
  * DENSER_NOALLOC_MAX_BLOCKS blocks: a larger n_blocks returns DENSER_ERR_TOO_LARGE.
@@ -432,8 +439,10 @@ int denser_pack_weights(const float* w32, void* wf, void* wb, void* stream);
  * share the array, which keeps the contents of the last call; the call clears what it
  * needs, but calls whose work overlaps on the GPU (different streams, or different
  * host threads) race and must be serialised by the caller.  Repeated or out-of-range
- * coordinates give NaN energies.  Returns DENSER_ERR_INVALID_ARG for host input
- * pointers, NULL pointers or lambda <= 0. */
+ * coordinates give NaN energies.  Returns DENSER_ERR_INVALID_ARG, before launching
+ * anything, for NULL, host, misaligned or other-device input pointers and for
+ * lambda <= 0.  A CUDA runtime error left pending by earlier calls of the process is
+ * cleared on entry, so that it is not reported as this call's failure. */
 #define DENSER_NOALLOC_MAX_BLOCKS 16384
 int denser_energy_noalloc(const int32_t* coords, const float* f, const float* w, const float* u,
                           const float* p, int64_t n_blocks, double lambda, double* out, void* stream);

@@ -25,7 +25,7 @@ namespace {
 
 constexpr int kNaMaxBlocks = DENSER_NOALLOC_MAX_BLOCKS;
 constexpr int kNaSlots = 2 * kNaMaxBlocks;  // power of two
-constexpr int kNaGrid = 608;                // 4 CTAs per SM on 152 SMs
+constexpr int kNaGrid = 608;                // fixed grid of the energy pass (one partial sum pair per CTA)
 constexpr int kNaThreads = 256;
 constexpr int kMaxDevices = 64;
 
@@ -217,14 +217,20 @@ int scratch_for_current_device(unsigned char** out) {
     return DENSER_OK;
 }
 
-bool on_device(const void* p) {
+// True when p is device (or managed) memory that the current device can dereference:
+// device memory of another GPU is rejected, since these kernels read the buffers
+// directly and a foreign pointer without peer access would fault instead of failing.
+bool on_current_device(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 }  // namespace
 }  // namespace denser
@@ -234,8 +240,31 @@ extern "C" int denser_energy_noalloc(const int32_t* coords, const float* f, cons
     using namespace denser;
     if (n_blocks < 0 || !out || !(lambda > 0)) return DENSER_ERR_INVALID_ARG;
     if (n_blocks > kNaMaxBlocks) return DENSER_ERR_TOO_LARGE;
-    if (n_blocks > 0 && (!coords || !f || !w || !u || !p || !on_device(coords) || !on_device(f) || !on_device(w) ||
-                         !on_device(u) || !on_device(p)))
+    // an error left pending by an earlier, unrelated runtime call must not be read as
+    // this call's launch failure below
+    cudaGetLastError();
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DENSER_ERR_CUDA;
+    }
+    if (n_blocks > 0) {
+        // the kernels read coords as int4 and the fields as float: a misaligned pointer
+        // would fault on the device, so it is refused here, before any launch
+        if (!coords || !f || !w || !u || !p || !aligned(coords, 16) || !aligned(f, 4) || !aligned(w, 4) ||
+            !aligned(u, 4) || !aligned(p, 4))
+            return DENSER_ERR_INVALID_ARG;
+        if (!on_current_device(coords, dev) || !on_current_device(f, dev) || !on_current_device(w, dev) ||
+            !on_current_device(u, dev) || !on_current_device(p, dev))
+            return DENSER_ERR_INVALID_ARG;
+    }
+    cudaPointerAttributes oat;
+    if (cudaPointerGetAttributes(&oat, out) != cudaSuccess) {
+        cudaGetLastError();
+        return DENSER_ERR_INVALID_ARG;
+    }
+    const bool dev_out = oat.type == cudaMemoryTypeDevice || oat.type == cudaMemoryTypeManaged;
+    if (dev_out && (!aligned(out, 8) || (oat.type == cudaMemoryTypeDevice && oat.device != dev)))
         return DENSER_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
     int rc = scratch_for_current_device(&base);
@@ -249,7 +278,6 @@ extern "C" int denser_energy_noalloc(const int32_t* coords, const float* f, cons
         na_tables_kernel<<<(n + 7) / 8, 256, 0, st>>>(s, coords, w, n);
     }
     na_energy_kernel<<<kNaGrid, kNaThreads, 0, st>>>(s, f, w, u, p, n, lambda);
-    const bool dev_out = on_device(out);
     double* res = dev_out ? out : reinterpret_cast<double*>(base + kOffOut);
     na_final_kernel<<<1, 1024, 0, st>>>(s, res);
     if (cudaGetLastError() != cudaSuccess) return DENSER_ERR_CUDA;

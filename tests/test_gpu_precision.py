@@ -6,8 +6,7 @@ units): 5e-3 for FP16.  BF16 keeps 8 mantissa bits, so one rounding of a value i
 [0.5, 1) already costs up to 2e-3 and the iterate drifts by a few of its spacings
 (3.9e-3): it is held to 2e-2 and does not meet 5e-3.  Allocation, block indices, w and f are unaffected by the storage type
 (they stay FP32 / exact) and are checked bit for bit against the FP32 context.
-The measured errors are printed so that the precision table in the design notes
-can be refreshed from a run (pytest -s).
+The measured errors are printed (pytest -s).
 """
 
 import numpy as np

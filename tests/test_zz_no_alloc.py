@@ -72,6 +72,21 @@ def test_noalloc_matches_context_energy_on_consecutive_calls():
     assert abs(Pa - Pb) > 1e-6 * abs(Pa)   # the two maps really differ
 
 
+def test_noalloc_leaves_device_memory_unchanged():
+    """After the first call on the device (which looks the array's address up), further
+    calls change neither the device's free memory nor torch's allocator."""
+    n, (P0, _), a = _map_and_buffers(seed=2, iters=5)
+    out_dev = torch.zeros(2, dtype=torch.float64, device="cuda")
+    assert _call(n, a, out_dev) == N.DENSER_OK
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert _call(n, a, out_dev) == N.DENSER_OK
+    free1, alloc1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    assert (free1, alloc1) == (free0, alloc0)
+    assert abs(out_dev[0].item() - P0) <= REL * abs(P0)
+
+
 def test_noalloc_rejects_bad_calls():
     n, _, a = _map_and_buffers(seed=1, iters=2)
     out = np.zeros(2)
@@ -80,6 +95,14 @@ def test_noalloc_rejects_bad_calls():
     host = {k: v.cpu().numpy() for k, v in a.items()}
     assert _call(n, host, out) == N.DENSER_ERR_INVALID_ARG
     assert _call(n, a, out, lam=0.0) == N.DENSER_ERR_INVALID_ARG
+    # coordinates 4 bytes past a 16-byte boundary (the kernels read them as int4) are
+    # refused before anything is launched
+    big = torch.zeros(4 * n + 4, dtype=torch.int32, device="cuda")
+    big[1:1 + 4 * n] = a["coords"].reshape(-1)
+    odd = dict(a)
+    odd["coords"] = big[1:1 + 4 * n]
+    assert odd["coords"].data_ptr() % 16 == 4
+    assert _call(n, odd, out) == N.DENSER_ERR_INVALID_ARG
     # a repeated coordinate is reported as NaN energies
     dup = dict(a)
     dup["coords"] = a["coords"].clone()
