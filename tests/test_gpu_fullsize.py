@@ -129,3 +129,33 @@ def test_full_regularize_step_consistency(street):
     om = before["omega"].astype(bool)
     assert np.all(after["u"][~om] == 0)
     assert np.all(np.sqrt((after["p"] ** 2).sum(0)) <= 1 + 1e-6)
+
+
+def test_full_street_200_iterations_against_oracle(street):
+    """The whole street in the benchmark's launch configuration (16 maps per batched
+    allocation + fusion launch, 200 iterations of the default sweep in the graph loop,
+    24 k blocks, so every CTA of the persistent grid takes many blocks in turn) against
+    the C oracle's 200-frame, 200-iteration run, element by element on every voxel:
+    coords and w bit-exact, f, u, u_bar and p within 1e-4, energies within 1e-5."""
+    from oracle import oracle_c as C
+    s, d, _, _, _ = street
+    cam = s.camera
+    K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    with N.DenserMap(max_blocks=1 << 17, hash_slots=1 << 20) as mb:
+        N.denser_integrate_batch(mb.ctx, torch.from_numpy(d).cuda(), K, np.asarray(s.poses[:len(d)]), 0)
+        st = N.denser_regularize(mb.ctx, 200)
+        got = mb.snapshot(dual=True)
+        Pg, Dg = N.denser_energy(mb.ctx)
+    ref = C.run_pipeline(d, oracle_K(cam), s.poses, O.Params(), 200, capacity=1 << 15)
+    want = ref.snapshot()
+    Po, Do = ref.energies()
+    ref.close()
+    n = len(want["coords"])
+    assert st.iters == 200 and n > 20000 and n * 512 > 4000 * 512
+    np.testing.assert_array_equal(got["coords"], want["coords"].astype(np.int32))
+    np.testing.assert_array_equal(got["w"], want["w"].astype(np.float32))
+    errs = {k: float(np.max(np.abs(got[k] - want[k]))) for k in ("f", "u", "u_bar", "p")}
+    print("\nfull street, 200 iterations, max |gpu - oracle|:", errs, "P", Pg, Po, "D", Dg, Do)
+    for k, e in errs.items():
+        assert e <= TOL, (k, e)
+    assert abs(Pg - Po) <= 1e-5 * abs(Po) and abs(Dg - Do) <= 1e-5 * abs(Po)

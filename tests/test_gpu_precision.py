@@ -1,19 +1,44 @@
 """Reduced-precision storage of u, u_bar and p (FP16 / BF16, FP32 stencil arithmetic,
 FP64 energies) against the FP64 oracle.
 
-Bars on u after 50 and 200 iterations of the tiny workload (normalised TSDF
-units): 5e-3 for FP16.  BF16 keeps 8 mantissa bits, so one rounding of a value in
-[0.5, 1) already costs up to 2e-3 and the iterate drifts by a few of its spacings
-(3.9e-3): it is held to 2e-2 and does not meet 5e-3.  Allocation, block indices, w and f are unaffected by the storage type
-(they stay FP32 / exact) and are checked bit for bit against the FP32 context.
-The measured errors are printed (pytest -s).
+Bars on u, in normalised TSDF units, after 50 and 200 iterations:
+
+  * FP16 is held to 5e-3, the tolerance for reduced-precision results.
+  * BF16 does not meet 5e-3 and is held to its own bound, 2e-2.
+
+Why 5e-3 cannot hold for BF16: storing u rounded to nearest stalls the iteration.
+Near the fixed point u* one primal step moves u by
+(u - u*) tau lambda w / (1 + tau lambda w). A stored u stops moving once that move is
+under half a unit in the last place. So u can stall up to
+(ulp / 2)(1 + tau lambda w) / (tau lambda w) from u*. That is 8.5 half-ulps at w = 1:
+
+  * FP16 (ulp 2^-11 on [0.5, 1)): 2.1e-3, which is what FP16 measures;
+  * BF16 (ulp 2^-8): 1.7e-2.
+
+Splits were tried in an FP64 emulation of the storage roundings. Every split that keeps
+u or p in BF16 stays above 5e-3, and so does stochastic rounding. Only BF16 u_bar with
+FP16 p and u passes, which is FP16 storage in all but name.
+
+p is compared through its divergence. The dual field is unique only up to a
+divergence-free part, which the iteration does not restore. The primal step and the
+dual energy read p only through div p (Eq. 4), so div p is what the storage must keep:
+
+  * FP16 div p is held to 5e-3;
+  * BF16 div p is held to 5e-2.
+
+Allocation, block indices, w and f do not depend on the storage type (they stay FP32
+or exact) and are checked bit for bit against the FP32 context. The second test cuts
+a 50 m crop (blocks with z in [25.6, 74.4] m) out of the 1 km street and compares 200
+iterations in each storage type with the C oracle. The measured errors are printed
+(pytest -s).
 """
 
 import numpy as np
 import pytest
 
-from synth.scenes import tiny_scene
-from tests.pipelines import run_gpu, run_oracle
+from oracle import denser_oracle as O
+from synth.scenes import street_scene, tiny_scene
+from tests.pipelines import oracle_K, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -22,7 +47,19 @@ if not torch.cuda.is_available():
 
 from paper_1604_03734_gb300 import native as N  # noqa: E402
 
-BAR = {0: 1e-4, 1: 5e-3, 2: 2e-2}   # by storage precision: FP32, FP16, BF16
+BAR_U = {0: 1e-4, 1: 5e-3, 2: 2e-2}      # by storage precision: FP32, FP16, BF16
+BAR_DIVP = {0: 1e-4, 1: 5e-3, 2: 5e-2}
+NAME = {N.DENSER_FP32: "fp32", N.DENSER_FP16: "fp16", N.DENSER_BF16: "bf16"}
+
+
+def _errors(g, snap):
+    """max |u - u*|, mean on Omega, max |div p - div p*| (oracle's Omega-aware divergence)."""
+    prob = O.PDProblem(g)
+    om = prob.om
+    du = np.abs(snap["u"].reshape(-1).astype(np.float64) - g.u.reshape(-1))
+    dv_gpu = prob.div(snap["p"].reshape(3, -1).astype(np.float64))
+    dv_ref = prob.div(g.p.reshape(3, -1))
+    return float(du.max()), float(du[om].mean()), float(np.max(np.abs(dv_gpu - dv_ref)[om]))
 
 
 @pytest.fixture(scope="module")
@@ -44,14 +81,63 @@ def test_reduced_precision_parity(tiny, precision, iters):
     m32.close()
     for k in ("coords", "w", "f", "omega"):
         np.testing.assert_array_equal(snap[k], s32[k])
-    err_u = float(np.max(np.abs(snap["u"] - g.u)))
+    err_u, mean_u, err_dv = _errors(g, snap)
     err_p = float(np.max(np.abs(snap["p"] - g.p)))
-    mean_u = float(np.mean(np.abs(snap["u"] - g.u)[g.w > 0]))
-    name = {N.DENSER_FP16: "fp16", N.DENSER_BF16: "bf16"}[precision]
-    print(f"\n{name} {iters} iters: max|u-u*| {err_u:.2e} mean {mean_u:.2e} max|p-p*| {err_p:.2e} "
-          f"rel gap {st.rel_gap:.3e} (fp32 {st32.rel_gap:.3e})")
-    assert err_u <= BAR[precision], err_u
+    print(f"\n{NAME[precision]} {iters} iters: max|u-u*| {err_u:.2e} mean {mean_u:.2e} "
+          f"max|div p - div p*| {err_dv:.2e} max|p-p*| {err_p:.2e} rel gap {st.rel_gap:.3e} "
+          f"(fp32 {st32.rel_gap:.3e})")
+    assert err_u <= BAR_U[precision], err_u
+    assert err_dv <= BAR_DIVP[precision], err_dv
     assert abs(st.primal - st32.primal) <= 1e-2 * abs(st32.primal)
+
+
+@pytest.fixture(scope="module")
+def crop_1km():
+    """Frames 0-159 of the 1 km street (the only frames that see z < 80 m) fused by the
+    GPU (batched, as the benchmark) and by the C oracle; the blocks entirely inside
+    z in [25.6, 74.4] m of each map, in block-index order."""
+    from oracle import oracle_c as C
+    s = street_scene(seed=0, length=1000.0)
+    frames = range(160)
+    d = s.depth_maps(frames, workers=8)
+    cam = s.camera
+    K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    with N.DenserMap(max_blocks=1 << 17, hash_slots=1 << 20) as m:
+        N.denser_integrate_batch(m.ctx, torch.from_numpy(d).cuda(), K, np.asarray(s.poses[:160]), 0)
+        gs = m.snapshot()
+    ref = C.run_pipeline(d, oracle_K(cam), s.poses[:160], O.Params(), 0, capacity=1 << 15)
+    rs = ref.snapshot()
+    ref.close()
+    np.testing.assert_array_equal(gs["coords"], rs["coords"].astype(np.int32))
+    bz = rs["coords"][:, 3]
+    sel = np.nonzero((bz >= 32) & (bz <= 92))[0]     # 32 * 0.8 m = 25.6 m .. 93 * 0.8 m = 74.4 m
+    return gs, rs, sel
+
+
+@pytest.mark.parametrize("precision", [N.DENSER_FP32, N.DENSER_FP16, N.DENSER_BF16])
+def test_crop_of_1km_street(crop_1km, precision):
+    from oracle import oracle_c as C
+    gs, rs, sel = crop_1km
+    assert len(sel) > 10000
+    coords = rs["coords"][sel]
+    ref = C.CMap(O.Params(), len(sel))
+    ref.load_blocks(coords, rs["f"][sel], rs["w"][sel])
+    ref.regularize(200)
+    want = ref.snapshot()
+    ref.close()
+    with N.DenserMap(max_blocks=1 << 15, hash_slots=1 << 17, precision=precision) as m:
+        N.denser_load_blocks(m.ctx, gs["coords"][sel], gs["f"][sel], gs["w"][sel])
+        N.denser_regularize(m.ctx, 200)
+        got = m.snapshot(dual=True)
+    g = O.SparseGrid(O.Params())
+    g.add_blocks([tuple(int(v) for v in c) for c in coords])
+    g.f[:], g.w[:] = want["f"], want["w"]
+    g.u, g.p = want["u"], want["p"]
+    err_u, mean_u, err_dv = _errors(g, got)
+    print(f"\n1 km street, 50 m crop ({len(sel)} blocks), {NAME[precision]}, 200 iters: max|u-u*| {err_u:.2e} "
+          f"mean {mean_u:.2e} max|div p - div p*| {err_dv:.2e}")
+    assert err_u <= BAR_U[precision], err_u
+    assert err_dv <= BAR_DIVP[precision], err_dv
 
 
 @pytest.mark.parametrize("precision", [N.DENSER_FP16, N.DENSER_BF16])
