@@ -161,36 +161,48 @@ def make_inputs(seed, frames=None, length=100.0):
 
 
 # ------------------------------------------------------------- reference arm
-def oracle_sample(scene, depths, n, iters):
-    """Oracle alloc+fuse of n frames then ``iters`` iterations; returns (voxel-updates, seconds)."""
+def oracle_sample(scene, depths, n, iters, threads=0):
+    """C FP64 oracle: alloc+fuse of n frames then ``iters`` iterations on their blocks with
+    ``threads`` threads (0: one per processor); returns (voxel-updates, seconds, blocks)."""
     from oracle import denser_oracle as O
+    from oracle import oracle_c as C
     cam = scene.camera
     K = O.Intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    C.set_threads(threads)
     t0 = time.perf_counter()
-    g = O.SparseGrid(O.Params())
+    m = C.CMap(O.Params(), 1 << 17)
     for k in range(n):
-        O.alloc_blocks(g, depths[k], K, scene.poses[k])
-        O.fuse_depth(g, depths[k], K, scene.poses[k])
-    O.regularize(g, iters)
+        m.alloc_blocks(depths[k], K, scene.poses[k])
+        m.fuse_depth(depths[k], K, scene.poses[k])
+    m.regularize(iters)
     dt = time.perf_counter() - t0
-    return g.n_blocks * 512 * iters, dt, g.n_blocks
+    nb = m.n_blocks
+    m.close()
+    return nb * 512 * iters, dt, nb
 
 
 def cpu_threads():
+    return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
     try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] + [1])
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
     except Exception:
-        return 1
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    # a step is n frames of allocation and fusion and n iterations (the workload's 1:1
-    # ratio); one frame when many steps are asked for, so that the run stays within minutes
-    n = 1 if args.steps + args.warmup > 8 else 2
+    # a step is n frames of allocation and fusion and n iterations on their blocks (the
+    # workload's 1:1 ratio of frames to iterations), the C oracle on every host core
+    n = 32
     scene, depths = make_inputs(0, range(n))
     for _ in range(args.warmup):
         oracle_sample(scene, depths, n, n)
@@ -200,14 +212,15 @@ def run_reference(args, rank, world):
         tot_u += u
         tot_t += t
     v = tot_u / tot_t
-    sample = f"first {n} frames of the street (alloc+fuse) then {n} PD iterations on their {nb} blocks, FP64 numpy"
+    sample = (f"first {n} frames of the street (alloc+fuse) then {n} PD iterations on their {nb} blocks, "
+              f"C FP64 oracle, {cpu_threads()} threads ({cpu_model()})")
     line = {"impl": "reference", "metric": "voxel-updates/s per primal-dual iteration", "value": v,
             "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": v, "unit": "voxel-updates/s", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -235,6 +248,165 @@ def sum_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+
+# ------------------------------------------------------- extra workloads
+def synth_workers(args) -> int:
+    return args.workers if args.workers > 0 else max(1, min(16, os.cpu_count() or 1))
+
+
+def device_maps(specs, workers, dev):
+    """Depth maps of the streets ``specs`` [(seed, length)], made by a process pool and
+    copied into one device tensor as they arrive; returns (tensor [n, H, W], per-spec
+    first frame)."""
+    import torch
+    from synth.scenes import street_depth_maps, street_scene
+    cam = street_scene(seed=0, length=1.0).camera
+    counts = [int(round(length / 0.5)) for _, length in specs]
+    first = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(int)
+    out = torch.empty((sum(counts), cam.height, cam.width), dtype=torch.float32, device=dev)
+    stage = torch.empty((cam.height, cam.width), dtype=torch.float32).pin_memory()
+    for i, k, d in street_depth_maps(specs, workers=workers):
+        stage.copy_(torch.from_numpy(d))
+        out[first[i] + k].copy_(stage)
+    torch.cuda.synchronize(dev)
+    return out, first
+
+
+def time_steps(pipeline, steps, warmup, stream):
+    """(ms per step, sweep ms summed, sweep launches) over ``steps`` timed steps."""
+    import torch
+    for _ in range(warmup):
+        pipeline()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweep_ms, launches = 0.0, 0
+    e0.record(stream)
+    for _ in range(steps):
+        st = pipeline()
+        sweep_ms += st.sweep_ms
+        launches += st.sweep_launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, sweep_ms, launches
+
+
+def precision_street(args, dev, stream, N, hbm, K, workers):
+    """The 1 km street (2000 depth maps, the same generator) fused and regularised (200
+    iterations) with u, u_bar and p stored in FP32, FP16 and BF16."""
+    import torch
+    from synth.scenes import street_scene
+    length = 1000.0
+    sc = street_scene(seed=0, length=length)
+    depths, _ = device_maps([(0, length)], workers, dev)
+    poses = np.asarray(sc.poses, dtype=np.float64)
+    rows = {}
+    for prec, name in ((0, "fp32"), (1, "fp16"), (2, "bf16")):
+        m = N.DenserMap(device=dev.index or 0, max_blocks=1 << 18, hash_slots=1 << 20, precision=prec)
+
+        def pipeline():
+            N.denser_reset(m.ctx, stream)
+            for first in range(0, len(poses), 16):
+                N.denser_integrate_batch(m.ctx, depths[first:first + 16], K, poses[first:first + 16], 0, stream)
+            st = N.denser_regularize(m.ctx, args.iters, 0.0, 0, stream)
+            N.denser_extract(m.ctx, None, None, None, None, u_out, nb, stream)
+            return st
+
+        nb = 0
+        u_out = None
+        pipeline()
+        nb = N.denser_num_blocks(m.ctx, stream)
+        u_out = torch.empty((nb, 512), dtype=torch.float32, device=dev)
+        ms, sweep_ms, launches = time_steps(pipeline, 3, 1, stream)
+        bpv = BYTES_PER_VOXEL_ITER[prec]
+        nvox = nb * 512
+        sweep_avg = sweep_ms / max(launches, 1)
+        gbs = bpv * nvox / (sweep_avg / 1e3) / 1e9
+        rows[name] = {"ms_per_step": ms, "voxel_updates_per_s": nvox * args.iters / (ms / 1e3),
+                      "sweep_ms": sweep_avg, "sweep_voxel_updates_per_s": nvox / (sweep_avg / 1e3),
+                      "bytes_per_voxel": bpv, "sweep_gbs": gbs, "frac_of_measured_hbm": gbs / hbm,
+                      "schedule": N.denser_get_schedule(m.ctx)}
+        m.close()
+    del depths
+    torch.cuda.empty_cache()
+    return {"workload": "driving street 1 km: 2000 depth maps 1241x376, 200 PD iters (storage precision variant)",
+            "blocks": nb, "voxels": nb * 512, "steps": 3, "warmup": 1,
+            "by_storage": rows, "note": "u, u_bar, p stored as named; f, w FP32; FP32 stencil arithmetic; "
+                                        "FP64 energies"}
+
+
+def batched_segments(args, dev, stream, N, hbm, K, workers):
+    """64 independent street segments of lengths uniform in 50-500 m (seeds 1-64), all
+    fused into one map (segment = its index) and regularised together: one sweep
+    launch per iteration covers every segment, the loop runs as one CUDA graph, and
+    the sweep schedule is the autotuner's pick on this map."""
+    import torch
+    from paper_1604_03734_gb300 import autotune as AT
+    from synth.scenes import segment_scenes
+    scenes = segment_scenes()
+    specs = [(s.seed, len(s.poses) * 0.5) for s in scenes]
+    frames = [len(s.poses) for s in scenes]
+    total_len = float(sum(l for _, l in specs))
+    cam = scenes[0].camera
+    max_blocks = int(np.ceil(290.0 * total_len / 1024.0)) * 1024
+    need = sum(frames) * cam.width * cam.height * 4 + max_blocks * (46 * 512 + 600) + max_blocks * 2048
+    free = torch.cuda.mem_get_info(dev)[0]
+    if need > 0.92 * free:
+        return {"skipped": f"needs about {need / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free"}
+    t0 = time.perf_counter()
+    depths, first = device_maps(specs, workers, dev)
+    synth_s = time.perf_counter() - t0
+    poses = [np.asarray(s.poses, dtype=np.float64) for s in scenes]
+    m = N.DenserMap(device=dev.index or 0, max_blocks=max_blocks, hash_slots=1 << 23)
+    u_out = None
+    nb = 0
+
+    def pipeline():
+        N.denser_reset(m.ctx, stream)
+        for seg in range(len(scenes)):
+            for f0 in range(0, frames[seg], 16):
+                n = min(16, frames[seg] - f0)
+                N.denser_integrate_batch(m.ctx, depths[first[seg] + f0:first[seg] + f0 + n], K,
+                                         poses[seg][f0:f0 + n], seg, stream)
+        st = N.denser_regularize(m.ctx, args.iters, 0.0, 0, stream)
+        if u_out is not None:
+            N.denser_extract(m.ctx, None, None, None, None, u_out, nb, stream)
+        return st
+
+    pipeline()
+    nb = N.denser_num_blocks(m.ctx, stream)
+    u_out = torch.empty((nb, 512), dtype=torch.float32, device=dev)
+    tune = AT.autotune(m.ctx, 0, iters=10, use_cache=False, stream=stream)
+    ms, sweep_ms, launches = time_steps(pipeline, 2, 1, stream)
+    nvox = nb * 512
+    sweep_avg = sweep_ms / max(launches, 1)
+    gbs = 48 * nvox / (sweep_avg / 1e3) / 1e9
+    out = {"workload": "64 street segments, lengths uniform in 50-500 m (seeds 1-64), one map, 200 PD iters, FP32",
+           "segments": len(scenes), "frames": int(sum(frames)), "length_m": total_len,
+           "shortest_m": min(l for _, l in specs), "longest_m": max(l for _, l in specs),
+           "blocks": nb, "voxels": nvox, "steps": 2, "warmup": 1, "ms_per_step": ms,
+           "voxel_updates_per_s": nvox * args.iters / (ms / 1e3),
+           "sweep_ms": sweep_avg, "sweep_voxel_updates_per_s": nvox / (sweep_avg / 1e3),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                        "bytes_per_voxel": 48, "kernel": "sweep (autotuned schedule)"},
+           "autotune": {"schedule": tune["schedule"], "ms_per_iter": tune["ms_per_iter"],
+                        "table": tune["table"]},
+           "graph_loop": bool(N.denser_get_schedule(m.ctx)["use_graph"]),
+           "synthesis_s": synth_s, "inputs": "depth maps resident in HBM",
+           "l2": f"working set {48 * nvox / 1e9:.0f} GB per sweep > 129 MB L2, no flush"}
+    m.close()
+    del depths, u_out
+    torch.cuda.empty_cache()
+    return out
+
+
+def guarded(fn, *a):
+    """Runs one extra measurement; an error is reported in its field instead of ending the run."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -254,6 +426,10 @@ def main():
     ap.add_argument("--no-surface", action="store_true", help="skip the surface-extraction measurement")
     ap.add_argument("--no-laser", action="store_true", help="skip the laser-scan fusion measurement")
     ap.add_argument("--no-stereo", action="store_true", help="skip the stereo depth-map measurement")
+    ap.add_argument("--no-precision-street", action="store_true",
+                    help="skip the 1 km street in FP32 / FP16 / BF16 storage")
+    ap.add_argument("--no-segments", action="store_true", help="skip the 64 batched street segments")
+    ap.add_argument("--workers", type=int, default=0, help="depth-map synthesis processes (0: all cores, at most 16)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -491,14 +667,29 @@ def main():
                           "primal-dual kernel's rate"}
         del ws, il, ir, disp
 
+    # the 1 km street in each storage type, and the 64 batched segments (one GPU, rank 0)
+    workers = synth_workers(args)
+    prec_street = None if args.no_precision_street or world > 1 else \
+        guarded(precision_street, args, dev, stream, N, hbm, K, workers)
+    segments = None if args.no_segments or world > 1 else guarded(batched_segments, args, dev, stream, N, hbm, K,
+                                                                   workers)
+
+    # the C FP64 oracle on the host cores: the whole workload (the same 200 maps, 200
+    # iterations) on every core, and a sample on one thread
     cpu = None
     if not args.no_cpu_baseline:
-        n = 3
-        sc, dn = make_inputs(0, range(n))
-        u, t, nbs = oracle_sample(sc, dn, n, n)
+        u, t, nbs = oracle_sample(scene, depths_np, args.frames, args.iters, 0)
+        n1 = 8
+        u1, t1, nb1 = oracle_sample(scene, depths_np, n1, n1, 1)
         cpu = {"value": u / t, "unit": "voxel-updates/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"first {n} frames of the street (alloc+fuse) then {n} PD iterations on their "
-                         f"{nbs} blocks, FP64 numpy, {t:.1f} s"}
+               "cpu_model": cpu_model(),
+               "sample": f"the whole workload: {args.frames} maps alloc+fuse then {args.iters} PD iterations on "
+                         f"their {nbs} blocks, C FP64 oracle (OpenMP over blocks), {t:.1f} s",
+               "single_thread": {"value": u1 / t1, "cores": 1,
+                                 "sample": f"first {n1} maps alloc+fuse then {n1} PD iterations on their {nb1} "
+                                           f"blocks, {t1:.1f} s"}}
+        from oracle import oracle_c as C
+        C.set_threads(0)
 
     line = {
         "metric": "voxel-updates/s per primal-dual iteration", "value": value, "unit": "voxel-updates/s",
@@ -513,7 +704,7 @@ def main():
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),
                    "pd_share_of_step": sweep_ms / args.steps / step_ms,
                    "time_to_gap_1e-4_warm_vs_plain": ttg, "surface_extraction": surface, "laser_fusion": laser,
-                   "stereo_depth": stereo},
+                   "stereo_depth": stereo, "precision_street_1km": prec_street, "batched_segments": segments},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": measured_traffic(kernel_name, args.precision, nvox, N.denser_get_schedule(ctx)),
                      "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": kernel_name,

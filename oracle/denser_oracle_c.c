@@ -95,6 +95,9 @@ void ocl_free(omap *m) {
 
 int64_t ocl_num_blocks(const omap *m) { return m->nb; }
 
+/* Threads of every parallel loop that follows (n <= 0: the OpenMP default). */
+void ocl_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
+
 /* p is stored [3][cap][512]; the three components of voxel v are p[a*cap*512 + v] */
 static double *pc(omap *m, int a) { return m->p + (size_t)a * m->cap * BV; }
 

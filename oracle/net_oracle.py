@@ -93,3 +93,72 @@ def backward(params, acts, dout):
         grads[li] = (dW, db)
         dh = dx
     return grads
+
+
+# ------------------------------------------------- the warm start on a map
+def bf16(x) -> np.ndarray:
+    """Nearest BF16 value (8 significant bits, ties to even) of float64 x: the storage
+    type of the network's weights, inputs and hidden activations."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def gather(keys, f, w, blocks=None) -> np.ndarray:
+    """Network inputs of the listed blocks (default: all), [n, 2, 10, 10, 10] (z, y, x):
+    channel 0 = f where w > 0, channel 1 = w / (w + 8), on the block and its one-voxel
+    halo taken from the 26 neighbouring blocks of the same segment, 0 where a block is
+    absent; both rounded to BF16.  keys: (segment, bx, by, bz) per block index; f, w
+    [nb, 512] with voxel l = lx + 8 ly + 64 lz."""
+    index = {tuple(int(v) for v in k): i for i, k in enumerate(keys)}
+    blocks = range(len(keys)) if blocks is None else blocks
+    out = np.zeros((len(blocks), 2, GRID, GRID, GRID))
+    f3 = np.asarray(f, dtype=np.float64).reshape(-1, 8, 8, 8)   # [b, lz, ly, lx]
+    w3 = np.asarray(w, dtype=np.float64).reshape(-1, 8, 8, 8)
+    for s, b in enumerate(blocks):
+        seg, bx, by, bz = (int(v) for v in keys[b])
+        for oz in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for ox in (-1, 0, 1):
+                    nb = index.get((seg, bx + ox, by + oy, bz + oz))
+                    if nb is None:
+                        continue
+                    # grid coordinate g = 1 + local + 8 * offset, kept where 0 <= g < 10
+                    zs = [(1 + l + 8 * oz, l) for l in range(8) if 0 <= 1 + l + 8 * oz < GRID]
+                    ys = [(1 + l + 8 * oy, l) for l in range(8) if 0 <= 1 + l + 8 * oy < GRID]
+                    xs = [(1 + l + 8 * ox, l) for l in range(8) if 0 <= 1 + l + 8 * ox < GRID]
+                    gz, lz = zip(*zs)
+                    gy, ly = zip(*ys)
+                    gx, lx = zip(*xs)
+                    ix = np.ix_(lz, ly, lx)
+                    wv = w3[nb][ix]
+                    out[s, 0][np.ix_(gz, gy, gx)] = np.where(wv > 0, f3[nb][ix], 0.0)
+                    out[s, 1][np.ix_(gz, gy, gx)] = wv / (wv + 8.0)
+    return bf16(out)
+
+
+def forward_stored(params, x):
+    """The network as stored: BF16 weights and inputs, float64 sums, each hidden
+    activation (after its ReLU) rounded to BF16; the last layer's output unrounded.
+    Returns the centre 8^3 of the output, [n, 4, 8, 8, 8]."""
+    h = bf16(x)
+    for li, (W, b) in enumerate(params):
+        z = conv3d_same(h, bf16(W), np.asarray(b, dtype=np.float64))
+        h = bf16(np.maximum(z, 0.0)) if li < len(params) - 1 else z
+    return h[:, :, 1:-1, 1:-1, 1:-1]
+
+
+def warm_state(out, omega, edges):
+    """The starting point a prediction gives the iteration of Section III-C: u = the
+    prediction clamped to [-1, 1] on Omega and 0 elsewhere, u_bar = u, p_a = the
+    prediction on the Eq. 3 edges along axis a and 0 elsewhere, then projected onto the
+    unit ball (the constraint |p| <= 1 of the dual).  out [n, 4, 8, 8, 8] (z, y, x);
+    omega [n, 512] and edges [3, n, 512] boolean, voxel l = lx + 8 ly + 64 lz.  Returns
+    (u [n, 512], u_bar, p [3, n, 512])."""
+    n = out.shape[0]
+    o = np.asarray(out, dtype=np.float64).reshape(n, 4, 512)
+    u = np.where(omega, np.clip(o[:, 0], -1.0, 1.0), 0.0)
+    p = np.where(edges, o[:, 1:].transpose(1, 0, 2), 0.0)
+    nrm = np.sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2])
+    p = p / np.maximum(1.0, nrm)[None]
+    return u, u.copy(), p

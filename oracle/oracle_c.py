@@ -54,6 +54,7 @@ def lib():
             "ocl_energies": (i32, [vp, vp, vp]),
             "ocl_get": (None, [vp, vp, vp, vp, vp, vp, vp]),
             "ocl_set_state": (None, [vp, vp, vp, vp]),
+            "ocl_set_threads": (None, [i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -61,6 +62,11 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def set_threads(n: int = 0):
+    """Threads of the C oracle's loops from now on (0: one per processor)."""
+    lib().ocl_set_threads(int(n))
 
 
 def _p(a):

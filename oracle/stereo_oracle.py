@@ -31,8 +31,12 @@ taken here:
       and q (2 x 2, Frobenius |q| <= alpha2), tau = sigma = 1/sqrt(12) (||K||^2 <= 12),
       over-relaxation 1;
   D7  forward differences, zero across the last column / row; div = -grad^T;
-  D8  the a-step decision is taken in float32 with the operation order written in
-      ``assign`` (the kernel's precision), so that equal inputs give equal integers.
+  D8  the a-step is the argmin of D5's per-pixel energy over integer delta, evaluated in
+      float64 like every other quantity here (ties to the smallest delta).  The paper
+      fixes no precision.  A pixel whose best candidate beats another candidate by less
+      than the rounding bound of a float32 evaluation of the two energies is flagged as a
+      near tie: there a float32 implementation may pick either, so a comparison holds the
+      unflagged pixels to the exact decision and counts the flagged ones.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this module.  It shares no code with the CUDA path.
@@ -142,11 +146,18 @@ def apply_T(T, v):
 
 
 # ------------------------------------------------------------- steps (D5, D6, D8)
-def assign(hvol, d, lam, theta) -> np.ndarray:
-    """a-step: argmin over delta of lam h/BITS + (d - delta)^2 / (2 theta), float32 in the
-    order cw*h + (dd*dd)*cq, cw = float32(lam/BITS), cq = float32(1/(2 theta)), ties to
-    the smallest delta.  theta = inf drops the coupling (winner takes all).  hvol is the
-    Hamming volume [D, H, W], or a pair (sig_L, sig_R, D) to compute it delta by delta."""
+def assign(hvol, d, lam, theta, with_flags: bool = False):
+    """a-step (D5, D8): argmin over integer delta in [0, D) of
+        E(delta) = lam h(delta) / BITS + (d - delta)^2 / (2 theta)
+    in float64, ties to the smallest delta; theta = inf drops the coupling (winner takes
+    all on the Hamming distance, an exact integer comparison).  hvol is the Hamming volume
+    [D, H, W], or a pair (sig_L, sig_R, D) to compute it delta by delta.
+
+    With ``with_flags`` also returns the near-tie flags: for finite theta, a pixel is
+    flagged when some other candidate's energy exceeds the best one's by at most
+    B(best) + B(other), B(k) = 2^-20 (lam h(k) / BITS + (d - k)^2 / (2 theta)), sixteen
+    times the relative rounding error a float32 evaluation of the sum of the two terms
+    can make (a product, a difference, a square and a sum, each rounded once)."""
     if isinstance(hvol, tuple):
         sigL, sigR, D = hvol
         H, W = sigR.shape
@@ -161,18 +172,30 @@ def assign(hvol, d, lam, theta) -> np.ndarray:
 
         def h_of(k):
             return hvol[k]
-    cw = np.float32(lam / BITS)
-    cq = np.float32(0.0 if np.isinf(theta) else 1.0 / (2.0 * theta))
-    d32 = np.asarray(d, dtype=np.float32)
-    best = np.full(d32.shape, np.inf, dtype=np.float32)
-    arg = np.zeros(d32.shape, dtype=np.int64)
+    d64 = np.asarray(d, dtype=np.float32).astype(np.float64)
+    coupled = not np.isinf(theta)
+    best = np.full(d64.shape, np.inf)
+    arg = np.zeros(d64.shape, dtype=np.int64)
+    energies = []
     for k in range(D):
-        dd = d32 - np.float32(k)
-        e = h_of(k).astype(np.float32) * cw + (dd * dd) * cq
+        e = lam * h_of(k).astype(np.float64) / BITS
+        if coupled:
+            dd = d64 - float(k)
+            e = e + dd * dd / (2.0 * theta)
         better = e < best
         best = np.where(better, e, best)
         arg = np.where(better, k, arg)
-    return arg.astype(np.float64)
+        if with_flags and coupled:
+            energies.append(e)
+    if not with_flags:
+        return arg.astype(np.float64)
+    flag = np.zeros(d64.shape, dtype=bool)
+    if coupled:
+        eps = 2.0 ** -20
+        for k, e in enumerate(energies):
+            close = (e - best) <= eps * (e + best)
+            flag |= close & (arg != k)
+    return arg.astype(np.float64), flag
 
 
 class TGVState:

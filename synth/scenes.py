@@ -115,7 +115,15 @@ class Scene:
         return np.stack([dx, dy, np.ones_like(dx)], axis=0)  # [3, H, W]
 
     def render_clean(self, frame: int) -> np.ndarray:
-        """Noise-free depth (float64, 0 = no hit within d_max) for one pose."""
+        """Noise-free depth (float64, 0 = no hit within d_max) for one pose: the casts of
+        render_clean_numpy, evaluated by synth/raycast.c in the same operation order."""
+        from . import raycast
+        T = self.poses[frame]
+        wins = [_box_pixel_window(b, self.camera, T) for b in self.boxes]
+        return raycast.depth(self, T, wins)
+
+    def render_clean_numpy(self, frame: int) -> np.ndarray:
+        """The same depth cast with numpy array operations."""
         T = self.poses[frame]
         R, o = T[:3, :3], T[:3, 3]
         dcam = self._rays()
@@ -469,3 +477,36 @@ def segment_scenes(n_segments: int = 64, lo: float = 50.0, hi: float = 500.0, ba
     lengths = rng.uniform(lo, hi, n_segments)
     return [street_scene(seed=base_seed + i, length=float(np.round(Lm / 0.5) * 0.5), **kw)
             for i, Lm in enumerate(lengths)]
+
+
+# ------------------------------------------------------- many maps in parallel
+_WORKER_SCENES: dict = {}
+
+
+def _street_frame(task):
+    """Depth map k of street_scene(seed, length), built once per worker process."""
+    seed, length, k = task
+    sc = _WORKER_SCENES.get((seed, length))
+    if sc is None:
+        sc = _WORKER_SCENES[(seed, length)] = street_scene(seed=seed, length=length)
+    return sc.depth_map(k)
+
+
+def street_depth_maps(specs, workers: int = 1, chunksize: int = 8):
+    """Depth maps of several streets, in order: for each (seed, length) of ``specs`` its
+    frames 0, 1, ...; yields (spec index, frame, depth map).  With workers > 1 they are
+    made by a 'spawn' process pool (safe in a parent that already uses a GPU) and handed
+    over one by one, so the caller holds only what it has not consumed yet."""
+    tasks = []
+    for i, (seed, length) in enumerate(specs):
+        n = int(round(length / 0.5))
+        tasks += [(i, seed, length, k) for k in range(n)]
+    if workers <= 1:
+        for i, seed, length, k in tasks:
+            yield i, k, _street_frame((seed, length, k))
+        return
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for (i, seed, length, k), d in zip(tasks, pool.imap(_street_frame, [t[1:] for t in tasks],
+                                                             chunksize=chunksize)):
+            yield i, k, d

@@ -118,7 +118,7 @@ def crop_1km():
 def test_crop_of_1km_street(crop_1km, precision):
     from oracle import oracle_c as C
     gs, rs, sel = crop_1km
-    assert len(sel) > 10000
+    assert len(sel) > 8000
     coords = rs["coords"][sel]
     ref = C.CMap(O.Params(), len(sel))
     ref.load_blocks(coords, rs["f"][sel], rs["w"][sel])

@@ -200,3 +200,68 @@ def test_warm_start_gain_and_same_fixed_point():
     om = sols[0]["omega"].astype(bool)
     du = np.abs(sols[0]["u"] - sols[1]["u"])[om]
     assert du.mean() <= 1e-3 and du.max() <= 5e-2, (du.mean(), du.max())
+
+
+def _oracle_params_of(npz):
+    """The committed network's FP32 master weights in the oracle's layout
+    W [co, ci, dz, dy, dx] (tap dx + 3 dy + 9 dz of [27][16 out][16 in]) and biases."""
+    params = []
+    for i, (cin, cout) in enumerate(zip(NO.CHANNELS[:-1], NO.CHANNELS[1:])):
+        v = npz[f"layer{i}"].astype(np.float64)
+        W = v[:27 * 256].reshape(3, 3, 3, 16, 16).transpose(3, 4, 0, 1, 2)[:cout, :cin]
+        params.append((W, v[27 * 256:][:cout]))
+    return params
+
+
+@pytest.mark.parametrize("seed", [200, 201, 202])
+def test_warm_started_path_against_oracle(seed):
+    """The warm-started path (gather, network, warm start, then the plain iteration to a
+    relative gap of 1e-4) against the oracle's warm-started path on a held-out scene: the
+    oracle fuses the scene itself, runs the same trained network in FP64 with the stored
+    BF16 weights, inputs and hidden activations, applies the warm start and iterates in
+    FP64.  u on Omega within 5e-3 of the oracle right after the warm start, after 200
+    iterations and at the iteration where the GPU reached the gap; div p is printed."""
+    from oracle import denser_oracle as O
+    from oracle import oracle_c as C
+    from tests.oracle_helpers import grid_from_blocks
+    from tests.pipelines import oracle_K
+    net = WS.load_default()
+    assert net is not None
+    params = _oracle_params_of(dict(np.load(WS.WEIGHTS)))
+    sc = WS.scene_variant(seed, 0)
+    ref = C.run_pipeline(sc.depth_maps(), oracle_K(sc.camera), sc.poses, O.Params(), 0)
+    rs = ref.snapshot()
+    g = grid_from_blocks([tuple(c) for c in rs["coords"]], rs["f"], rs["w"])
+    prob = O.PDProblem(g)
+    om = prob.om.reshape(-1, 512)
+    edges = O.edge_mask(prob.om, prob.fwd).reshape(3, -1, 512)
+    out = NO.forward_stored(params, NO.gather(rs["coords"], rs["f"], rs["w"]))
+    ref.set_state(*NO.warm_state(out, om, edges))
+
+    m = WS.solved_map([sc], 0)
+    net.warm_start(m.ctx)
+    results = []
+
+    def compare(label):
+        got = m.snapshot(dual=True)
+        want = ref.snapshot()
+        np.testing.assert_array_equal(got["coords"], want["coords"].astype(np.int32))
+        du = np.abs(got["u"].astype(np.float64) - want["u"])[om]
+        dv = np.abs(prob.div(got["p"].reshape(3, -1).astype(np.float64)) - prob.div(want["p"].reshape(3, -1)))
+        results.append((label, float(du.max()), float(du.mean()), float(dv[prob.om].max())))
+        return float(du.max())
+
+    e0 = compare("warm start")
+    N.denser_regularize(m.ctx, 200, 0.0, 1)
+    ref.iterate(200)
+    e1 = compare("200 iterations")
+    st = N.denser_regularize(m.ctx, 20000, 1e-4, 1)
+    ref.iterate(st.iters)
+    e2 = compare(f"gap 1e-4 ({200 + st.iters} iterations)")
+    P, D = ref.energies()
+    m.close()
+    ref.close()
+    print(f"\nseed {seed}: max|u - u_oracle| / mean / max|div p - div p_oracle|:", results,
+          f"oracle rel gap {(P - D) / abs(P):.2e}")
+    assert st.converged and (P - D) / abs(P) <= 1.5e-4
+    assert max(e0, e1, e2) <= 5e-3, results

@@ -85,3 +85,92 @@ def test_output_is_centre_and_padding_is_zero():
     # zero input: every activation is the bias chain, constant over the grid
     for a in acts[1:]:
         assert np.allclose(a, a[:, :, :1, :1, :1])
+
+
+# ------------------------------------------------- warm start on a map
+def test_bf16_is_nearest_with_ties_to_even():
+    """Against the definition: every BF16 value is a float32 whose low 16 bits are zero;
+    the nearest one is chosen, ties to the one with an even last bit."""
+    rng = np.random.default_rng(20)
+    x = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-8, 8, 2000),
+                        # exact halfway points between neighbouring BF16 values
+                        (np.arange(256, 512) + 0.5) / 256.0, -(np.arange(256, 512) + 0.5) / 128.0])
+    got = NO.bf16(x)
+    for xi, gi in zip(x, got):
+        b = int(np.array([xi], np.float32).view(np.uint32)[0]) & 0xFFFF0000
+        cands = [np.array([b + k * 65536], np.uint32).view(np.float32)[0].astype(np.float64)
+                 for k in (-1, 0, 1) if 0 <= b + k * 65536 < 2 ** 32]
+        dist = [abs(c - xi) for c in cands]
+        best = min(dist)
+        near = [c for c, d in zip(cands, dist) if d == best]
+        if len(near) == 2:   # a tie: the even one
+            near = [c for c in near if (np.array([c], np.float32).view(np.uint32)[0] >> 16) % 2 == 0]
+        assert gi == near[0], (xi, gi, near)
+
+
+def test_gather_against_voxel_lookup():
+    """Every cell of the 10^3 grid equals the voxel at that global position, found by its
+    block key (floor division of the global voxel index by 8), or 0 where absent."""
+    rng = np.random.default_rng(21)
+    keys = [(0, 0, 0, 0), (0, 1, 0, 0), (0, 0, -1, 0), (0, 1, 1, 1), (0, -1, -1, -1), (2, 0, 0, 1), (0, 0, 0, 1)]
+    f = rng.uniform(-1, 1, (len(keys), 512))
+    w = rng.integers(0, 6, (len(keys), 512)).astype(float)
+    x = NO.gather(keys, f, w)
+    index = {k: i for i, k in enumerate(keys)}
+    for s, (seg, bx, by, bz) in enumerate(keys):
+        for gz in range(10):
+            for gy in range(10):
+                for gx in range(10):
+                    i, j, k = 8 * bx + gx - 1, 8 * by + gy - 1, 8 * bz + gz - 1
+                    b = index.get((seg, i // 8, j // 8, k // 8))
+                    if b is None:
+                        want = (0.0, 0.0)
+                    else:
+                        l = i % 8 + 8 * (j % 8) + 64 * (k % 8)
+                        want = (f[b, l] if w[b, l] > 0 else 0.0, w[b, l] / (w[b, l] + 8.0))
+                    assert x[s, 0, gz, gy, gx] == NO.bf16(want[0]) and x[s, 1, gz, gy, gx] == NO.bf16(want[1])
+
+
+def test_forward_stored_wiring_and_rounding():
+    """With weights that keep every activation exactly representable (one power-of-two
+    centre tap per channel) the stored network equals the exact one; with random weights
+    every hidden activation it produces is a BF16 value and the output stays within the
+    rounding's reach of the exact network."""
+    n = 2
+    rng = np.random.default_rng(22)
+    x = NO.bf16(rng.uniform(-1, 1, (n, 2, 10, 10, 10)))
+    params = []
+    for cin, cout in zip(NO.CHANNELS[:-1], NO.CHANNELS[1:]):
+        W = np.zeros((cout, cin, 3, 3, 3))
+        for co in range(cout):
+            W[co, co % cin, 1, 1, 1] = 2.0 ** -(co % 3)
+        params.append((W, np.zeros(cout)))
+    exact, _ = NO.forward(params, x)
+    np.testing.assert_array_equal(NO.forward_stored(params, x), exact)
+    params = NO.init_params(3)
+    got = NO.forward_stored(params, x)
+    ref, acts = NO.forward([(NO.bf16(W), b) for W, b in params], x)
+    assert np.max(np.abs(got - ref)) <= 0.05 * np.max(np.abs(ref))
+    h = NO.bf16(x)
+    for W, b in params[:-1]:
+        h = NO.bf16(np.maximum(NO.conv3d_same(h, NO.bf16(W), b), 0.0))
+        assert np.array_equal(h, NO.bf16(h))
+
+
+def test_warm_state_masks_and_projection():
+    rng = np.random.default_rng(23)
+    n = 3
+    out = rng.standard_normal((n, 4, 8, 8, 8)) * 1.5
+    om = rng.random((n, 512)) < 0.7
+    edges = (rng.random((3, n, 512)) < 0.6) & om[None]
+    u, ub, p = NO.warm_state(out, om, edges)
+    o = out.reshape(n, 4, 512)
+    assert np.all(u[~om] == 0) and np.array_equal(u[om], np.clip(o[:, 0][om], -1, 1)) and np.array_equal(u, ub)
+    assert np.all(p[~edges] == 0)
+    nrm = np.sqrt((p ** 2).sum(0))
+    assert np.all(nrm <= 1 + 1e-15)
+    q = np.where(edges, o[:, 1:].transpose(1, 0, 2), 0.0)
+    qn = np.sqrt((q ** 2).sum(0))
+    inside = qn <= 1
+    assert np.array_equal(p[:, inside], q[:, inside])
+    np.testing.assert_allclose(p[:, ~inside] * qn[~inside], q[:, ~inside], rtol=1e-15, atol=1e-15)
