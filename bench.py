@@ -260,7 +260,7 @@ def device_maps(specs, workers, dev):
     first frame)."""
     import torch
     from synth.scenes import street_depth_maps, street_scene
-    cam = street_scene(seed=0, length=1.0).camera
+    cam = street_scene(seed=specs[0][0], length=specs[0][1]).camera
     counts = [int(round(length / 0.5)) for _, length in specs]
     first = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(int)
     out = torch.empty((sum(counts), cam.height, cam.width), dtype=torch.float32, device=dev)

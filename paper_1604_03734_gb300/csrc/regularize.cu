@@ -760,12 +760,52 @@ __device__ __forceinline__ void convert_row_halos(RowTiles& s, const HaloRaw<T>&
     if (ly == 7 && lz == 0) row(s.ub[r10(8, -1)], raw.ub[r10(8, -1)]);
 }
 
+// Per-thread stage of the prefetching row sweep: thread r's slot holds row r of the
+// next block's own fields (u_bar, p_x, p_y, p_z, u as stored, f, w as float32) and the
+// Omega word that holds the row's bits.  Each thread copies and later reads only its own
+// slot, so the stage needs no barrier.  The slot strides (240 and 176 bytes, 60 and 44
+// words) put the 16-byte reads of eight consecutive threads on distinct banks.
+template <typename T>
+struct OwnSlot {
+    static constexpr int kRowT = 8 * (int)sizeof(T);
+    static constexpr int kUb = 0;
+    static constexpr int kP = kRowT;
+    static constexpr int kU = 4 * kRowT;
+    static constexpr int kF = 5 * kRowT;
+    static constexpr int kW = kF + 32;
+    static constexpr int kBits = kW + 32;
+    static constexpr int kBytes = sizeof(T) == 4 ? 240 : 176;
+    static_assert(kBits + 4 <= kBytes, "slot too small");
+};
+
+// 8 values of a stored field (32 or 16 bytes) by cp.async into a slot.
+template <typename T>
+__device__ inline void cp_row(char* dst, const T* src) {
+    cp_async16(dst, src);
+    if constexpr (sizeof(T) == 4) cp_async16(dst + 16, src + 4);
+}
+
+// Issues the copies of row r of block b's own fields into the thread's slot.
+template <typename T>
+__device__ __forceinline__ void issue_own_row(const SweepArgs<T>& a, char* slot, int b, int r) {
+    using L = OwnSlot<T>;
+    const size_t base = (size_t)b * kBlockVoxels + 8 * r;
+    cp_row<T>(slot + L::kUb, a.ub_in + base);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cp_row<T>(slot + L::kP + c * L::kRowT, a.p_in + c * a.pstride + base);
+    cp_row<T>(slot + L::kU, a.u + base);
+    cp_row<float>(slot + L::kF, a.f + base);
+    cp_row<float>(slot + L::kW, a.w + base);
+    cp_async4(slot + L::kBits, a.bits + (size_t)b * 16 + (r >> 2));
+}
+
 // One block of the row sweep: staging of the rows, faces and edges, the dual steps,
 // the primal step and the relaxation.  `stage` holds the block's own fields when they
 // were prefetched into shared memory (else they are read from global memory).
-template <typename T, bool ASYNC = false>
+template <typename T, bool ASYNC = false, bool PREFETCH = false>
 __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, int b, int r, const char* stage,
-                                           const int* nb, HaloRaw<T>* raw = nullptr) {
+                                           const int* nb, HaloRaw<T>* raw = nullptr, char* slot = nullptr,
+                                           int b_next = -1) {
     const int ly = r & 7, lz = r >> 3;
     const int rr = r10(ly, lz);
     const size_t ps = a.pstride;
@@ -776,7 +816,20 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
     if constexpr (kAsync) issue_row_halos<T>(a, s, *raw, r, ly, lz, nb, hom);
     float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
     unsigned om_r;
-    if (stage) {  // this block's rows were brought into shared memory by the bulk copies
+    if constexpr (PREFETCH) {  // this block's row r is in the thread's slot (copied one block ago)
+        using L = OwnSlot<T>;
+        ld_row_smem<T>(reinterpret_cast<const T*>(slot + L::kUb), ub);
+        ld_row_smem<T>(reinterpret_cast<const T*>(slot + L::kP), p0);
+        ld_row_smem<T>(reinterpret_cast<const T*>(slot + L::kP + L::kRowT), p1);
+        ld_row_smem<T>(reinterpret_cast<const T*>(slot + L::kP + 2 * L::kRowT), p2);
+        ld_row_smem<T>(reinterpret_cast<const T*>(slot + L::kU), uo);
+        lds_row(reinterpret_cast<const float*>(slot + L::kF), fv);
+        lds_row(reinterpret_cast<const float*>(slot + L::kW), wv);
+        om_r = (*reinterpret_cast<const uint32_t*>(slot + L::kBits) >> (8 * (r & 3))) & 0xffu;
+        // the slot is free again: bring in the next block's row while this one computes
+        if (b_next >= 0) issue_own_row<T>(a, slot, b_next, r);
+        cp_async_commit();
+    } else if (stage) {  // this block's rows were brought into shared memory by the bulk copies
         using L = RowStage<T>;
         ld_row_smem<T>(reinterpret_cast<const T*>(stage + L::kUb) + 8 * r, ub);
         ld_row_smem<T>(reinterpret_cast<const T*>(stage + L::kP) + 8 * r, p0);
@@ -811,7 +864,13 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
         if (lz == 0) s.om[r10(ly, -1)] = (unsigned short)hom[2];
         if (ly == 0 && lz == 7) s.om[r10(-1, 8)] = (unsigned short)hom[3];
         if (ly == 7 && lz == 0) s.om[r10(8, -1)] = (unsigned short)hom[3];
-        cp_async_wait_all();
+        if constexpr (PREFETCH) {
+            // the halo group is complete; the next block's rows (the newest group) may
+            // still be in flight
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            cp_async_wait_all();
+        }
         if constexpr (sizeof(T) != 4) convert_row_halos<T>(s, *raw, r, ly, lz);
     } else {
         {
@@ -999,6 +1058,42 @@ __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs
             load_nbr_row(a.nbr, b_next, nb_next);
         }
         rows_block<T, ASYNC>(a, s, b, threadIdx.x, nullptr, nb, &raw);
+        __syncthreads();  // the tiles are rewritten for the next block
+        b = b_next;
+#pragma unroll
+        for (int i = 0; i < kNeighbours; ++i) nb[i] = nb_next[i];
+    }
+}
+
+// Row sweep with asynchronous halos and the next block's own rows prefetched: while a
+// CTA computes block k, every thread's copies of its row of block k + grid are already
+// in flight into its stage slot, so the DRAM latency of a block's own fields overlaps
+// the previous block's arithmetic instead of following it.  Same arithmetic as every
+// other variant (bit-identical iterates).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_prefetch_kernel(SweepArgs<T> a) {
+    __shared__ RowTiles s;
+    __shared__ HaloRaw<T> raw;
+    __shared__ __align__(16) char stage[kRowThreads * OwnSlot<T>::kBytes];
+    const int G = gridDim.x;
+    const int r = threadIdx.x;
+    char* slot = stage + r * OwnSlot<T>::kBytes;
+    int k = blockIdx.x;
+    if (k >= a.n_blocks) return;
+    int b = a.order ? __ldg(a.order + k) : k;
+    int nb[kNeighbours], nb_next[kNeighbours];
+    load_nbr_row(a.nbr, b, nb);
+    issue_own_row<T>(a, slot, b, r);
+    cp_async_commit();
+    for (; k < a.n_blocks; k += G) {
+        const int kn = k + G;
+        int b_next = -1;
+        if (kn < a.n_blocks) {
+            b_next = a.order ? __ldg(a.order + kn) : kn;
+            load_nbr_row(a.nbr, b_next, nb_next);
+        }
+        cp_async_wait_all();  // this block's own rows (and nothing else) were pending
+        rows_block<T, true, true>(a, s, b, r, nullptr, nb, &raw, slot, b_next);
         __syncthreads();  // the tiles are rewritten for the next block
         b = b_next;
 #pragma unroll
@@ -1276,6 +1371,19 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 8, true>, kRowThreads, 0);
             sweep_rows_kernel<T, 8, true><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
                                             kRowThreads, 0, s>>>(a);
+        }
+    } else if (c->sched.sweep_kernel == 5) {
+        // prefetching row sweep (about 27 KB of shared memory per CTA): ctas_per_sm 2 caps
+        // the registers for 10 resident CTAs, otherwise for 8
+        int per_sm = 0;
+        if (c->sched.ctas_per_sm == 2) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_prefetch_kernel<T, 10>, kRowThreads, 0);
+            sweep_rows_prefetch_kernel<T, 10>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_prefetch_kernel<T, 8>, kRowThreads, 0);
+            sweep_rows_prefetch_kernel<T, 8>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
         }
     } else if (c->sched.sweep_kernel == 3) {
         int per_sm = 0;
