@@ -667,6 +667,39 @@ def main():
                           "primal-dual kernel's rate"}
         del ws, il, ir, disp
 
+    # fusion roofline: the same 200 maps allocated and fused with the library's fusion
+    # profiling on (CUDA events around the key pass, the rest of the allocation, culling
+    # and the fusion kernel; the call waits after each group, so this is not the step above)
+    fusion = None
+    if args.batch > 1:
+        N.denser_set_fusion_profiling(ctx, True)
+        reps = 3
+        for _ in range(reps):
+            N.denser_reset(ctx, stream)
+            for first in range(0, args.frames, args.batch):
+                N.denser_integrate_batch(ctx, depths_dev[first:first + args.batch], K,
+                                         poses_arr[first:first + args.batch], 0, stream)
+        pr = N.denser_get_fusion_profile(ctx)
+        N.denser_set_fusion_profiling(ctx, False)
+        npix = cam.width * cam.height
+        fuse_bytes = 16.0 * 512 * pr["listed_blocks"] + 4.0 * npix * pr["maps"]
+        key_bytes = 4.0 * npix * pr["maps"] + 16.0 * pr["new_blocks"]
+        fusion = {"maps": pr["maps"] // reps, "groups": pr["groups"] // reps,
+                  "listed_blocks_per_group": pr["listed_blocks"] / max(pr["groups"], 1),
+                  "ms_per_pass": (pr["key_pass_ms"] + pr["alloc_rest_ms"] + pr["cull_ms"] + pr["fuse_ms"]) / reps,
+                  "key_pass": {"ms_per_map": pr["key_pass_ms"] / pr["maps"],
+                               "achieved_gbs": key_bytes / (pr["key_pass_ms"] / 1e3) / 1e9,
+                               "frac_of_measured_hbm": key_bytes / (pr["key_pass_ms"] / 1e3) / 1e9 / hbm,
+                               "bytes": "4 B of depth per pixel + 16 B per new block key"},
+                  "fuse_kernel": {"ms_per_map": pr["fuse_ms"] / pr["maps"],
+                                  "achieved_gbs": fuse_bytes / (pr["fuse_ms"] / 1e3) / 1e9,
+                                  "frac_of_measured_hbm": fuse_bytes / (pr["fuse_ms"] / 1e3) / 1e9 / hbm,
+                                  "bytes": "16 B per listed voxel per launch (f, w read and written once for the "
+                                           "group's maps) + 4 B of depth per pixel and map"},
+                  "alloc_rest_ms_per_map": pr["alloc_rest_ms"] / pr["maps"],
+                  "cull_ms_per_map": pr["cull_ms"] / pr["maps"],
+                  "timing": "CUDA events inside the library, fusion profiling on (waits after each group)"}
+
     # the 1 km street in each storage type, and the 64 batched segments (one GPU, rank 0)
     workers = synth_workers(args)
     prec_street = None if args.no_precision_street or world > 1 else \
@@ -704,7 +737,8 @@ def main():
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),
                    "pd_share_of_step": sweep_ms / args.steps / step_ms,
                    "time_to_gap_1e-4_warm_vs_plain": ttg, "surface_extraction": surface, "laser_fusion": laser,
-                   "stereo_depth": stereo, "precision_street_1km": prec_street, "batched_segments": segments},
+                   "stereo_depth": stereo, "fusion_roofline": fusion, "precision_street_1km": prec_street,
+                   "batched_segments": segments},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": measured_traffic(kernel_name, args.precision, nvox, N.denser_get_schedule(ctx)),
                      "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": kernel_name,

@@ -78,7 +78,7 @@ typedef struct {
     double tau;               /* primal step (Section III-C, step 3) */
     double theta;             /* relaxation (Section III-C, step 4) */
     uint32_t hash_slots;      /* power of two, > max_blocks */
-    uint32_t max_blocks;      /* block pool capacity */
+    uint32_t max_blocks;      /* block pool capacity, at most 2^24 (voxel offsets are 64-bit) */
     uint32_t max_new_blocks;  /* new blocks one allocation call may add (0: max_blocks) */
     int32_t precision;        /* DENSER_FP32 / FP16 / BF16 storage of u, u_bar, p */
     int32_t gap_every;        /* evaluate the primal-dual gap every this many iterations (0: never) */
@@ -356,6 +356,27 @@ int denser_load_state(denser_ctx* ctx, const float* u, const float* u_bar, const
  * DENSER_ERR_INVALID_ARG. */
 int denser_set_schedule(denser_ctx* ctx, const denser_schedule* sch);
 int denser_get_schedule(const denser_ctx* ctx, denser_schedule* sch);
+
+/* Fusion profile: device times of the allocation and fusion kernels of
+ * denser_integrate_batch, measured with CUDA events while profiling is on.  With
+ * profiling on, every batched call waits for its stream after each group of maps (to
+ * read the events and counters), so the profile is for measurement, not for the
+ * fastest pipeline.  Totals since profiling was last switched on: */
+typedef struct {
+    int64_t groups;           /* groups of up to DENSER_MAX_BATCH maps (one launch sequence each) */
+    int64_t maps;             /* depth maps */
+    int64_t listed_blocks;    /* sum over groups of the blocks the culling listed for the fusion kernel */
+    int64_t new_blocks;       /* blocks the allocation added */
+    double key_pass_ms;       /* the key pass: one thread per pixel, band samples, hash inserts */
+    double alloc_rest_ms;     /* sort, index, zero and commit of the new keys */
+    double cull_ms;           /* culling and per-map block origins */
+    double fuse_ms;           /* the fusion kernel: Eq. 1 on every listed voxel, maps in order */
+} denser_fusion_profile;
+
+/* Switches fusion profiling on (1; the totals restart at zero) or off (0). */
+int denser_set_fusion_profiling(denser_ctx* ctx, int32_t enable);
+/* Copies the totals accumulated since profiling was switched on. */
+int denser_get_fusion_profile(const denser_ctx* ctx, denser_fusion_profile* out);
 
 /* Number of allocated blocks (waits for the stream); negative on error. */
 int64_t denser_num_blocks(denser_ctx* ctx, void* stream);

@@ -693,10 +693,14 @@ int launch_alloc(denser_ctx* c, const float* depth, int n_frames, const denser_i
     // the fusion of the same maps reads the visible count and the largest valid depths
     // that this pass records (zeroed first, with the words between them)
     cudaMemsetAsync(c->d.counters + kNumVisible, 0, (kCounterWords - kNumVisible) * sizeof(int32_t), s);
+    if (c->profile) cudaEventRecord(c->prof_ev[0], s);
     alloc_keys_kernel<<<grid_for(c->sm_count, (int64_t)n_frames * a.tiles * 256, 256, 8), 256, 0, s>>>(depth, a,
                                                                                                         c->d);
     c->launches += 1;
-    return finish_alloc(c, s);
+    if (c->profile) cudaEventRecord(c->prof_ev[1], s);
+    const int rc = finish_alloc(c, s);
+    if (c->profile) cudaEventRecord(c->prof_ev[2], s);
+    return rc;
 }
 
 // The inserted keys of one allocation call become blocks: sorted (chunks, then ranks

@@ -232,6 +232,8 @@ void free_all(denser_ctx* c) {
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->laser_acc) cudaFree(c->laser_acc);
     if (c->laser_touched) cudaFree(c->laser_touched);
+    for (cudaEvent_t e : c->prof_ev)
+        if (e) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -260,7 +262,7 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     const denser_params& p = *prm;
     if (!(p.voxel_size > 0) || !(p.mu > 0) || !(p.lambda > 0) || !(p.sigma > 0) || !(p.tau > 0) ||
         !(p.theta >= 0) || !isfinite(p.voxel_size) || !isfinite(p.mu) || p.max_blocks == 0 ||
-        p.max_blocks > (1u << 30) / kBlockVoxels * 2 || p.hash_slots < 2 || (p.hash_slots & (p.hash_slots - 1)) ||
+        p.max_blocks > kMaxPoolBlocks || p.hash_slots < 2 || (p.hash_slots & (p.hash_slots - 1)) ||
         p.hash_slots <= p.max_blocks || p.precision < DENSER_FP32 || p.precision > DENSER_BF16 || p.gap_every < 0)
         return DENSER_ERR_INVALID_ARG;
     int ndev = 0;
@@ -379,6 +381,25 @@ void denser_destroy(denser_ctx* c) {
     delete c;
 }
 
+int denser_set_fusion_profiling(denser_ctx* c, int32_t enable) {
+    return guarded(c, [&]() -> int {
+        if (enable && !c->prof_ev[0])
+            for (cudaEvent_t& e : c->prof_ev) {
+                const int rc = cuda_check(c, cudaEventCreate(&e), "cudaEventCreate(profile)");
+                if (rc) return rc;
+            }
+        c->profile = enable != 0;
+        c->prof = denser_fusion_profile{};
+        return DENSER_OK;
+    });
+}
+
+int denser_get_fusion_profile(const denser_ctx* c, denser_fusion_profile* out) {
+    if (!c || !out) return DENSER_ERR_INVALID_ARG;
+    *out = c->prof;
+    return DENSER_OK;
+}
+
 int denser_reset(denser_ctx* c, void* stream) {
     return guarded(c, [&]() -> int {
         cudaStream_t s = (cudaStream_t)stream;
@@ -486,6 +507,20 @@ int denser_integrate_batch(denser_ctx* c, const float* depths, int32_t n_frames,
             if (!rc) rc = launch_fuse(c, dd, n, K, T_gc + 16 * (size_t)first, segment, s, true);
             const int rr = release_depth(c, slot, s);
             if (rc || (rc = rr)) return rc;
+            if (c->profile) {
+                if ((rc = read_counters(c, s))) return rc;
+                float ms[4];
+                for (int e = 0; e < 4; ++e)
+                    if ((rc = cuda_check(c, cudaEventElapsedTime(&ms[e], c->prof_ev[e], c->prof_ev[e + 1]),
+                                         "profile events")))
+                        return rc;
+                c->prof.groups += 1;
+                c->prof.maps += n;
+                c->prof.listed_blocks += c->h_counters[kNumVisible];
+                c->prof.new_blocks += c->h_counters[kLastNew];
+                c->prof.key_pass_ms += ms[0], c->prof.alloc_rest_ms += ms[1];
+                c->prof.cull_ms += ms[2], c->prof.fuse_ms += ms[3];
+            }
             if (n_new_out) {
                 if ((rc = read_counters(c, s))) return rc;
                 added += c->h_counters[kLastNew];

@@ -18,6 +18,10 @@ constexpr int kNeighbours = 12;
 constexpr int kMaxProbe = 512;             // linear-probe limit of the hash table
 constexpr int kSortChunk = 2048;           // keys sorted per CTA before the rank merge
 constexpr int kSweepThreads = 512;
+// Largest block pool a context accepts.  Voxel offsets (block * 512 + l) are computed in
+// 64 bits everywhere; block indices are 32-bit, and 2^24 blocks (8.6 G voxels, about
+// 400 GB of FP32 state) is beyond any one device's memory.
+constexpr uint32_t kMaxPoolBlocks = 1u << 24;
 constexpr int kMaxBatch = 16;              // depth maps per batched allocation + fusion launch
 
 // ---------------------------------------------------------------- block keys
@@ -185,6 +189,12 @@ struct denser_ctx {
         cudaGraph_t graph;
         cudaGraphExec_t exec;
     } loop;
+    // fusion profiling (denser_set_fusion_profiling): events recorded before the key
+    // pass, after it, after the rest of the allocation, after culling and origins, and
+    // after the fusion kernel of each batched group
+    bool profile;
+    cudaEvent_t prof_ev[5];
+    denser_fusion_profile prof;
     std::string msg;
 };
 

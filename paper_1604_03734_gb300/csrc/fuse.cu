@@ -389,7 +389,9 @@ int launch_fuse(denser_ctx* c, const float* depth, int n_frames, const denser_in
     }
     cull_kernel<<<grid_for(c->sm_count, c->d.max_blocks, 256, 4), 256, 0, s>>>(c->d, a);
     origin_kernel<<<grid_for(c->sm_count, (int64_t)c->d.max_blocks * n_frames, 256, 8), 256, 0, s>>>(c->d, a);
+    if (c->profile) cudaEventRecord(c->prof_ev[3], s);
     fuse_kernel<<<c->sm_count * 16, 128, 0, s>>>(depth, c->d, a);
+    if (c->profile) cudaEventRecord(c->prof_ev[4], s);
     c->launches += 3;
     return cuda_check(c, cudaGetLastError(), "fusion kernels");
 }

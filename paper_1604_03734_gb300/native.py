@@ -35,6 +35,7 @@ EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_r
            "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual", "denser_extract_surface",
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
            "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc",
+           "denser_set_fusion_profiling", "denser_get_fusion_profile",
            "denser_net_gather", "denser_net_targets", "denser_net_apply", "denser_conv3", "denser_conv3_wgrad",
            "denser_relu_backward", "denser_net_loss", "denser_adam", "denser_pack_weights",
            "denser_stereo_default_params", "denser_census", "denser_diffusion_tensor", "denser_disparity_assign",
@@ -48,6 +49,12 @@ class denser_params(ctypes.Structure):
                 ("hash_slots", ctypes.c_uint32), ("max_blocks", ctypes.c_uint32),
                 ("max_new_blocks", ctypes.c_uint32), ("precision", ctypes.c_int32),
                 ("gap_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class denser_fusion_profile(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int64), ("maps", ctypes.c_int64), ("listed_blocks", ctypes.c_int64),
+                ("new_blocks", ctypes.c_int64), ("key_pass_ms", ctypes.c_double), ("alloc_rest_ms", ctypes.c_double),
+                ("cull_ms", ctypes.c_double), ("fuse_ms", ctypes.c_double)]
 
 
 class denser_intrinsics(ctypes.Structure):
@@ -119,6 +126,8 @@ def lib():
             "denser_load_state": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp]),
             "denser_num_blocks": (_i64, [_vp, _vp]),
             "denser_launch_count": (_u64, [_vp]),
+            "denser_set_fusion_profiling": (_i32, [_vp, _i32]),
+            "denser_get_fusion_profile": (_i32, [_vp, _vp]),
             "denser_set_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_get_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_energy_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _dbl, _vp, _vp]),
@@ -366,6 +375,16 @@ def denser_num_blocks(ctx, stream=None) -> int:
 
 def denser_launch_count(ctx) -> int:
     return int(lib().denser_launch_count(ctx))
+
+
+def denser_set_fusion_profiling(ctx, enable: bool = True):
+    return _check(ctx, lib().denser_set_fusion_profiling(ctx, 1 if enable else 0))
+
+
+def denser_get_fusion_profile(ctx) -> dict:
+    pr = denser_fusion_profile()
+    _check(ctx, lib().denser_get_fusion_profile(ctx, ctypes.byref(pr)))
+    return {name: getattr(pr, name) for name, _ in pr._fields_}
 
 
 def denser_set_schedule(ctx, sweep_kernel=2, order=1, ctas_per_sm=0, use_graph=1):

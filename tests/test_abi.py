@@ -45,6 +45,8 @@ def test_null_context_is_rejected(library):
     assert L.denser_sync(None, None) == native.DENSER_ERR_INVALID_ARG
     assert L.denser_integrate_batch(None, None, 1, None, None, 0, None, None) == native.DENSER_ERR_INVALID_ARG
     assert L.denser_launch_count(None) == 0
+    assert L.denser_set_fusion_profiling(None, 1) == native.DENSER_ERR_INVALID_ARG
+    assert L.denser_get_fusion_profile(None, None) == native.DENSER_ERR_INVALID_ARG
     assert L.denser_last_error(None) == b"null context"
 
 
@@ -52,6 +54,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(native.denser_params) == 6 * 8 + 6 * 4
     assert ctypes.sizeof(native.denser_intrinsics) == 4 * 8 + 2 * 4
     assert ctypes.sizeof(native.denser_reg_stats) == 2 * 4 + 6 * 8 + 2 * 4 + 2 * 8
+    assert ctypes.sizeof(native.denser_fusion_profile) == 4 * 8 + 4 * 8
 
 
 def test_batch_binding_checks_shapes_without_a_gpu(library):
