@@ -1,5 +1,5 @@
 """The batched-segments workload: 64 independent street segments of lengths uniform in
-50-500 m (seeds 1-64, 36 193 depth maps, about 4.5 M blocks) fused into one map with
+50-500 m (seeds 1-64, 36 193 depth maps, 3.95 M blocks) fused into one map with
 the segment as part of the block key, then regularised together (one sweep launch per
 iteration over every segment, the loop as one CUDA graph, the autotuner's schedule),
 as the benchmark runs it.  Blocks of different segments are never neighbours, so each
@@ -55,7 +55,7 @@ def test_batched_segments_against_oracle():
         N.denser_integrate_batch(m.ctx, torch.from_numpy(np.stack(batch)).cuda(), K,
                                  np.asarray(scenes[seg_of_batch].poses[first:first + len(batch)]), seg_of_batch)
         nb = N.denser_num_blocks(m.ctx)
-        assert nb > 4_000_000
+        assert nb > 3_500_000
         tune = AT.autotune(m.ctx, 0, iters=10, use_cache=False)
         st = N.denser_regularize(m.ctx, 200)
         assert st.iters == 200 and st.n_blocks == nb
