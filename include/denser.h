@@ -414,12 +414,18 @@ int denser_net_targets(denser_ctx* ctx, const int32_t* blocks, int64_t n, float*
 int denser_net_apply(denser_ctx* ctx, const int32_t* blocks, int64_t n, const float* out, int32_t with_dual,
                      void* stream);
 
-/* One layer: y = conv(x, w) + bias, then ReLU when relu != 0.  x BF16 [n][1000][16];
+/* One layer: y = conv(x, w) + bias, then ReLU when relu != 0, on the fifth-generation
+ * tensor cores (tcgen05.mma, BF16 products accumulated in FP32 in tensor memory; a wait
+ * for their completion that runs out is reported by denser_net_check).  x BF16 [n][1000][16];
  * bias FP32 [16] or NULL; outputs y_bf16 BF16 and/or y_f32 FP32 [n][1000][16] (either
  * may be NULL).  The data gradient of a layer is the same call on its output gradient
  * with the mirrored, transposed weights of denser_pack_weights and no bias or ReLU. */
 int denser_conv3(const void* x, const void* w, const float* bias, int32_t relu, void* y_bf16, float* y_f32,
                  int64_t n, void* stream);
+
+/* Waits for `stream`; DENSER_ERR_TIMEOUT when a denser_conv3 since the last check gave up
+ * waiting for its tensor-core products (its outputs are then incomplete), else DENSER_OK. */
+int denser_net_check(void* stream);
 
 /* Weight and bias gradients of a layer, accumulated (+=) into dw FP32 [27][16][16] and
  * db FP32 [16]: dw[tap][co][ci] += sum_n sum_v dz[v][co] h[v + offset(tap)][ci], db[co] +=

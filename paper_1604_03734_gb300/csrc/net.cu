@@ -9,9 +9,11 @@
 // are zero).  Activations are BF16, channel-last: act[sample][voxel][16], voxel
 // v = x + 10 y + 100 z.  Weights are BF16 [27 taps][16 out][16 in], tap = dx + 3 dy +
 // 9 dz for the offset (dx - 1, dy - 1, dz - 1).  Products run on the tensor cores as
-// implicit GEMMs with mma.sync m16n8k16 (BF16 in, FP32 accumulate):
-//   forward / data gradient: M = 16 voxels, N = 8 channels, K = 16 channels of one tap;
-//   weight gradient:         M = 16 out channels, N = 8 in channels, K = 16 voxels.
+// implicit GEMMs (BF16 in, FP32 accumulate):
+//   forward / data gradient: tcgen05.mma, M = 128 padded voxels, N = 16 channels, K = 16
+//                            channels of one tap, accumulated in tensor memory;
+//   weight gradient:         mma.sync m16n8k16, M = 16 out channels, N = 8 in channels,
+//                            K = 16 voxels.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -123,6 +125,189 @@ __global__ void __launch_bounds__(kNetThreads) conv3_kernel(const __nv_bfloat16*
             }
         }
     }
+}
+
+// ------------------------------------------------------------------ tcgen05 conv
+// The same convolution on the fifth-generation tensor cores.  Per sample, the padded
+// 12^3 activation grid sits in shared memory in the canonical K-major layout without
+// swizzle: two planes of 16-byte rows, plane h holding channels 8h .. 8h + 7 of every
+// padded voxel p = x' + 12 y' + 144 z'.  An M-tile is 128 consecutive padded rows; for tap
+// (dx, dy, dz) its A operand is the same two planes read from a start row shifted by
+// (dx - 1) + 12 (dy - 1) + 144 (dz - 1), so one shared-memory descriptor per (tile, tap)
+// and no data movement.  B (the tap's 16 x 16 weights, K-major) has the same two-plane
+// layout.  tcgen05.mma (M 128, N 16, K 16, BF16 in, FP32 out) accumulates the 27 taps of
+// each of the 12 tiles in tensor memory (16 columns per tile, 192 of the CTA's 256); one
+// thread issues the MMAs and commits them to an mbarrier; the four warps wait for it
+// (bounded) and read their 32 TMEM lanes back with tcgen05.ld for bias, ReLU and the
+// stores.  The 12 tiles start at padded row 157 (grid voxel (0, 0, 0)) and reach row 1692
+// (>= 1570, voxel (9, 9, 9)); with the tap shifts they read rows 0 .. 1849.
+constexpr int kTcRows = 1856;                              // staged padded rows (zeros beyond the grid)
+constexpr int kTcRow0 = 157;                               // padded row of grid voxel (0, 0, 0)
+constexpr int kTcTiles = 12;
+constexpr uint32_t kTcPlane = (uint32_t)kTcRows * 16;      // 29696 bytes per A plane
+constexpr uint32_t kTcA = 2 * kTcPlane;                    // 59392
+constexpr uint32_t kTcTap = 2 * kC * 16;                   // 512 bytes of B per tap (two planes)
+constexpr uint32_t kTcB = 27 * kTcTap;                     // 13824
+// 100 KB per CTA keeps at most two CTAs on an SM, so their TMEM allocations (256 columns
+// each of the SM's 512) never wait for each other
+constexpr size_t kTcSmem = 100 * 1024;
+static_assert((size_t)kTcA + kTcB <= kTcSmem, "planes and weights exceed the conv's shared memory");
+constexpr uint32_t kTcCols = 256;                          // TMEM columns per CTA
+constexpr long long kTcWaitLimit = 1ll << 24;              // mbarrier polls before a wait counts as lost
+// kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12
+// = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ int g_tc_timeout;  // set when an MMA completion wait ran out (read by denser_net_check)
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension byte
+// offset (between core matrices adjacent in K), stride-dimension byte offset (between
+// 8-row groups), descriptor version 1 at bit 46, no swizzle.
+__device__ inline uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ inline void tc_mma(uint32_t d, uint64_t a, uint64_t b, int accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ inline bool tc_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ inline void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kNetThreads, 1) conv3_tc_kernel(const __nv_bfloat16* __restrict__ x,
+                                                                  const __nv_bfloat16* __restrict__ w,
+                                                                  const float* __restrict__ bias, int relu,
+                                                                  __nv_bfloat16* __restrict__ y_bf16,
+                                                                  float* __restrict__ y_f32, int n) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    char* planes = smem;
+    char* wts = smem + kTcA;
+    for (int i = t; i < (int)(kTcA / 16); i += blockDim.x) reinterpret_cast<uint4*>(planes)[i] = make_uint4(0, 0, 0, 0);
+    // weights [tap][co][ci] -> [tap][plane h][co][ci 8h .. 8h + 7]
+    for (int i = t; i < 27 * kC * 2; i += blockDim.x) {
+        const int tap = i / (kC * 2), co = (i / 2) % kC, h = i & 1;
+        *reinterpret_cast<uint4*>(wts + tap * kTcTap + h * (kC * 16) + co * 16) = __ldg(reinterpret_cast<const uint4*>(w) + i);
+    }
+    float bv[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) bv[c] = bias ? bias[c] : 0.0f;
+    const uint32_t bar_a = smem_u32(&bar);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t a0 = smem_u32(planes), b0 = smem_u32(wts);
+    uint32_t parity = 0;
+    bool lost = false;
+    for (int s = blockIdx.x; s < n && !lost; s += gridDim.x) {
+        // the sample's voxels into their padded rows (the border rows stay zero)
+        const uint4* src = reinterpret_cast<const uint4*>(x + (size_t)s * kGV * kC);
+        for (int i = t; i < kGV * 2; i += blockDim.x) {
+            const int v = i >> 1, h = i & 1;
+            const int px = v % kG + 1, py = (v / kG) % kG + 1, pz = v / (kG * kG) + 1;
+            *reinterpret_cast<uint4*>(planes + h * kTcPlane + (px + 12 * py + 144 * pz) * 16) = __ldg(src + i);
+        }
+        // generic-proxy stores become visible to the tensor cores' async proxy
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            for (int tile = 0; tile < kTcTiles; ++tile) {
+                const int row0 = kTcRow0 + 128 * tile;
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int off = (tap % 3 - 1) + 12 * ((tap / 3) % 3 - 1) + 144 * (tap / 9 - 1);
+                    const uint64_t ad = tc_desc(a0 + (uint32_t)(row0 + off) * 16, kTcPlane, 128);
+                    const uint64_t bd = tc_desc(b0 + (uint32_t)tap * kTcTap, kC * 16, 128);
+                    tc_mma(tmem + (uint32_t)(kC * tile), ad, bd, tap > 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
+                         : "memory");
+        }
+        long long it = 0;
+        bool done = false;
+        while (!(done = tc_try_wait(bar_a, parity)) && ++it < kTcWaitLimit) {
+        }
+        if (!done) {
+            if (t == 0) atomicExch(&g_tc_timeout, 1);
+            lost = true;
+        } else {
+            parity ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            // warp w reads TMEM lanes 32 w .. 32 w + 31: rows row0 + 32 w + lane of each tile
+            for (int tile = 0; tile < kTcTiles; ++tile) {
+                float v[kC];
+                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(kC * tile), v);
+                const int row = kTcRow0 + 128 * tile + 32 * warp + lane;
+                const int px = row % 12, py = (row / 12) % 12, pz = row / 144;
+                if (px < 1 || px > kG || py < 1 || py > kG || pz < 1 || pz > kG) continue;
+                const int vox = (px - 1) + kG * (py - 1) + kG * kG * (pz - 1);
+#pragma unroll
+                for (int c = 0; c < kC; ++c) {
+                    v[c] += bv[c];
+                    if (relu) v[c] = fmaxf(v[c], 0.0f);
+                }
+                const size_t off = ((size_t)s * kGV + vox) * kC;
+                if (y_f32) {
+                    float4* d = reinterpret_cast<float4*>(y_f32 + off);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+                if (y_bf16) {
+                    __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(y_bf16 + off);
+#pragma unroll
+                    for (int q = 0; q < kC / 2; ++q) d[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();  // TMEM reads and the planes are done before the next sample
+    }
+    if (lost) {
+        // give the MMAs in flight a second bounded chance to land before TMEM is freed
+        long long it = 0;
+        while (!tc_try_wait(bar_a, parity) && ++it < kTcWaitLimit) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
 // dW[tap][co][ci] += sum_samples sum_v dz[v][co] h[v + offset(tap)][ci] (zero padding);
@@ -362,6 +547,8 @@ __global__ void apply_kernel(DeviceMap m, T* u, T* ub, T* p, size_t pstride, con
 int configure_net_kernels() {
     cudaError_t e = cudaFuncSetAttribute(conv3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kTileBytes + (size_t)kTiles * 16 * kC * 2));
     return e == cudaSuccess ? DENSER_OK : DENSER_ERR_CUDA;
@@ -439,9 +626,24 @@ extern "C" int denser_conv3(const void* x, const void* w, const float* bias, int
     if (!x || !w || n < 0 || (!y_bf16 && !y_f32)) return DENSER_ERR_INVALID_ARG;
     if (n == 0) return DENSER_OK;
     if (configure_net_kernels() != DENSER_OK) return DENSER_ERR_CUDA;
-    conv3_kernel<<<net_grid((int)n, 3), kNetThreads, kConvSmem, (cudaStream_t)stream>>>(
+    conv3_tc_kernel<<<net_grid((int)n, 2), kNetThreads, kTcSmem, (cudaStream_t)stream>>>(
         (const __nv_bfloat16*)x, (const __nv_bfloat16*)w, bias, relu, (__nv_bfloat16*)y_bf16, y_f32, (int)n);
     return net_status();
+}
+
+extern "C" int denser_net_check(void* stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DENSER_ERR_CUDA;
+    }
+    int lost = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbol(&lost, g_tc_timeout, sizeof(int)) != cudaSuccess ||
+        (lost && cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int)) != cudaSuccess)) {
+        cudaGetLastError();
+        return DENSER_ERR_CUDA;
+    }
+    return lost ? DENSER_ERR_TIMEOUT : DENSER_OK;
 }
 
 extern "C" int denser_conv3_wgrad(const void* h, const void* dz, float* dw, float* db, int64_t n, void* stream) {

@@ -35,7 +35,7 @@ EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_r
            "denser_regularize", "denser_energy", "denser_extract", "denser_extract_dual", "denser_extract_surface",
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
            "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc",
-           "denser_set_fusion_profiling", "denser_get_fusion_profile",
+           "denser_set_fusion_profiling", "denser_get_fusion_profile", "denser_net_check",
            "denser_net_gather", "denser_net_targets", "denser_net_apply", "denser_conv3", "denser_conv3_wgrad",
            "denser_relu_backward", "denser_net_loss", "denser_adam", "denser_pack_weights",
            "denser_stereo_default_params", "denser_census", "denser_diffusion_tensor", "denser_disparity_assign",
@@ -127,6 +127,7 @@ def lib():
             "denser_num_blocks": (_i64, [_vp, _vp]),
             "denser_launch_count": (_u64, [_vp]),
             "denser_set_fusion_profiling": (_i32, [_vp, _i32]),
+            "denser_net_check": (_i32, [_vp]),
             "denser_get_fusion_profile": (_i32, [_vp, _vp]),
             "denser_set_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_get_schedule": (_i32, [_vp, P(denser_schedule)]),
@@ -375,6 +376,11 @@ def denser_num_blocks(ctx, stream=None) -> int:
 
 def denser_launch_count(ctx) -> int:
     return int(lib().denser_launch_count(ctx))
+
+
+def denser_net_check(stream=None) -> int:
+    """Waits for the stream; the C status (DENSER_ERR_TIMEOUT if a tensor-core wait ran out)."""
+    return int(lib().denser_net_check(_stream(stream)))
 
 
 def denser_set_fusion_profiling(ctx, enable: bool = True):

@@ -1,4 +1,6 @@
-"""Warm-start network kernels against the FP64 oracle (oracle/net_oracle.py).
+"""Warm-start network kernels against the FP64 oracle (oracle/net_oracle.py).  The
+forward and data-gradient convolutions run on tcgen05 (tensor memory accumulators),
+the weight gradient on mma.sync.
 
 Per layer, on BF16-representable inputs (so that only the FP32 accumulation differs
 from the oracle): forward convolution, data gradient and weight/bias gradient to a
@@ -76,6 +78,7 @@ def test_conv3_forward_layer(layer_case):
     got = from_ours(y.cpu().numpy().astype(np.float64), 16)
     assert np.max(np.abs(got - np.maximum(ref, 0))) <= 1e-5 * np.max(np.abs(ref))
     np.testing.assert_array_equal(yb.float().cpu().numpy(), y.to(torch.bfloat16).float().cpu().numpy())
+    assert N.denser_net_check() == N.DENSER_OK   # every tensor-core wait completed
 
 
 def test_conv3_gradients_layer(layer_case):
