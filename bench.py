@@ -68,6 +68,15 @@ def measured_traffic(kernel: str, precision: int, nvox: int, schedule=None):
     return float(j["dram_read_bytes"]) + float(j["dram_write_bytes"])
 
 
+def peaks_bf16() -> float:
+    """Measured dense BF16 tensor throughput (TFLOP/s, the burst figure) or the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -667,6 +676,33 @@ def main():
                           "primal-dual kernel's rate"}
         del ws, il, ir, disp
 
+    # the warm-start network's convolution on the tensor cores (tcgen05): one 16 -> 16
+    # channel 3^3 layer over 4096 blocks (10^3 voxels each), BF16 in, FP32 accumulate
+    conv = None
+    if not args.no_warmstart:
+        ns = 4096
+        xs = torch.randn(ns, 1000, 16, device=dev).to(torch.bfloat16)
+        wts = (torch.randn(27, 16, 16, device=dev) * 0.1).to(torch.bfloat16)
+        ys = torch.empty(ns, 1000, 16, dtype=torch.bfloat16, device=dev)
+        for _ in range(3):
+            N.denser_conv3(xs, wts, None, 1, ys, None, ns, stream)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        c0.record(stream)
+        for _ in range(reps):
+            N.denser_conv3(xs, wts, None, 1, ys, None, ns, stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / reps
+        flops = 2.0 * ns * 1000 * 16 * 16 * 27
+        peak_tf = peaks_bf16()
+        conv = {"samples": ns, "ms_per_layer": cms, "useful_tflops": flops / (cms / 1e3) / 1e12,
+                "frac_of_measured_bf16": flops / (cms / 1e3) / 1e12 / peak_tf, "peak_tflops": peak_tf,
+                "kernel": "conv3_tc_kernel (tcgen05.mma M128 N16 K16, accumulators in TMEM)",
+                "flops": "2 x 1000 voxels x 16 x 16 x 27 per sample (the padded rows the kernel also computes "
+                         "are not counted)", "net_check": N.denser_net_check(stream)}
+        del xs, wts, ys
+
     # fusion roofline: the same 200 maps allocated and fused with the library's fusion
     # profiling on (CUDA events around the key pass, the rest of the allocation, culling
     # and the fusion kernel; the call waits after each group, so this is not the step above)
@@ -737,7 +773,8 @@ def main():
                    "pd_only_voxel_updates_per_s": nvox / (sweep_avg_ms / 1e3),
                    "pd_share_of_step": sweep_ms / args.steps / step_ms,
                    "time_to_gap_1e-4_warm_vs_plain": ttg, "surface_extraction": surface, "laser_fusion": laser,
-                   "stereo_depth": stereo, "fusion_roofline": fusion, "precision_street_1km": prec_street,
+                   "stereo_depth": stereo, "warmstart_conv": conv, "fusion_roofline": fusion,
+                   "precision_street_1km": prec_street,
                    "batched_segments": segments},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": measured_traffic(kernel_name, args.precision, nvox, N.denser_get_schedule(ctx)),

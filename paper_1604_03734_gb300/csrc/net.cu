@@ -31,8 +31,6 @@ constexpr int kP = 12;           // padded tile side
 constexpr int kTiles = 63;       // 16-voxel row tiles covering 1000 voxels (1008)
 constexpr int kNetThreads = 128;
 constexpr size_t kTileBytes = (size_t)kP * kP * kP * kC * 2;   // 55296
-constexpr size_t kWBytes = (size_t)27 * kC * kC * 2;            // 13824
-constexpr size_t kConvSmem = kTileBytes + kWBytes;
 
 __device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -64,66 +62,6 @@ __device__ inline void load_tile(char* tile, const __nv_bfloat16* src) {
         const int v = i >> 1, half = i & 1;
         const int x = v % kG, y = (v / kG) % kG, z = v / (kG * kG);
         *reinterpret_cast<uint4*>(tile + tile_off(x + 1, y + 1, z + 1) + half * 16) = __ldg(s + i);
-    }
-}
-
-// y[v][co] = sum_taps sum_ci W[tap][co][ci] x[v + offset(tap)][ci] (+ bias, ReLU).
-__global__ void __launch_bounds__(kNetThreads) conv3_kernel(const __nv_bfloat16* __restrict__ x,
-                                                             const __nv_bfloat16* __restrict__ w,
-                                                             const float* __restrict__ bias, int relu,
-                                                             __nv_bfloat16* __restrict__ y_bf16,
-                                                             float* __restrict__ y_f32, int n) {
-    extern __shared__ __align__(16) char smem[];
-    char* tile = smem;
-    char* ws = smem + kTileBytes;
-    for (int i = threadIdx.x; i < (int)(kTileBytes / 16); i += blockDim.x)
-        reinterpret_cast<uint4*>(tile)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = threadIdx.x; i < (int)(kWBytes / 16); i += blockDim.x)
-        reinterpret_cast<uint4*>(ws)[i] = __ldg(reinterpret_cast<const uint4*>(w) + i);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, c = lane & 3;
-    float bv[2][2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-        for (int e = 0; e < 2; ++e) bv[j][e] = bias ? bias[8 * j + 2 * c + e] : 0.0f;
-    for (int s = blockIdx.x; s < n; s += gridDim.x) {
-        __syncthreads();
-        load_tile(tile, x + (size_t)s * kGV * kC);
-        __syncthreads();
-        for (int t = warp; t < kTiles; t += kNetThreads / 32) {
-            // this lane's A row: voxel of the tile (clamped inside the grid for the padding rows)
-            const int vr = min(t * 16 + (lane & 15), kGV - 1);
-            const int xr = vr % kG, yr = (vr / kG) % kG, zr = vr / (kG * kG);
-            const unsigned arow = smem_u32(tile) + tile_off(xr, yr, zr) + (lane >> 4) * 16;
-            float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-#pragma unroll 1
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
-                unsigned a[4];
-                ldsm_x4(arow + tile_off(dx, dy, dz), a);
-                const unsigned* wt = reinterpret_cast<const unsigned*>(ws + tap * kC * kC * 2);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    // B[k = ci][n = co]: W[tap][8 j + g][2 c .. 2 c + 1] and [.. + 8]
-                    const unsigned b0 = wt[((8 * j + g) * kC + 2 * c) >> 1];
-                    const unsigned b1 = wt[((8 * j + g) * kC + 2 * c + 8) >> 1];
-                    mma_bf16(acc[j], a, b0, b1);
-                }
-            }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int v = t * 16 + g + 8 * half;
-                if (v >= kGV) continue;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    float o0 = acc[j][2 * half] + bv[j][0], o1 = acc[j][2 * half + 1] + bv[j][1];
-                    if (relu) o0 = fmaxf(o0, 0.0f), o1 = fmaxf(o1, 0.0f);
-                    const size_t off = ((size_t)s * kGV + v) * kC + 8 * j + 2 * c;
-                    if (y_bf16) *reinterpret_cast<__nv_bfloat162*>(y_bf16 + off) = __floats2bfloat162_rn(o0, o1);
-                    if (y_f32) *reinterpret_cast<float2*>(y_f32 + off) = make_float2(o0, o1);
-                }
-            }
-        }
     }
 }
 
@@ -545,9 +483,7 @@ __global__ void apply_kernel(DeviceMap m, T* u, T* ub, T* p, size_t pstride, con
 }  // namespace
 
 int configure_net_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(conv3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaError_t e = cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kTileBytes + (size_t)kTiles * 16 * kC * 2));
