@@ -407,10 +407,20 @@ int denser_net_gather(denser_ctx* ctx, const int32_t* blocks, int64_t n, void* x
 int denser_net_targets(denser_ctx* ctx, const int32_t* blocks, int64_t n, float* target, float* mask,
                        float u_weight, float p_weight, void* stream);
 
+/* Divergence targets from the context's current state: target FP32 [n][6][512], channels
+ * 0 u (0 off Omega), 1 Omega (1 or 0), 2 the divergence of p over the block's inner Eq. 3
+ * edges (Eq. 4 with the edges that cross the block's faces left out; 0 off Omega), 3..5
+ * the inner edge masks e_a = Omega(l) and Omega(l + a) and l_a < 7, for the loss of
+ * denser_net_loss_div.  The dual field is unique only up to a divergence-free part;
+ * its divergence is what a warm start must get right. */
+int denser_net_targets_div(denser_ctx* ctx, const int32_t* blocks, int64_t n, float* target, void* stream);
+
 /* Writes a warm start into the state from network outputs out FP32 [n][1000][16]:
  * u = clamp(out_0, -1, 1) on Omega and 0 elsewhere, u_bar = u, p_a = out_{1+a} on the
- * Eq. 3 edges and 0 elsewhere (p = 0 everywhere when with_dual is 0), then p projected
- * onto the unit ball.  Follow it with denser_regularize(start = 1). */
+ * Eq. 3 edges and 0 elsewhere, then p projected onto the unit ball.  with_dual 0: p = 0
+ * everywhere; 1: p on every Eq. 3 edge; 2: p on the edges inside the block only (0 on the
+ * edges that cross a block face, the network trained by denser_net_loss_div).  Follow it
+ * with denser_regularize(start = 1). */
 int denser_net_apply(denser_ctx* ctx, const int32_t* blocks, int64_t n, const float* out, int32_t with_dual,
                      void* stream);
 
@@ -440,6 +450,16 @@ int denser_relu_backward(const void* dh, const void* h, void* dz, int64_t count,
  * (device FP64), dout BF16 [n][1000][16] = its gradient (zero off the centre). */
 int denser_net_loss(const float* out, const float* target, const float* mask, void* dout, double* loss,
                     int64_t n, void* stream);
+
+/* Loss of the divergence-trained warm start, for outputs out FP32 [n][1000][16] (u =
+ * channel 0, p_a = channel 1 + a on the centre 8^3) and targets FP32 [n][6][512] of
+ * denser_net_targets_div:
+ *   *loss += (1/n) sum_samples sum_Omega [ u_weight (u - u*)^2 + div_weight (div p - div p*)^2 ]
+ * with div the inner-edge divergence (p counted on the inner edges only); dout BF16
+ * [n][1000][16] = its gradient (zero off the centre and off channels 0..3).  loss is a
+ * device FP64 scalar; every pointer is device memory. */
+int denser_net_loss_div(const float* out, const float* target, float u_weight, float div_weight, void* dout,
+                        double* loss, int64_t n, void* stream);
 
 /* Adam update of FP32 parameters w with gradient grad and moments m, v (count elements),
  * bias-corrected for step `step` (>= 1). */

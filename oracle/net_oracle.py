@@ -162,3 +162,70 @@ def warm_state(out, omega, edges):
     nrm = np.sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2])
     p = p / np.maximum(1.0, nrm)[None]
     return u, u.copy(), p
+
+
+# ------------------------------------------- the divergence-trained warm start
+def inner_edges(omega):
+    """Inner Eq. 3 edge masks of each block, [3, n, 512]: voxel l and l + a both in Omega
+    and l + a inside the same block (l_a < 7)."""
+    om = np.asarray(omega, dtype=bool).reshape(-1, 8, 8, 8)       # [b, lz, ly, lx]
+    e = np.zeros((3,) + om.shape, dtype=bool)
+    e[0][..., :-1] = om[..., :-1] & om[..., 1:]
+    e[1][:, :, :-1, :] = om[:, :, :-1, :] & om[:, :, 1:, :]
+    e[2][:, :-1] = om[:, :-1] & om[:, 1:]
+    return e.reshape(3, -1, 512)
+
+
+def inner_divergence(p, edges):
+    """Divergence of p [3, n, 512] over the inner edges only (Eq. 4, the negative adjoint of
+    the masked forward difference, with the edges that cross a block face left out)."""
+    d = np.zeros(p.shape[1:])
+    q = np.where(edges, p, 0.0).reshape(3, -1, 8, 8, 8)
+    out = np.zeros(q.shape[1:])
+    for a, ax in enumerate((3, 2, 1)):             # x, y, z axes of [b, lz, ly, lx]
+        back = np.zeros_like(q[a])
+        sl_dst = [slice(None)] * 4
+        sl_src = [slice(None)] * 4
+        sl_dst[ax], sl_src[ax] = slice(1, None), slice(None, -1)
+        back[tuple(sl_dst)] = q[a][tuple(sl_src)]
+        out = out + (q[a] - back)
+    d[:] = out.reshape(d.shape)
+    return d
+
+
+def targets_div(u, p, omega):
+    """[n, 6, 512]: u on Omega, Omega, the inner divergence of p on Omega, the inner edges."""
+    om = np.asarray(omega, dtype=bool).reshape(-1, 512)
+    e = inner_edges(om)
+    t = np.zeros((om.shape[0], 6, 512))
+    t[:, 0] = np.where(om, np.asarray(u).reshape(-1, 512), 0.0)
+    t[:, 1] = om
+    t[:, 2] = np.where(om, inner_divergence(np.asarray(p).reshape(3, -1, 512), e), 0.0)
+    t[:, 3:6] = e.transpose(1, 0, 2)
+    return t
+
+
+def loss_div(out, target, wu, wd):
+    """Mean over samples of sum_Omega [wu (u - u*)^2 + wd (div p - div p*)^2] for outputs
+    out [n, 4, 512] (u, p_x, p_y, p_z on the block) and targets [n, 6, 512]; returns (loss,
+    d loss / d out [n, 4, 512])."""
+    n = out.shape[0]
+    om = target[:, 1] != 0
+    e = (target[:, 3:6] != 0).transpose(1, 0, 2)
+    ru = np.where(om, out[:, 0] - target[:, 0], 0.0)
+    dv = inner_divergence(out[:, 1:4].transpose(1, 0, 2), e)
+    rd = np.where(om, dv - target[:, 2], 0.0)
+    loss = float(np.sum(wu * ru * ru + wd * rd * rd) / n)
+    g = np.zeros_like(out)
+    g[:, 0] = 2.0 * wu * ru / n
+    # d div / d p_a(l) = +1 at l and -1 at l + a (for an inner edge): the gradient is the
+    # negative inner forward difference of the residual, masked to the edges
+    r3 = rd.reshape(-1, 8, 8, 8)
+    for a, ax in enumerate((3, 2, 1)):
+        nxt = np.zeros_like(r3)
+        sl_dst = [slice(None)] * 4
+        sl_src = [slice(None)] * 4
+        sl_dst[ax], sl_src[ax] = slice(None, -1), slice(1, None)
+        nxt[tuple(sl_dst)] = r3[tuple(sl_src)]
+        g[:, 1 + a] = np.where(e[a], 2.0 * wd * (rd - nxt.reshape(-1, 512)) / n, 0.0)
+    return loss, g

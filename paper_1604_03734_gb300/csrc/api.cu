@@ -995,6 +995,21 @@ int denser_net_gather(denser_ctx* c, const int32_t* blocks, int64_t n, void* x, 
     });
 }
 
+int denser_net_targets_div(denser_ctx* c, const int32_t* blocks, int64_t n, float* target, void* stream) {
+    return guarded(c, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = read_counters(c, s);
+        if (rc) return rc;
+        const int64_t nb = c->h_counters[kNumBlocks];
+        if ((rc = net_blocks_check(c, blocks, n, nb))) return rc;
+        if (n == 0) return DENSER_OK;
+        if (!target || !is_device_ptr(target))
+            return set_error(c, DENSER_ERR_INVALID_ARG, "net_targets_div: target must be device memory");
+        if ((rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s))) return rc;
+        return launch_net_targets_div(c, blocks, (int)n, target, s);
+    });
+}
+
 int denser_net_targets(denser_ctx* c, const int32_t* blocks, int64_t n, float* target, float* mask, float u_weight,
                        float p_weight, void* stream) {
     return guarded(c, [&]() -> int {
@@ -1021,6 +1036,7 @@ int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const floa
         if ((rc = net_blocks_check(c, blocks, n, nb))) return rc;
         if (n == 0) return DENSER_OK;
         if (!out || !is_device_ptr(out)) return set_error(c, DENSER_ERR_INVALID_ARG, "net_apply: out must be device memory");
+        if (with_dual < 0 || with_dual > 2) return set_error(c, DENSER_ERR_INVALID_ARG, "net_apply: with_dual must be 0, 1 or 2");
         if ((rc = launch_prepare_regularize(c, nb, c->nbr_valid_blocks != nb, s))) return rc;
         return launch_net_apply(c, blocks, (int)n, out, with_dual, s);
     });

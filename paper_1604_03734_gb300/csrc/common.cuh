@@ -240,6 +240,7 @@ int launch_block_order(denser_ctx* c, int64_t n_blocks, cudaStream_t s);
 int configure_kernels(denser_ctx* c);
 int launch_graph_loop(denser_ctx* c, int64_t n_blocks, int k, bool with_gap, cudaStream_t s);
 int launch_net_gather(denser_ctx* c, const int32_t* blocks, int n, void* x, cudaStream_t s);
+int launch_net_targets_div(denser_ctx* c, const int32_t* blocks, int n, float* target, cudaStream_t s);
 int launch_net_targets(denser_ctx* c, const int32_t* blocks, int n, float* target, float* mask, float mu, float mp,
                        cudaStream_t s);
 int launch_net_apply(denser_ctx* c, const int32_t* blocks, int n, const float* out, int with_dual, cudaStream_t s);

@@ -469,7 +469,11 @@ __global__ void apply_kernel(DeviceMap m, T* u, T* ub, T* p, size_t pstride, con
         const float u0 = om ? fminf(1.0f, fmaxf(-1.0f, o[0])) : 0.0f;
         float q[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) q[a] = (with_dual && edge_of(m, b, l, a)) ? o[1 + a] : 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            const int lc = a == 0 ? (l & 7) : (a == 1 ? ((l >> 3) & 7) : (l >> 6));
+            const bool keep = with_dual == 1 || (with_dual == 2 && lc < 7);  // 2: edges inside the block only
+            q[a] = (keep && edge_of(m, b, l, a)) ? o[1 + a] : 0.0f;
+        }
         const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
         const float sc = n2 > 1.0f ? rsqrtf(n2) : 1.0f;
         const size_t v = (size_t)b * kBlockVoxels + l;
@@ -481,6 +485,99 @@ __global__ void apply_kernel(DeviceMap m, T* u, T* ub, T* p, size_t pstride, con
 }
 
 }  // namespace
+
+// Divergence targets of the listed blocks from the context's state, FP32 [n][6][512]:
+// 0 u, 1 Omega (1 / 0), 2 the divergence of p over the block's inner Eq. 3 edges
+// (Eq. 4 with the edges that cross the block's faces left out), 3..5 the inner edge
+// masks e_a(l) = Omega(l) and Omega(l + a) and l_a < 7.
+template <typename T>
+__global__ void targets_div_kernel(DeviceMap m, const T* u, const T* p, size_t pstride,
+                                   const int32_t* __restrict__ blocks, int n, float* target) {
+    const long long total = (long long)n * kBlockVoxels;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(i / kBlockVoxels), l = (int)(i % kBlockVoxels);
+        const int b = blocks ? blocks[s] : s;
+        const size_t v = (size_t)b * kBlockVoxels + l;
+        const int lc[3] = {l & 7, (l >> 3) & 7, l >> 6};
+        const int step[3] = {1, 8, 64};
+        const bool o = omega_of(m, b, l);
+        float dv = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const bool e = o && lc[a] < 7 && omega_of(m, b, l + step[a]);
+            const bool eb = lc[a] > 0 && omega_of(m, b, l - step[a]) && o;
+            const float own = e ? Store<T>::ld(p + a * pstride + v) : 0.0f;
+            const float back = eb ? Store<T>::ld(p + a * pstride + v - step[a]) : 0.0f;
+            dv = __fadd_rn(dv, __fsub_rn(own, back));
+            target[((size_t)s * 6 + 3 + a) * 512 + l] = e ? 1.0f : 0.0f;
+        }
+        target[((size_t)s * 6 + 0) * 512 + l] = o ? Store<T>::ld(u + v) : 0.0f;
+        target[((size_t)s * 6 + 1) * 512 + l] = o ? 1.0f : 0.0f;
+        target[((size_t)s * 6 + 2) * 512 + l] = o ? dv : 0.0f;
+    }
+}
+
+// Loss of the divergence-trained warm start, one CTA of 512 threads per sample:
+//   L = (1/n) sum_samples sum_Omega [ wu (u - u*)^2 + wd (div p - div p*)^2 ]
+// with u = out channel 0 and p_a = out channel 1 + a on the centre 8^3, div the inner-edge
+// divergence of the targets (channel 2), and dout = dL/dout in BF16 on the 10^3 grid
+// (zero off the centre and off channels 0..3).  d(div)/dp_a(l) is e_a(l) at l and -e_a(l)
+// at l + a, so the p gradient is 2 wd e_a(l) (r(l) - r(l + a)) / n, r the divergence residual.
+__global__ void __launch_bounds__(512) loss_div_kernel(const float* __restrict__ out, const float* __restrict__ target,
+                                                       float wu, float wd, __nv_bfloat16* __restrict__ dout,
+                                                       double* loss, int n) {
+    __shared__ float P[3][512];
+    __shared__ float R[512];
+    __shared__ double red[16];
+    const int s = blockIdx.x, l = threadIdx.x;
+    const int lc[3] = {l & 7, (l >> 3) & 7, l >> 6};
+    const int step[3] = {1, 8, 64};
+    const int gv = (lc[0] + 1) + kG * (lc[1] + 1) + kG * kG * (lc[2] + 1);
+    const float* o = out + ((size_t)s * kGV + gv) * kC;
+    const float* tg = target + (size_t)s * 6 * 512;
+    const bool om = tg[512 + l] != 0.0f;
+    bool e[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        e[a] = tg[(3 + a) * 512 + l] != 0.0f;
+        P[a][l] = e[a] ? o[1 + a] : 0.0f;
+    }
+    __syncthreads();
+    float dv = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dv += P[a][l] - (lc[a] > 0 ? P[a][l - step[a]] : 0.0f);
+    const float rd = om ? dv - tg[2 * 512 + l] : 0.0f;
+    const float ru = om ? o[0] - tg[l] : 0.0f;
+    R[l] = rd;
+    double acc = (double)wu * ru * ru + (double)wd * rd * rd;
+    __syncthreads();
+    const float inv_n = 1.0f / (float)n;
+    float g[4];
+    g[0] = 2.0f * wu * ru * inv_n;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[1 + a] = e[a] ? 2.0f * wd * (rd - R[l + step[a]]) * inv_n : 0.0f;
+    // dout: the centre voxel's four channels here, then zeros for the rest of the grid
+    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(dout + ((size_t)s * kGV + gv) * kC);
+    dst[0] = __floats2bfloat162_rn(g[0], g[1]);
+    dst[1] = __floats2bfloat162_rn(g[2], g[3]);
+#pragma unroll
+    for (int q = 2; q < kC / 2; ++q) dst[q] = __floats2bfloat162_rn(0.0f, 0.0f);
+    for (int v = l; v < kGV; v += 512) {
+        const int x = v % kG, y = (v / kG) % kG, z = v / (kG * kG);
+        if (x >= 1 && x <= 8 && y >= 1 && y <= 8 && z >= 1 && z <= 8) continue;
+        uint4* d = reinterpret_cast<uint4*>(dout + ((size_t)s * kGV + v) * kC);
+        d[0] = make_uint4(0, 0, 0, 0);
+        d[1] = make_uint4(0, 0, 0, 0);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((l & 31) == 0) red[l >> 5] = acc;
+    __syncthreads();
+    if (l == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 16; ++i) t += red[i];
+        atomicAdd(loss, t / n);
+    }
+}
 
 int configure_net_kernels() {
     cudaError_t e = cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
@@ -510,6 +607,27 @@ int launch_net_targets(denser_ctx* c, const int32_t* blocks, int n, float* targe
     }
     c->launches += 1;
     return cuda_check(c, cudaGetLastError(), "targets kernel");
+}
+
+int launch_net_targets_div(denser_ctx* c, const int32_t* blocks, int n, float* target, cudaStream_t s) {
+    const size_t ps = (size_t)c->d.max_blocks * kBlockVoxels;
+    const int g = grid_for(c->sm_count, (long long)n * kBlockVoxels, 256, 8);
+    switch (c->prm.precision) {
+        case DENSER_FP16:
+            targets_div_kernel<__half><<<g, 256, 0, s>>>(c->d, (const __half*)c->d.u, (const __half*)c->d.p[c->cur],
+                                                         ps, blocks, n, target);
+            break;
+        case DENSER_BF16:
+            targets_div_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(c->d, (const __nv_bfloat16*)c->d.u,
+                                                                (const __nv_bfloat16*)c->d.p[c->cur], ps, blocks, n,
+                                                                target);
+            break;
+        default:
+            targets_div_kernel<float><<<g, 256, 0, s>>>(c->d, (const float*)c->d.u, (const float*)c->d.p[c->cur], ps,
+                                                        blocks, n, target);
+    }
+    c->launches += 1;
+    return cuda_check(c, cudaGetLastError(), "divergence targets kernel");
 }
 
 int launch_net_apply(denser_ctx* c, const int32_t* blocks, int n, const float* out, int with_dual, cudaStream_t s) {
@@ -604,6 +722,15 @@ extern "C" int denser_net_loss(const float* out, const float* target, const floa
     if (!out || !target || !mask || !dout || !loss || n <= 0) return DENSER_ERR_INVALID_ARG;
     loss_kernel<<<net_grid((int)std::min<int64_t>(n * kGV / 256 + 1, 1 << 20), 8), 256, 0, (cudaStream_t)stream>>>(
         out, target, mask, (__nv_bfloat16*)dout, loss, (int)n);
+    return net_status();
+}
+
+extern "C" int denser_net_loss_div(const float* out, const float* target, float u_weight, float div_weight,
+                                   void* dout, double* loss, int64_t n, void* stream) {
+    if (!out || !target || !dout || !loss || n <= 0 || n > (1 << 30) || !(u_weight >= 0) || !(div_weight >= 0))
+        return DENSER_ERR_INVALID_ARG;
+    loss_div_kernel<<<(unsigned)n, 512, 0, (cudaStream_t)stream>>>(out, target, u_weight, div_weight,
+                                                                   (__nv_bfloat16*)dout, loss, (int)n);
     return net_status();
 }
 

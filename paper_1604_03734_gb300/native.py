@@ -36,6 +36,7 @@ EXPORTS = ("denser_default_params", "denser_create", "denser_destroy", "denser_r
            "denser_load_blocks", "denser_load_state", "denser_num_blocks", "denser_launch_count",
            "denser_set_schedule", "denser_get_schedule", "denser_energy_noalloc",
            "denser_set_fusion_profiling", "denser_get_fusion_profile", "denser_net_check",
+           "denser_net_targets_div", "denser_net_loss_div",
            "denser_net_gather", "denser_net_targets", "denser_net_apply", "denser_conv3", "denser_conv3_wgrad",
            "denser_relu_backward", "denser_net_loss", "denser_adam", "denser_pack_weights",
            "denser_stereo_default_params", "denser_census", "denser_diffusion_tensor", "denser_disparity_assign",
@@ -128,6 +129,8 @@ def lib():
             "denser_launch_count": (_u64, [_vp]),
             "denser_set_fusion_profiling": (_i32, [_vp, _i32]),
             "denser_net_check": (_i32, [_vp]),
+            "denser_net_targets_div": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+            "denser_net_loss_div": (_i32, [_vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _i64, _vp]),
             "denser_get_fusion_profile": (_i32, [_vp, _vp]),
             "denser_set_schedule": (_i32, [_vp, P(denser_schedule)]),
             "denser_get_schedule": (_i32, [_vp, P(denser_schedule)]),
@@ -376,6 +379,18 @@ def denser_num_blocks(ctx, stream=None) -> int:
 
 def denser_launch_count(ctx) -> int:
     return int(lib().denser_launch_count(ctx))
+
+
+def denser_net_targets_div(ctx, blocks, n, target, stream=None):
+    return _check(ctx, lib().denser_net_targets_div(ctx, _tptr(blocks), int(n), _tptr(target), _stream(stream)))
+
+
+def denser_net_loss_div(out, target, u_weight, div_weight, dout, loss, n, stream=None):
+    rc = lib().denser_net_loss_div(_tptr(out), _tptr(target), float(u_weight), float(div_weight), _tptr(dout),
+                                   _tptr(loss), int(n), _stream(stream))
+    if rc != DENSER_OK:
+        raise DenserError(rc, "denser_net_loss_div failed")
+    return rc
 
 
 def denser_net_check(stream=None) -> int:

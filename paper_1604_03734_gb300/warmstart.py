@@ -46,6 +46,9 @@ class WarmStartNet:
         self.m = [torch.zeros(27 * C * C + C, device=self.device) for _ in self.w32]
         self.v = [torch.zeros(27 * C * C + C, device=self.device) for _ in self.w32]
         self.params = [torch.cat([w.reshape(-1), b]) for w, b in zip(self.w32, self.b32)]
+        # how a prediction's dual is applied (denser_net_apply): 1 on every Eq. 3 edge (the
+        # network trained on p), 2 on the block's inner edges (trained on div p)
+        self.dual_mode = 1
         self._views()
         self.pack()
 
@@ -101,9 +104,21 @@ class WarmStartNet:
         N.denser_net_loss(out, target, mask, dout, loss, n)
         return loss, dout
 
+    def loss_and_grad_div(self, out, target):
+        """Divergence loss (denser_net_loss_div) for targets [n, 6, 512]."""
+        torch = _torch()
+        n = out.shape[0]
+        dout = torch.empty(n, GV, C, dtype=torch.bfloat16, device=self.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        N.denser_net_loss_div(out, target, U_WEIGHT, DIV_WEIGHT, dout, loss, n)
+        return loss, dout
+
     def train_step(self, x, target, mask, lr=1e-3):
         out, acts = self.forward(x)
-        loss, dout = self.loss_and_grad(out, target, mask)
+        if mask is None:
+            loss, dout = self.loss_and_grad_div(out, target)
+        else:
+            loss, dout = self.loss_and_grad(out, target, mask)
         grads = self.backward(acts, dout)
         self.step += 1
         for p, g, m, v in zip(self.params, grads, self.m, self.v):
@@ -114,12 +129,15 @@ class WarmStartNet:
 
     # -------------------------------------------------------- save / load
     def state_dict(self):
-        return {f"layer{i}": p.detach().cpu().numpy() for i, p in enumerate(self.params)}
+        sd = {f"layer{i}": p.detach().cpu().numpy() for i, p in enumerate(self.params)}
+        sd["dual_mode"] = np.array(self.dual_mode, dtype=np.int32)
+        return sd
 
     def load_state_dict(self, sd):
         torch = _torch()
         for i in range(4):
             self.params[i].copy_(torch.as_tensor(sd[f"layer{i}"], device=self.device))
+        self.dual_mode = int(sd["dual_mode"]) if "dual_mode" in sd else 1
         self._views()
         self.pack()
 
@@ -135,7 +153,7 @@ class WarmStartNet:
             x = torch.empty(n, GV, C, dtype=torch.bfloat16, device=self.device)
             N.denser_net_gather(ctx, blocks, n, x, stream)
             out, _ = self.forward(x)
-            N.denser_net_apply(ctx, blocks, n, out, 1 if dual else 0, stream)
+            N.denser_net_apply(ctx, blocks, n, out, self.dual_mode if dual else 0, stream)
 
 
 # ------------------------------------------------------------ training data
@@ -164,13 +182,19 @@ def solved_map(scenes, iters: int, gap_tol: float = 0.0, **params):
 
 
 # Loss weights of u and p: the squared distance in the metric of the Chambolle-Pock
-# analysis, |u - u*|^2 / tau + |p - p*|^2 / sigma (tau = 1/6, sigma = 0.5).
+# analysis, |u - u*|^2 / tau + |p - p*|^2 / sigma (tau = 1/6, sigma = 0.5).  The
+# divergence loss weighs (div p - div p*)^2 by DIV_WEIGHT instead of the p term: p* is
+# unique only up to a divergence-free part, which a regression on p cannot predict.
 U_WEIGHT, P_WEIGHT = 6.0, 2.0
+DIV_WEIGHT = 2.0
 
 
-def make_training_set(seeds, variants_per_seed: int, iters: int = 8000, gap_tol: float = 1e-7, per_map: int = 64):
-    """(x BF16 [n, 1000, 16], target FP32 [n, 4, 512], mask FP32 [n, 4, 512]) from the
-    plain solver on scene variants of the given seeds; masks carry the loss weights."""
+def make_training_set(seeds, variants_per_seed: int, iters: int = 8000, gap_tol: float = 1e-7, per_map: int = 64,
+                      div: bool = False):
+    """(x BF16 [n, 1000, 16], target, mask) from the plain solver on scene variants of the
+    given seeds.  p loss: target FP32 [n, 4, 512] and mask FP32 [n, 4, 512] carrying the
+    loss weights; divergence loss (div): target FP32 [n, 6, 512] of denser_net_targets_div
+    and mask None."""
     torch = _torch()
     xs, ts, ms = [], [], []
     jobs = [(s, v) for s in seeds for v in range(variants_per_seed)]
@@ -180,13 +204,18 @@ def make_training_set(seeds, variants_per_seed: int, iters: int = 8000, gap_tol:
         nb = N.denser_num_blocks(m.ctx)
         blocks = torch.arange(nb, dtype=torch.int32, device="cuda")
         x = torch.empty(nb, GV, C, dtype=torch.bfloat16, device="cuda")
-        t = torch.empty(nb, 4, 512, device="cuda")
-        mk = torch.empty(nb, 4, 512, device="cuda")
         N.denser_net_gather(m.ctx, blocks, nb, x)
-        N.denser_net_targets(m.ctx, blocks, nb, t, mk, U_WEIGHT, P_WEIGHT)
+        if div:
+            t = torch.empty(nb, 6, 512, device="cuda")
+            N.denser_net_targets_div(m.ctx, blocks, nb, t)
+            mk = None
+        else:
+            t = torch.empty(nb, 4, 512, device="cuda")
+            mk = torch.empty(nb, 4, 512, device="cuda")
+            N.denser_net_targets(m.ctx, blocks, nb, t, mk, U_WEIGHT, P_WEIGHT)
         xs.append(x), ts.append(t), ms.append(mk)
         m.close()
-    return torch.cat(xs), torch.cat(ts), torch.cat(ms)
+    return torch.cat(xs), torch.cat(ts), (None if div else torch.cat(ms))
 
 
 def train(net: WarmStartNet, data, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, log=None):
@@ -200,7 +229,8 @@ def train(net: WarmStartNet, data, epochs: int, batch: int = 256, lr: float = 1e
         tot = torch.zeros(1, dtype=torch.float64, device=x.device)
         for i in range(0, n - batch + 1, batch):
             idx = perm[i:i + batch]
-            tot += net.train_step(x[idx].contiguous(), t[idx].contiguous(), mk[idx].contiguous(), lr) * batch
+            tot += net.train_step(x[idx].contiguous(), t[idx].contiguous(),
+                                  None if mk is None else mk[idx].contiguous(), lr) * batch
         history.append(float(tot.item()) / max(1, (n // batch) * batch))
         if log:
             log(f"epoch {ep}: loss {history[-1]:.5f}")
@@ -267,7 +297,8 @@ def load_default(device=None):
 
 def main(argv=None):
     """python -m paper_1604_03734_gb300.warmstart OUT.npz [--seeds 100:200] [--variants 4]
-    [--epochs 30]: trains the network on scene variants of the given seeds and saves it."""
+    [--epochs 30] [--loss div|p]: trains the network on scene variants of the given seeds
+    and saves it."""
     import argparse
     ap = argparse.ArgumentParser()
     ap.add_argument("out")
@@ -275,10 +306,14 @@ def main(argv=None):
     ap.add_argument("--variants", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--eval-seeds", default="200:220")
+    ap.add_argument("--loss", default="div", choices=["div", "p"],
+                    help="div: u and the inner divergence of p (applied on inner edges); p: u and p")
+    ap.add_argument("--iters", type=int, default=8000, help="iterations of the plain solves that make the targets")
     args = ap.parse_args(argv)
     a, b = (int(v) for v in args.seeds.split(":"))
-    data = make_training_set(list(range(a, b)), args.variants)
+    data = make_training_set(list(range(a, b)), args.variants, iters=args.iters, div=args.loss == "div")
     net = WarmStartNet(seed=0)
+    net.dual_mode = 2 if args.loss == "div" else 1
     n_ep = args.epochs
     for ep in range(n_ep):
         lr = 2e-3 if ep < 0.4 * n_ep else (1e-3 if ep < 0.75 * n_ep else 3e-4)

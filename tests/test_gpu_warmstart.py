@@ -268,3 +268,54 @@ def test_warm_started_path_against_oracle(seed):
           f"oracle rel gap {(P - D) / abs(P):.2e}")
     assert st.converged and (P - D) / abs(P) <= 1.5e-4
     assert max(e0, e1, e2) <= 5e-3, results
+
+
+def test_divergence_loss_and_targets_against_oracle():
+    """denser_net_loss_div (loss and BF16 gradient) and denser_net_targets_div (from a map's
+    own state) against the FP64 definitions of oracle/net_oracle.py; apply mode 2 keeps p
+    on the inner edges only."""
+    rng = np.random.default_rng(30)
+    n = 3
+    om = rng.random((n, 512)) < 0.75
+    tgt = NO.targets_div(rng.uniform(-1, 1, (n, 512)), rng.standard_normal((3, n, 512)) * 0.5, om)
+    out4 = rng.standard_normal((n, 4, 512)) * 0.5
+    L_ref, g_ref = NO.loss_div(out4, tgt, WS.U_WEIGHT, WS.DIV_WEIGHT)
+    grid = np.zeros((n, 4, 10, 10, 10))
+    grid[:, :, 1:-1, 1:-1, 1:-1] = out4.reshape(n, 4, 8, 8, 8)
+    out = to_ours(grid)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dout = torch.empty(n, 1000, 16, dtype=torch.bfloat16, device="cuda")
+    N.denser_net_loss_div(dev(out), dev(tgt), WS.U_WEIGHT, WS.DIV_WEIGHT, dout, loss, n)
+    assert abs(loss.item() - L_ref) <= 1e-5 * L_ref
+    got = from_ours(dout.float().cpu().numpy().astype(np.float64), 4)
+    assert np.all(got[:, :, 0] == 0) and np.all(got[:, :, :, 0] == 0) and np.all(got[:, :, :, :, 9] == 0)
+    g = got[:, :, 1:-1, 1:-1, 1:-1].reshape(n, 4, 512)
+    assert np.max(np.abs(g - g_ref)) <= 1e-2 * np.max(np.abs(g_ref))
+    # targets from a regularised map's own state
+    from synth.scenes import tiny_scene
+    s = tiny_scene(seed=0)
+    d = s.depth_maps()
+    cam = s.camera
+    K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    with N.DenserMap() as m:
+        for k in range(len(d)):
+            N.denser_integrate(m.ctx, torch.from_numpy(np.ascontiguousarray(d[k])).cuda(), K, s.poses[k], 0)
+        N.denser_regularize(m.ctx, 50)
+        snap = m.snapshot(dual=True)
+        nb = len(snap["coords"])
+        t = torch.empty(nb, 6, 512, device="cuda")
+        N.denser_net_targets_div(m.ctx, None, nb, t)
+        want = NO.targets_div(snap["u"].astype(np.float64), snap["p"].astype(np.float64), snap["omega"].astype(bool))
+        got_t = t.cpu().numpy().astype(np.float64)
+        np.testing.assert_array_equal(got_t[:, [1, 3, 4, 5]], want[:, [1, 3, 4, 5]])
+        assert np.max(np.abs(got_t[:, [0, 2]] - want[:, [0, 2]])) <= 1e-6
+        # apply mode 2: p on the inner edges (projected), 0 on the edges crossing a block face
+        outs = torch.from_numpy(rng.standard_normal((nb, 1000, 16)).astype(np.float32) * 0.3).cuda()
+        N.denser_net_apply(m.ctx, None, nb, outs, 2)
+        st = m.snapshot(dual=True)
+    e_in = NO.inner_edges(snap["omega"].astype(bool))
+    assert np.all(st["p"][~e_in] == 0)
+    o = outs.cpu().numpy().reshape(nb, 10, 10, 10, 16)[:, 1:-1, 1:-1, 1:-1, 1:4].reshape(nb, 512, 3)
+    q = np.where(e_in, o.transpose(2, 0, 1), 0.0)
+    q = q / np.maximum(1.0, np.sqrt((q ** 2).sum(0)))[None]
+    assert np.max(np.abs(st["p"] - q)) <= 1e-6

@@ -174,3 +174,55 @@ def test_warm_state_masks_and_projection():
     inside = qn <= 1
     assert np.array_equal(p[:, inside], q[:, inside])
     np.testing.assert_allclose(p[:, ~inside] * qn[~inside], q[:, ~inside], rtol=1e-15, atol=1e-15)
+
+
+def test_inner_divergence_brute_force_and_adjoint():
+    """The inner divergence against a per-voxel loop of its definition, and against the
+    inner forward difference through the adjoint identity <grad u, p> = -<u, div p>."""
+    rng = np.random.default_rng(24)
+    n = 3
+    om = rng.random((n, 512)) < 0.7
+    e = NO.inner_edges(om)
+    p = rng.standard_normal((3, n, 512))
+    d = NO.inner_divergence(p, e)
+    for b in range(n):
+        for l in range(512):
+            lc = (l % 8, (l // 8) % 8, l // 64)
+            want = 0.0
+            for a, st in enumerate((1, 8, 64)):
+                if lc[a] < 7 and om[b, l] and om[b, l + st]:
+                    want += p[a, b, l]
+                if lc[a] > 0 and om[b, l - st] and om[b, l]:
+                    want -= p[a, b, l - st]
+            assert abs(d[b, l] - want) < 1e-12
+    u = rng.standard_normal((n, 512))
+    g = np.zeros((3, n, 512))
+    for a, st in enumerate((1, 8, 64)):
+        nxt = np.zeros_like(u)
+        idx = np.arange(512)
+        ok = (np.array([(l % 8, (l // 8) % 8, l // 64)[a] for l in idx]) < 7)
+        nxt[:, ok] = u[:, idx[ok] + st]
+        g[a] = np.where(e[a], nxt - u, 0.0)
+    assert abs(np.sum(g * p) + np.sum(u * d)) < 1e-10
+
+
+def test_loss_div_gradient_by_finite_differences():
+    rng = np.random.default_rng(25)
+    n = 2
+    om = rng.random((n, 512)) < 0.75
+    tgt = NO.targets_div(rng.uniform(-1, 1, (n, 512)), rng.standard_normal((3, n, 512)) * 0.5, om)
+    out = rng.standard_normal((n, 4, 512)) * 0.5
+    L, g = NO.loss_div(out, tgt, 6.0, 2.0)
+    for _ in range(40):
+        i, c, l = rng.integers(n), rng.integers(4), rng.integers(512)
+        h = 1e-6
+        o1, o2 = out.copy(), out.copy()
+        o1[i, c, l] += h
+        o2[i, c, l] -= h
+        fd = (NO.loss_div(o1, tgt, 6.0, 2.0)[0] - NO.loss_div(o2, tgt, 6.0, 2.0)[0]) / (2 * h)
+        assert abs(fd - g[i, c, l]) <= 1e-6 * max(1.0, abs(fd)), (i, c, l, fd, g[i, c, l])
+    # targets of the exact state give zero loss
+    u, p = rng.uniform(-1, 1, (n, 512)), rng.standard_normal((3, n, 512))
+    t = NO.targets_div(u, p, om)
+    exact = np.concatenate([np.where(om, u, 0)[:, None], p.transpose(1, 0, 2)], axis=1)
+    assert NO.loss_div(exact, t, 6.0, 2.0)[0] < 1e-20
