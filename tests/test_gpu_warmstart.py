@@ -237,7 +237,11 @@ def test_warm_started_path_against_oracle(seed):
     g = grid_from_blocks([tuple(c) for c in rs["coords"]], rs["f"], rs["w"])
     prob = O.PDProblem(g)
     om = prob.om.reshape(-1, 512)
+    # the dual goes on every Eq. 3 edge (network trained on p) or on the block's inner edges
+    # only (trained on div p), as the network's apply mode says
     edges = O.edge_mask(prob.om, prob.fwd).reshape(3, -1, 512)
+    if net.dual_mode == 2:
+        edges = edges & NO.inner_edges(om)
     out = NO.forward_stored(params, NO.gather(rs["coords"], rs["f"], rs["w"]))
     ref.set_state(*NO.warm_state(out, om, edges))
 
