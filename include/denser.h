@@ -118,13 +118,16 @@ typedef struct {
  *                    default, with order 0 and ctas_per_sm 2,
  *                 5: as 4, and each thread's row of the next block's own fields is
  *                    copied (cp.async) into a shared-memory slot of its own while the
- *                    current block computes
+ *                    current block computes,
+ *                 6: software-pipelined rows: the next block's halos (cp.async, into a
+ *                    second tile set) and own rows (into registers) are in flight while
+ *                    the current block computes
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)
  *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default); for
  *                 the row kernels (2, 4) it picks the register budget: 0/1 -> 8 CTAs of
- *                 64 threads per SM, 2 -> 10, 3 -> 12 (kernel 5: 2 -> 10, else 8); for
- *                 kernel 3 it caps CTAs at 2x this
+ *                 64 threads per SM, 2 -> 10, 3 -> 12 (kernel 5: 2 -> 10, else 8; kernel 6:
+ *                 1 -> 5, 3 -> 7, else 6); for kernel 3 it caps CTAs at 2x this
  *   use_graph     1: the iteration loop of denser_regularize runs as one CUDA graph: a
  *                 WHILE conditional node whose body is gap_every sweeps (10 when no gap
  *                 test is asked for) plus the FP64 gap evaluation, and whose condition is

@@ -26,6 +26,7 @@ DEFAULT_CANDIDATES = (
     (3, 1, 0, 1), (3, 0, 0, 1), (1, 1, 0, 1), (0, 1, 0, 1), (2, 1, 0, 0),
     (4, 1, 0, 1), (4, 1, 2, 1), (4, 0, 2, 1), (4, 0, 0, 1), (4, 0, 3, 1),
     (5, 0, 0, 1), (5, 1, 0, 1), (5, 0, 2, 1),
+    (6, 0, 0, 1), (6, 1, 0, 1), (6, 0, 1, 1), (6, 0, 3, 1),
 )
 
 _cache: dict = {}

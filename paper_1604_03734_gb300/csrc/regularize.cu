@@ -799,6 +799,103 @@ __device__ __forceinline__ void issue_own_row(const SweepArgs<T>& a, char* slot,
     cp_async4(slot + L::kBits, a.bits + (size_t)b * 16 + (r >> 2));
 }
 
+// The arithmetic half of one block of the row sweep, after its staging: the dual steps
+// (the row's voxels, its -x voxel and one voxel of each low face), then the primal step
+// and the relaxation, and the stores.  om_r holds the row's Omega bits (0-7) and those of
+// its x halos (8: x = 8, 9: x = -1); hm0..hm2 the old p at x = -1.
+template <typename T>
+__device__ __forceinline__ void rows_compute(const SweepArgs<T>& a, RowTiles& s, int r, unsigned om_r, float* ub,
+                                             float* p0, float* p1, float* p2, const float* uo, const float* fv,
+                                             const float* wv, float hm0, float hm1, float hm2, size_t base) {
+    const int ly = r & 7, lz = r >> 3;
+    const int rr = r10(ly, lz);
+    const size_t ps = a.pstride;
+    // ------------------------------------------------------- dual steps
+    {
+        float uy[8], uz[8];
+        lds_row(s.ub[r10(ly + 1, lz)], uy);
+        lds_row(s.ub[r10(ly, lz + 1)], uz);
+        const unsigned om_y = s.om[r10(ly + 1, lz)], om_z = s.om[r10(ly, lz + 1)];
+        const float xp = s.xhp[rr];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const bool o = (om_r >> x) & 1u;
+            const float g0 = masked_diff(o && ((om_r >> (x + 1)) & 1u), x < 7 ? ub[x < 7 ? x + 1 : 7] : xp, ub[x]);
+            const float g1 = masked_diff(o && ((om_y >> x) & 1u), uy[x], ub[x]);
+            const float g2 = masked_diff(o && ((om_z >> x) & 1u), uz[x], ub[x]);
+            float out[3];
+            dual_update(p0[x], p1[x], p2[x], g0, g1, g2, a.sigma, out);
+            p0[x] = out[0], p1[x] = out[1], p2[x] = out[2];
+        }
+        // the -x face voxel (-1, ly, lz)
+        const bool o = (om_r >> 9) & 1u;
+        const float um = s.xhm[rr];
+        const int ry = r10(ly + 1, lz), rz = r10(ly, lz + 1);
+        const float g0 = masked_diff(o && (om_r & 1u), ub[0], um);
+        const float g1 = masked_diff(o && ((s.om[ry] >> 9) & 1u), s.xhm[ry], um);
+        const float g2 = masked_diff(o && ((s.om[rz] >> 9) & 1u), s.xhm[rz], um);
+        float out[3];
+        dual_update(hm0, hm1, hm2, g0, g1, g2, a.sigma, out);
+        s.pxm[r] = out[0];
+    }
+    {
+        // one voxel of the -y face, (fx, -1, fz), and one of the -z face, (fx, fy, -1)
+        const int fx = r & 7, fw = r >> 3;
+        {  // -y face: fw is z
+            const int d = r10(-1, fw), dz = r10(-1, fw + 1), dc = r10(0, fw);
+            const unsigned om = s.om[d];
+            const bool o = (om >> fx) & 1u;
+            const float v = s.ub[d][fx];
+            const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
+            const float g1 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
+            const float g2 = masked_diff(o && ((s.om[dz] >> fx) & 1u), s.ub[dz][fx], v);
+            float out[3];
+            dual_update(s.pfy[0][fw][fx], s.pfy[1][fw][fx], s.pfy[2][fw][fx], g0, g1, g2, a.sigma, out);
+            s.py[r9(-1, fw)][fx] = out[1];
+        }
+        {  // -z face: fw is y
+            const int d = r10(fw, -1), dy = r10(fw + 1, -1), dc = r10(fw, 0);
+            const unsigned om = s.om[d];
+            const bool o = (om >> fx) & 1u;
+            const float v = s.ub[d][fx];
+            const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
+            const float g1 = masked_diff(o && ((s.om[dy] >> fx) & 1u), s.ub[dy][fx], v);
+            const float g2 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
+            float out[3];
+            dual_update(s.pfz[0][fw][fx], s.pfz[1][fw][fx], s.pfz[2][fw][fx], g0, g1, g2, a.sigma, out);
+            s.pz[r9(fw, -1)][fx] = out[2];
+        }
+    }
+    sts_row(s.py[r9(ly, lz)], p1);
+    sts_row(s.pz[r9(ly, lz)], p2);
+    __syncthreads();
+
+    // ----------------------------------------------- primal + relaxation
+    {
+        float pym[8], pzm[8];
+        lds_row(s.py[r9(ly - 1, lz)], pym);
+        lds_row(s.pz[r9(ly, lz - 1)], pzm);
+        const unsigned om_ym = s.om[r10(ly - 1, lz)], om_zm = s.om[r10(ly, lz - 1)];
+        const unsigned om_yp = s.om[r10(ly + 1, lz)], om_zp = s.om[r10(ly, lz + 1)];
+        const float pxm = s.pxm[r];
+        float un[8], ubn[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const bool o = (om_r >> x) & 1u;
+            const bool exm = o && (x > 0 ? ((om_r >> (x - 1)) & 1u) : ((om_r >> 9) & 1u));
+            const float dv = div_terms(o && ((om_r >> (x + 1)) & 1u), p0[x], exm, x > 0 ? p0[x > 0 ? x - 1 : 0] : pxm,
+                                       o && ((om_yp >> x) & 1u), p1[x], o && ((om_ym >> x) & 1u), pym[x],
+                                       o && ((om_zp >> x) & 1u), p2[x], o && ((om_zm >> x) & 1u), pzm[x]);
+            primal_update(o, uo[x], o ? dv : 0.0f, fv[x], wv[x], a.tau, a.tau_lam, a.theta, &un[x], &ubn[x]);
+        }
+        st_row<T>(a.u + base, un);
+        st_row<T>(a.ub_out + base, ubn);
+        st_row<T>(a.p_out + base, p0);
+        st_row<T>(a.p_out + ps + base, p1);
+        st_row<T>(a.p_out + 2 * ps + base, p2);
+    }
+}
+
 // One block of the row sweep: staging of the rows, faces and edges, the dual steps,
 // the primal step and the relaxation.  `stage` holds the block's own fields when they
 // were prefetched into shared memory (else they are read from global memory).
@@ -943,91 +1040,7 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
     }
     __syncthreads();
     if constexpr (kAsync) hm0 = s.phm[0][r], hm1 = s.phm[1][r], hm2 = s.phm[2][r];
-
-    // ------------------------------------------------------- dual steps
-    {
-        float uy[8], uz[8];
-        lds_row(s.ub[r10(ly + 1, lz)], uy);
-        lds_row(s.ub[r10(ly, lz + 1)], uz);
-        const unsigned om_y = s.om[r10(ly + 1, lz)], om_z = s.om[r10(ly, lz + 1)];
-        const float xp = s.xhp[rr];
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const bool o = (om_r >> x) & 1u;
-            const float g0 = masked_diff(o && ((om_r >> (x + 1)) & 1u), x < 7 ? ub[x < 7 ? x + 1 : 7] : xp, ub[x]);
-            const float g1 = masked_diff(o && ((om_y >> x) & 1u), uy[x], ub[x]);
-            const float g2 = masked_diff(o && ((om_z >> x) & 1u), uz[x], ub[x]);
-            float out[3];
-            dual_update(p0[x], p1[x], p2[x], g0, g1, g2, a.sigma, out);
-            p0[x] = out[0], p1[x] = out[1], p2[x] = out[2];
-        }
-        // the -x face voxel (-1, ly, lz)
-        const bool o = (om_r >> 9) & 1u;
-        const float um = s.xhm[rr];
-        const int ry = r10(ly + 1, lz), rz = r10(ly, lz + 1);
-        const float g0 = masked_diff(o && (om_r & 1u), ub[0], um);
-        const float g1 = masked_diff(o && ((s.om[ry] >> 9) & 1u), s.xhm[ry], um);
-        const float g2 = masked_diff(o && ((s.om[rz] >> 9) & 1u), s.xhm[rz], um);
-        float out[3];
-        dual_update(hm0, hm1, hm2, g0, g1, g2, a.sigma, out);
-        s.pxm[r] = out[0];
-    }
-    {
-        // one voxel of the -y face, (fx, -1, fz), and one of the -z face, (fx, fy, -1)
-        const int fx = r & 7, fw = r >> 3;
-        {  // -y face: fw is z
-            const int d = r10(-1, fw), dz = r10(-1, fw + 1), dc = r10(0, fw);
-            const unsigned om = s.om[d];
-            const bool o = (om >> fx) & 1u;
-            const float v = s.ub[d][fx];
-            const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
-            const float g1 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
-            const float g2 = masked_diff(o && ((s.om[dz] >> fx) & 1u), s.ub[dz][fx], v);
-            float out[3];
-            dual_update(s.pfy[0][fw][fx], s.pfy[1][fw][fx], s.pfy[2][fw][fx], g0, g1, g2, a.sigma, out);
-            s.py[r9(-1, fw)][fx] = out[1];
-        }
-        {  // -z face: fw is y
-            const int d = r10(fw, -1), dy = r10(fw + 1, -1), dc = r10(fw, 0);
-            const unsigned om = s.om[d];
-            const bool o = (om >> fx) & 1u;
-            const float v = s.ub[d][fx];
-            const float g0 = masked_diff(o && ((om >> (fx + 1)) & 1u), fx < 7 ? s.ub[d][fx < 7 ? fx + 1 : 7] : s.xhp[d], v);
-            const float g1 = masked_diff(o && ((s.om[dy] >> fx) & 1u), s.ub[dy][fx], v);
-            const float g2 = masked_diff(o && ((s.om[dc] >> fx) & 1u), s.ub[dc][fx], v);
-            float out[3];
-            dual_update(s.pfz[0][fw][fx], s.pfz[1][fw][fx], s.pfz[2][fw][fx], g0, g1, g2, a.sigma, out);
-            s.pz[r9(fw, -1)][fx] = out[2];
-        }
-    }
-    sts_row(s.py[r9(ly, lz)], p1);
-    sts_row(s.pz[r9(ly, lz)], p2);
-    __syncthreads();
-
-    // ----------------------------------------------- primal + relaxation
-    {
-        float pym[8], pzm[8];
-        lds_row(s.py[r9(ly - 1, lz)], pym);
-        lds_row(s.pz[r9(ly, lz - 1)], pzm);
-        const unsigned om_ym = s.om[r10(ly - 1, lz)], om_zm = s.om[r10(ly, lz - 1)];
-        const unsigned om_yp = s.om[r10(ly + 1, lz)], om_zp = s.om[r10(ly, lz + 1)];
-        const float pxm = s.pxm[r];
-        float un[8], ubn[8];
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const bool o = (om_r >> x) & 1u;
-            const bool exm = o && (x > 0 ? ((om_r >> (x - 1)) & 1u) : ((om_r >> 9) & 1u));
-            const float dv = div_terms(o && ((om_r >> (x + 1)) & 1u), p0[x], exm, x > 0 ? p0[x > 0 ? x - 1 : 0] : pxm,
-                                       o && ((om_yp >> x) & 1u), p1[x], o && ((om_ym >> x) & 1u), pym[x],
-                                       o && ((om_zp >> x) & 1u), p2[x], o && ((om_zm >> x) & 1u), pzm[x]);
-            primal_update(o, uo[x], o ? dv : 0.0f, fv[x], wv[x], a.tau, a.tau_lam, a.theta, &un[x], &ubn[x]);
-        }
-        st_row<T>(a.u + base, un);
-        st_row<T>(a.ub_out + base, ubn);
-        st_row<T>(a.p_out + base, p0);
-        st_row<T>(a.p_out + ps + base, p1);
-        st_row<T>(a.p_out + 2 * ps + base, p2);
-    }
+    rows_compute<T>(a, s, r, om_r, ub, p0, p1, p2, uo, fv, wv, hm0, hm1, hm2, base);
 }
 
 // Loads the neighbour row of block b (every thread reads the same 48 bytes).
@@ -1098,6 +1111,122 @@ __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_prefetch_kernel(
         b = b_next;
 #pragma unroll
         for (int i = 0; i < kNeighbours; ++i) nb[i] = nb_next[i];
+    }
+}
+
+// One thread's row of a block's own fields as stored (16-byte words), loaded ahead of use.
+template <typename T>
+struct OwnRows {
+    static constexpr int R = sizeof(T) == 4 ? 2 : 1;  // 16-byte words per row of 8 values
+    uint4 ub[R], p[3][R], u[R];
+    float4 f[2], w[2];
+    unsigned bits;  // the row's Omega byte
+};
+
+template <typename T>
+__device__ __forceinline__ void load_own_rows(const SweepArgs<T>& a, int b, int r, OwnRows<T>& o) {
+    constexpr int R = OwnRows<T>::R;
+    const size_t base = (size_t)b * kBlockVoxels + 8 * r;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        o.ub[i] = __ldg(reinterpret_cast<const uint4*>(a.ub_in + base) + i);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o.p[c][i] = __ldg(reinterpret_cast<const uint4*>(a.p_in + c * a.pstride + base) + i);
+        o.u[i] = __ldg(reinterpret_cast<const uint4*>(a.u + base) + i);
+    }
+    o.f[0] = __ldg(reinterpret_cast<const float4*>(a.f + base));
+    o.f[1] = __ldg(reinterpret_cast<const float4*>(a.f + base) + 1);
+    o.w[0] = __ldg(reinterpret_cast<const float4*>(a.w + base));
+    o.w[1] = __ldg(reinterpret_cast<const float4*>(a.w + base) + 1);
+    o.bits = row_bits(a.bits, b, r);
+}
+
+template <typename T>
+__device__ __forceinline__ void unpack_row(const uint4* q, float* v) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            v[4 * i] = __uint_as_float(q[i].x), v[4 * i + 1] = __uint_as_float(q[i].y);
+            v[4 * i + 2] = __uint_as_float(q[i].z), v[4 * i + 3] = __uint_as_float(q[i].w);
+        }
+    } else {
+        const T* h = reinterpret_cast<const T*>(q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(h + i);
+    }
+}
+
+__device__ __forceinline__ void unpack_f4(const float4* q, float* v) {
+    v[0] = q[0].x, v[1] = q[0].y, v[2] = q[0].z, v[3] = q[0].w;
+    v[4] = q[1].x, v[5] = q[1].y, v[6] = q[1].z, v[7] = q[1].w;
+}
+
+// Software-pipelined row sweep: while a CTA computes block k from one tile set, the
+// halos of block k + grid are already being copied (cp.async) into the other tile set,
+// and every thread's own row of that block is in flight into registers.  A block's
+// data is therefore requested one whole block ahead, and a CTA's critical path is its
+// arithmetic rather than its memory round trips.  Same arithmetic as every other
+// variant (bit-identical iterates).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_pipelined_kernel(SweepArgs<T> a) {
+    __shared__ RowTiles tiles[2];
+    __shared__ HaloRaw<T> raws[2];
+    const int G = gridDim.x;
+    const int r = threadIdx.x, ly = r & 7, lz = r >> 3, rr = r10(ly, lz);
+    int k = blockIdx.x;
+    if (k >= a.n_blocks) return;
+    int b = a.order ? __ldg(a.order + k) : k;
+    int nb[kNeighbours], nb_next[kNeighbours];
+    load_nbr_row(a.nbr, b, nb);
+    OwnRows<T> own, own_next;
+    unsigned hom[4], hom_next[4];
+    issue_row_halos<T>(a, tiles[0], raws[0], r, ly, lz, nb, hom);
+    load_own_rows<T>(a, b, r, own);
+    for (int i = 0; k < a.n_blocks; k += G, ++i) {
+        RowTiles& S = tiles[i & 1];
+        const int kn = k + G;
+        int b_next = -1;
+        if (kn < a.n_blocks) {
+            b_next = a.order ? __ldg(a.order + kn) : kn;
+            load_nbr_row(a.nbr, b_next, nb_next);
+        }
+        float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
+        unpack_row<T>(own.ub, ub);
+        unpack_row<T>(own.p[0], p0);
+        unpack_row<T>(own.p[1], p1);
+        unpack_row<T>(own.p[2], p2);
+        unpack_row<T>(own.u, uo);
+        unpack_f4(own.f, fv);
+        unpack_f4(own.w, wv);
+        const unsigned om_r = own.bits | hom[0];
+        // the next block goes in flight: its halos into the other tile set (free since the
+        // barrier that ended the previous block), its own row into registers
+        if (b_next >= 0) {
+            issue_row_halos<T>(a, tiles[(i & 1) ^ 1], raws[(i & 1) ^ 1], r, ly, lz, nb_next, hom_next);
+            load_own_rows<T>(a, b_next, r, own_next);
+        } else {
+            cp_async_commit();  // an empty group: the wait below then always leaves the newest group
+        }
+        sts_row(S.ub[rr], ub);
+        S.om[rr] = (unsigned short)om_r;
+        if (ly == 7) S.om[r10(8, lz)] = (unsigned short)hom[1];
+        if (ly == 0) S.om[r10(-1, lz)] = (unsigned short)hom[1];
+        if (lz == 7) S.om[r10(ly, 8)] = (unsigned short)hom[2];
+        if (lz == 0) S.om[r10(ly, -1)] = (unsigned short)hom[2];
+        if (ly == 0 && lz == 7) S.om[r10(-1, 8)] = (unsigned short)hom[3];
+        if (ly == 7 && lz == 0) S.om[r10(8, -1)] = (unsigned short)hom[3];
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this block's halos have landed
+        if constexpr (sizeof(T) != 4) convert_row_halos<T>(S, raws[i & 1], r, ly, lz);
+        __syncthreads();
+        const float hm0 = S.phm[0][r], hm1 = S.phm[1][r], hm2 = S.phm[2][r];
+        rows_compute<T>(a, S, r, om_r, ub, p0, p1, p2, uo, fv, wv, hm0, hm1, hm2, (size_t)b * kBlockVoxels + 8 * r);
+        __syncthreads();  // this tile set is refilled for the block after next
+        b = b_next;
+#pragma unroll
+        for (int q = 0; q < kNeighbours; ++q) nb[q] = nb_next[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) hom[q] = hom_next[q];
+        own = own_next;
     }
 }
 
@@ -1371,6 +1500,23 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, 8, true>, kRowThreads, 0);
             sweep_rows_kernel<T, 8, true><<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)),
                                             kRowThreads, 0, s>>>(a);
+        }
+    } else if (c->sched.sweep_kernel == 6) {
+        // software-pipelined row sweep: ctas_per_sm 1 -> registers for 5 resident CTAs,
+        // 3 -> 7, otherwise 6
+        int per_sm = 0;
+        if (c->sched.ctas_per_sm == 1) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_pipelined_kernel<T, 5>, kRowThreads, 0);
+            sweep_rows_pipelined_kernel<T, 5>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
+        } else if (c->sched.ctas_per_sm == 3) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_pipelined_kernel<T, 7>, kRowThreads, 0);
+            sweep_rows_pipelined_kernel<T, 7>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_pipelined_kernel<T, 6>, kRowThreads, 0);
+            sweep_rows_pipelined_kernel<T, 6>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
         }
     } else if (c->sched.sweep_kernel == 5) {
         // prefetching row sweep (about 27 KB of shared memory per CTA): ctas_per_sm 2 caps
