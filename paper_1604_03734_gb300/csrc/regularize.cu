@@ -162,6 +162,13 @@ __device__ inline float div_terms(bool ex, float px, bool exm, float pxm, bool e
     return __fadd_rn(__fadd_rn(d0, d1), d2);
 }
 
+// The hardware's approximate reciprocal (at most 1 ulp from 1/x); x >= 1 here.
+__device__ inline float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;\n" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Primal proximal step on Omega and the relaxation.
 __device__ inline void primal_update(bool o, float uo, float dv, float fv, float wv, float tau, float tau_lam,
                                      float theta, float* un, float* ubn) {
@@ -169,7 +176,7 @@ __device__ inline void primal_update(bool o, float uo, float dv, float fv, float
     if (o) {
         const float ut = __fmaf_rn(tau, dv, uo);
         const float tlw = __fmul_rn(tau_lam, wv);
-        u = __fmul_rn(__fmaf_rn(tlw, fv, ut), __frcp_rn(__fadd_rn(1.0f, tlw)));
+        u = __fmul_rn(__fmaf_rn(tlw, fv, ut), rcp_approx(__fadd_rn(1.0f, tlw)));
     }
     *un = u;
     *ubn = __fmaf_rn(theta, __fsub_rn(u, uo), u);
@@ -817,12 +824,13 @@ __device__ __forceinline__ void rows_compute(const SweepArgs<T>& a, RowTiles& s,
         lds_row(s.ub[r10(ly, lz + 1)], uz);
         const unsigned om_y = s.om[r10(ly + 1, lz)], om_z = s.om[r10(ly, lz + 1)];
         const float xp = s.xhp[rr];
+        // Eq. 3 edge masks of the row, one bit per voxel (bit 8 of om_r is the +x halo)
+        const unsigned ex = om_r & (om_r >> 1), ey = om_r & om_y, ez = om_r & om_z;
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
-            const bool o = (om_r >> x) & 1u;
-            const float g0 = masked_diff(o && ((om_r >> (x + 1)) & 1u), x < 7 ? ub[x < 7 ? x + 1 : 7] : xp, ub[x]);
-            const float g1 = masked_diff(o && ((om_y >> x) & 1u), uy[x], ub[x]);
-            const float g2 = masked_diff(o && ((om_z >> x) & 1u), uz[x], ub[x]);
+            const float g0 = masked_diff((ex >> x) & 1u, x < 7 ? ub[x < 7 ? x + 1 : 7] : xp, ub[x]);
+            const float g1 = masked_diff((ey >> x) & 1u, uy[x], ub[x]);
+            const float g2 = masked_diff((ez >> x) & 1u, uz[x], ub[x]);
             float out[3];
             dual_update(p0[x], p1[x], p2[x], g0, g1, g2, a.sigma, out);
             p0[x] = out[0], p1[x] = out[1], p2[x] = out[2];
@@ -878,14 +886,16 @@ __device__ __forceinline__ void rows_compute(const SweepArgs<T>& a, RowTiles& s,
         const unsigned om_ym = s.om[r10(ly - 1, lz)], om_zm = s.om[r10(ly, lz - 1)];
         const unsigned om_yp = s.om[r10(ly + 1, lz)], om_zp = s.om[r10(ly, lz + 1)];
         const float pxm = s.pxm[r];
+        // edge masks of the row's voxels towards +a and from -a (bit 9 of om_r is the -x halo)
+        const unsigned exp_ = om_r & (om_r >> 1), exm_ = om_r & ((om_r << 1) | ((om_r >> 9) & 1u));
+        const unsigned eyp = om_r & om_yp, eym = om_r & om_ym, ezp = om_r & om_zp, ezm = om_r & om_zm;
         float un[8], ubn[8];
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
             const bool o = (om_r >> x) & 1u;
-            const bool exm = o && (x > 0 ? ((om_r >> (x - 1)) & 1u) : ((om_r >> 9) & 1u));
-            const float dv = div_terms(o && ((om_r >> (x + 1)) & 1u), p0[x], exm, x > 0 ? p0[x > 0 ? x - 1 : 0] : pxm,
-                                       o && ((om_yp >> x) & 1u), p1[x], o && ((om_ym >> x) & 1u), pym[x],
-                                       o && ((om_zp >> x) & 1u), p2[x], o && ((om_zm >> x) & 1u), pzm[x]);
+            const float dv = div_terms((exp_ >> x) & 1u, p0[x], (exm_ >> x) & 1u, x > 0 ? p0[x > 0 ? x - 1 : 0] : pxm,
+                                       (eyp >> x) & 1u, p1[x], (eym >> x) & 1u, pym[x],
+                                       (ezp >> x) & 1u, p2[x], (ezm >> x) & 1u, pzm[x]);
             primal_update(o, uo[x], o ? dv : 0.0f, fv[x], wv[x], a.tau, a.tau_lam, a.theta, &un[x], &ubn[x]);
         }
         st_row<T>(a.u + base, un);
