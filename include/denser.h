@@ -115,7 +115,8 @@ typedef struct {
  *                    (TMA) into a double-buffered shared-memory stage,
  *                 4: rows with the halos (faces, edges, x halos) copied asynchronously
  *                    (cp.async) into shared memory while the block's own rows load; the
- *                    default, with order 0 and ctas_per_sm 2,
+ *                    default for FP32 storage, with order 0 and ctas_per_sm 2 (16-bit
+ *                    storage defaults to kernel 2, order 0, ctas_per_sm 2),
  *                 5: as 4, and each thread's row of the next block's own fields is
  *                    copied (cp.async) into a shared-memory slot of its own while the
  *                    current block computes,

@@ -135,32 +135,16 @@ struct RayKeys {
     }
 };
 
-// Inserts the pending keys of a warp.  Round after round every lane offers its next key
-// and lanes offering the same key elect one leader (match.any); the elections need no
-// memory, so they all come first.  Then every leader probes the home slots of all the
-// keys it leads at once (up to four loads in flight instead of one round trip per
-// round): a key found there only lowers its birth, the others take the full insertion.
-// The inserted set and the births do not depend on the order, so neither does the map.
+// Inserts the pending keys of a warp: round after round every lane offers its next key,
+// lanes offering the same key elect one leader (match.any), and the leaders insert.
 __device__ inline void warp_insert(const DeviceMap& m, const RayKeys& rk, int lane, int frame) {
-    RayKeys led;
     for (int i = 0;; ++i) {
         const unsigned long long key = i < rk.count ? rk.at(i) : kEmptyKey;
         const unsigned active = __ballot_sync(0xffffffffu, key != kEmptyKey);
         if (!active) break;
         if (key != kEmptyKey) {
             const unsigned peers = __match_any_sync(active, key);
-            if (lane == __ffs(peers) - 1) led.push(key);  // at most one key per round, four rounds
-        }
-    }
-    unsigned long long cur[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (j < led.count) cur[j] = __ldcg(m.hash_keys + (hash_key(led.at(j)) & m.slot_mask));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if (j < led.count) {
-            if (cur[j] == led.at(j)) atomicMin(m.hash_birth + (hash_key(led.at(j)) & m.slot_mask), frame);
-            else hash_insert(m, led.at(j), frame);
+            if (lane == __ffs(peers) - 1) hash_insert(m, key, frame);
         }
     }
 }

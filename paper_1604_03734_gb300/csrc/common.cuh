@@ -89,13 +89,37 @@ template <> struct Store<float> {
     __device__ static float ld(const float* p) { return *p; }
     __device__ static void st(float* p, float v) { *p = v; }
 };
+// The 16-bit types also convert pairs (a 32-bit word, lower address in the low half):
+// the same values as two single conversions, in fewer instructions.
 template <> struct Store<__half> {
     __device__ static float ld(const __half* p) { return __half2float(*p); }
     __device__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+    __device__ static float2 ld2(uint32_t w) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    }
+    __device__ static uint32_t st2(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
 };
 template <> struct Store<__nv_bfloat16> {
     __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static float2 ld2(uint32_t w) {
+        __nv_bfloat162 h;
+        memcpy(&h, &w, 4);
+        return __bfloat1622float2(h);
+    }
+    __device__ static uint32_t st2(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
 };
 
 // All device pointers of one context.

@@ -510,6 +510,13 @@ struct __align__(16) RowTiles {
     unsigned short om[100];  // Omega: bits 0-7 at x = 0..7, bit 8 at x = 8, bit 9 at x = -1
 };
 
+// 8 stored 16-bit values (one 16-byte word) as floats, converted in pairs.
+template <typename T>
+__device__ inline void unpack8(const uint4& q, float* v) {
+    const float2 a = Store<T>::ld2(q.x), b = Store<T>::ld2(q.y), c = Store<T>::ld2(q.z), d = Store<T>::ld2(q.w);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y, v[4] = c.x, v[5] = c.y, v[6] = d.x, v[7] = d.y;
+}
+
 template <typename T>
 __device__ inline void ld_row(const T* __restrict__ p, float* v) {
     if constexpr (sizeof(T) == 4) {
@@ -518,9 +525,7 @@ __device__ inline void ld_row(const T* __restrict__ p, float* v) {
         v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
     } else {
         const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
-        const T* h = reinterpret_cast<const T*>(&q);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(h + i);
+        unpack8<T>(q, v);
     }
 }
 
@@ -530,11 +535,8 @@ __device__ inline void st_row(T* p, const float* v) {
         reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
         reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
     } else {
-        uint4 q;
-        T* h = reinterpret_cast<T*>(&q);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) Store<T>::st(h + i, v[i]);
-        *reinterpret_cast<uint4*>(p) = q;
+        *reinterpret_cast<uint4*>(p) = make_uint4(Store<T>::st2(v[0], v[1]), Store<T>::st2(v[2], v[3]),
+                                                  Store<T>::st2(v[4], v[5]), Store<T>::st2(v[6], v[7]));
     }
 }
 
@@ -601,10 +603,7 @@ __device__ inline void ld_row_smem(const T* p, float* v) {
     if constexpr (sizeof(T) == 4) {
         lds_row(reinterpret_cast<const float*>(p), v);
     } else {
-        const uint4 q = *reinterpret_cast<const uint4*>(p);
-        const T* h = reinterpret_cast<const T*>(&q);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(h + i);
+        unpack8<T>(*reinterpret_cast<const uint4*>(p), v);
     }
 }
 
@@ -731,8 +730,7 @@ __device__ __forceinline__ void convert_row_halos(RowTiles& s, const HaloRaw<T>&
     const int rr = r10(ly, lz);
     auto row = [&](float* dst, const T* src) {
         float v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(src + i);
+        unpack8<T>(*reinterpret_cast<const uint4*>(src), v);
         sts_row(dst, v);
     };
     s.xhp[rr] = word_half<T>(raw.xhp[rr], 0);
@@ -1160,9 +1158,7 @@ __device__ __forceinline__ void unpack_row(const uint4* q, float* v) {
             v[4 * i + 2] = __uint_as_float(q[i].z), v[4 * i + 3] = __uint_as_float(q[i].w);
         }
     } else {
-        const T* h = reinterpret_cast<const T*>(q);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = Store<T>::ld(h + i);
+        unpack8<T>(q[0], v);
     }
 }
 
