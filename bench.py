@@ -563,7 +563,8 @@ def main():
     achieved = bpv * nvox / (sweep_avg_ms / 1e3) / 1e9
     kernel_name = ["sweep_kernel", "sweep_pipe_kernel", "sweep_rows_kernel", "sweep_rows_tma_kernel",
                    "sweep_rows_kernel", "sweep_rows_prefetch_kernel",
-                   "sweep_rows_pipelined_kernel"][N.denser_get_schedule(ctx)["sweep_kernel"]]
+                   "sweep_rows_pipelined_kernel", "sweep_rows_kernel",
+                   "sweep_rows_kernel"][N.denser_get_schedule(ctx)["sweep_kernel"]]
 
     if rank != 0:
         if world > 1:

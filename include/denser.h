@@ -114,19 +114,23 @@ typedef struct {
  *                 3: rows with the next block's own fields prefetched by 1-D bulk copies
  *                    (TMA) into a double-buffered shared-memory stage,
  *                 4: rows with the halos (faces, edges, x halos) copied asynchronously
- *                    (cp.async) into shared memory while the block's own rows load; the
- *                    default for FP32 storage, with order 0 and ctas_per_sm 2 (16-bit
- *                    storage defaults to kernel 2, order 0, ctas_per_sm 2),
+ *                    (cp.async) into shared memory while the block's own rows load,
  *                 5: as 4, and each thread's row of the next block's own fields is
  *                    copied (cp.async) into a shared-memory slot of its own while the
  *                    current block computes,
  *                 6: software-pipelined rows: the next block's halos (cp.async, into a
  *                    second tile set) and own rows (into registers) are in flight while
- *                    the current block computes
+ *                    the current block computes,
+ *                 7: as 4 with the face and edge halos split into balanced items over
+ *                    all 64 threads (82 row items: two per thread for 18 threads, one
+ *                    for the rest) instead of one branch per face; the default for FP32
+ *                    storage, with order 0 and ctas_per_sm 2,
+ *                 8: as 2 with the same balanced face items; the default for 16-bit
+ *                    storage, with order 0 and ctas_per_sm 2
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)
  *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default); for
- *                 the row kernels (2, 4) it picks the register budget: 0/1 -> 8 CTAs of
+ *                 the row kernels (2, 4, 7, 8) it picks the register budget: 0/1 -> 8 CTAs of
  *                 64 threads per SM, 2 -> 10, 3 -> 12 (kernel 5: 2 -> 10, else 8; kernel 6:
  *                 1 -> 5, 3 -> 7, else 6); for kernel 3 it caps CTAs at 2x this
  *   use_graph     1: the iteration loop of denser_regularize runs as one CUDA graph: a

@@ -283,10 +283,10 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     c->surf_items = 0;
     c->h_counters = nullptr, c->h_energy = nullptr;
     c->launches = 0;
-    // the row sweep with asynchronous halos, 10 CTAs per SM, blocks in index order
-    // the fastest measured schedule per storage type: asynchronous halos for float32; for
-    // 16-bit storage (fewer bytes, more conversions) the row kernel with synchronous halos
-    c->sched.sweep_kernel = p.precision == DENSER_FP32 ? 4 : 2;
+    // the fastest measured schedule per storage type, both the row sweep with balanced
+    // face items, 10 CTAs per SM and blocks in index order: asynchronous halos for float32;
+    // for 16-bit storage (fewer bytes, more conversions) halos through registers
+    c->sched.sweep_kernel = p.precision == DENSER_FP32 ? 7 : 8;
     c->sched.order = 0;
     c->sched.ctas_per_sm = 2;
     c->sched.use_graph = 1;
@@ -1046,7 +1046,7 @@ int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const floa
 
 int denser_set_schedule(denser_ctx* c, const denser_schedule* sch) {
     if (!c || !sch) return DENSER_ERR_INVALID_ARG;
-    if (sch->sweep_kernel < 0 || sch->sweep_kernel > 6 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
+    if (sch->sweep_kernel < 0 || sch->sweep_kernel > 8 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
         sch->ctas_per_sm > 8 || sch->use_graph < 0 || sch->use_graph > 1)
         return set_error(c, DENSER_ERR_INVALID_ARG, "set_schedule: field out of range");
     c->sched = *sch;

@@ -18,7 +18,9 @@
 //                          ASYNC (the default) the halos are copied by cp.async straight
 //                          into shared memory while the block's own rows load;
 //   sweep_rows_tma_kernel  the row kernel with the next block's own fields brought in by
-//                          1-D bulk copies (TMA) into a double-buffered stage.
+//                          1-D bulk copies (TMA) into a double-buffered stage;
+//   sweep_rows_kernel<.., BAL>  the row kernel with the face halos split into balanced
+//                          items over all threads (asynchronous or through registers).
 // and on demand:
 //   energy       FP64 primal P(u) and dual D(p) partial sums per CTA (fixed grid, fixed
 //                order: deterministic), then one CTA sums the partials.
@@ -650,13 +652,146 @@ __device__ inline float word_half(uint32_t w, int odd) {
     return Store<T>::ld(reinterpret_cast<const T*>(&w) + odd);
 }
 
+// Balanced face staging.  Besides the x halos of its own rows, a block's stencil reads
+// 34 u_bar rows of its neighbours (8 behind each of the four y and z faces, and the two
+// edge rows the -y and -z face voxels' dual steps read), the 32 voxels at the x ends of
+// the four face rows and 48 rows of old p behind the -y and -z faces.  They are split
+// into 82 row items:
+//   0-31   u_bar face row j of face F (F = i / 8: +y, -y, +z, -z), with its end voxel
+//          and the tile row's Omega word;
+//   32-79  p row: k = i - 32, component (k % 24) / 8 of row k % 8 behind -y (k < 24)
+//          or -z (the pfy and pfz tiles read as one array of 48 rows);
+//   80-81  the edge rows (-1, 8) and (8, -1).
+// Thread t takes item t and, for t < 18, item t + 64, so each warp runs one or two kinds
+// of item with most lanes active instead of one branch per face with four or eight.
+struct FaceRow {
+    int n, row, d;     // source block, source row, tile row
+    int ne, le, odd;   // end voxel: source block, offset; odd: at x = -1 (else x = 8)
+};
+
+__device__ __forceinline__ FaceRow face_row(const int* nb, int i) {
+    const int F = i >> 3, j = i & 7;
+    FaceRow f;
+    f.n = F == 0 ? nb[1] : (F == 1 ? nb[4] : (F == 2 ? nb[2] : nb[5]));
+    f.ne = F == 0 ? nb[6] : (F == 1 ? nb[8] : (F == 2 ? nb[7] : nb[10]));
+    // +y: tile row (8, j) <- row (0, j), end voxel (-1, 8, j) <- (7, 0, j) of block (-x,+y)
+    // -y: tile row (-1, j) <- row (7, j), end voxel (8, -1, j) <- (0, 7, j) of block (+x,-y)
+    // +z: tile row (j, 8) <- row (j, 0), end voxel (-1, j, 8) <- (7, j, 0) of block (-x,+z)
+    // -z: tile row (j, -1) <- row (j, 7), end voxel (8, j, -1) <- (0, j, 7) of block (+x,-z)
+    f.row = F == 0 ? 8 * j : (F == 1 ? 7 + 8 * j : (F == 2 ? j : 56 + j));
+    f.d = F == 0 ? 19 + 10 * j : (F == 1 ? 10 + 10 * j : (F == 2 ? 91 + j : 1 + j));
+    f.odd = (F & 1) ^ 1;
+    f.le = 8 * f.row + (f.odd ? 7 : 0);
+    return f;
+}
+
+// p item k in [0, 48): source block, source row and component.
+__device__ __forceinline__ void p_row_item(const int* nb, int k, int* n, int* row, int* c) {
+    const bool zf = k >= 24;
+    const int kk = zf ? k - 24 : k, j = kk & 7;
+    *c = kk >> 3;
+    *n = zf ? nb[5] : nb[4];
+    *row = zf ? 56 + j : 7 + 8 * j;
+}
+
+// Issues the copies of the balanced face items of thread t (cp.async, zero fill), and
+// stores the Omega words of the tile rows they fill.
+template <typename T>
+__device__ __forceinline__ void issue_faces_balanced(const SweepArgs<T>& a, RowTiles& s, HaloRaw<T>& raw, int t,
+                                                     const int* nb) {
+    constexpr bool kF = sizeof(T) == 4;
+    static_assert(offsetof(RowTiles, pfz) == offsetof(RowTiles, pfy) + sizeof(float) * 192, "pfy/pfz layout");
+    auto ub_row = [&](int d) -> void* { if constexpr (kF) return s.ub[d]; else return raw.ub[d]; };
+    auto p_dst = [&](int k) -> void* {
+        if constexpr (kF) return &s.pfy[0][0][0] + 8 * k; else return &raw.pfy[0][0][0] + 8 * k;
+    };
+    if (t < 32) {
+        const FaceRow f = face_row(nb, t);
+        cp_row_z<T>(ub_row(f.d), a.ub_in, f.n, f.row);
+        void* xd;
+        if constexpr (kF) xd = f.odd ? &s.xhm[f.d] : &s.xhp[f.d]; else xd = f.odd ? &raw.xhm[f.d] : &raw.xhp[f.d];
+        cp_voxel_z<T>(xd, a.ub_in, f.ne, f.le);
+        s.om[f.d] = (unsigned short)((f.n >= 0 ? row_bits(a.bits, f.n, f.row) : 0u) |
+                                     (voxel_bit(a.bits, f.ne, f.le) << (f.odd ? 9 : 8)));
+    } else {
+        int n, row, c;
+        p_row_item(nb, t - 32, &n, &row, &c);
+        cp_row_z<T>(p_dst(t - 32), a.p_in + c * a.pstride, n, row);
+    }
+    if (t < 16) {
+        int n, row, c;
+        p_row_item(nb, t + 32, &n, &row, &c);
+        cp_row_z<T>(p_dst(t + 32), a.p_in + c * a.pstride, n, row);
+    } else if (t < 18) {
+        const int n = t == 16 ? nb[9] : nb[11], row = t == 16 ? 7 : 56, d = t == 16 ? 90 : 9;
+        cp_row_z<T>(ub_row(d), a.ub_in, n, row);
+        s.om[d] = (unsigned short)(n >= 0 ? row_bits(a.bits, n, row) : 0u);
+    }
+}
+
+// 16-bit storage: converts what issue_faces_balanced copied for thread t (after its
+// copies have landed) into the float32 tiles.
+template <typename T>
+__device__ __forceinline__ void convert_faces_balanced(RowTiles& s, const HaloRaw<T>& raw, int t, const int* nb) {
+    static_assert(offsetof(HaloRaw<T>, pfz) == offsetof(HaloRaw<T>, pfy) + sizeof(T) * 192, "pfy/pfz layout");
+    auto row = [&](float* dst, const T* src) {
+        float v[8];
+        unpack8<T>(*reinterpret_cast<const uint4*>(src), v);
+        sts_row(dst, v);
+    };
+    if (t < 32) {
+        const FaceRow f = face_row(nb, t);
+        row(s.ub[f.d], raw.ub[f.d]);
+        if (f.odd) s.xhm[f.d] = word_half<T>(raw.xhm[f.d], 1);
+        else s.xhp[f.d] = word_half<T>(raw.xhp[f.d], 0);
+    } else {
+        row(&s.pfy[0][0][0] + 8 * (t - 32), &raw.pfy[0][0][0] + 8 * (t - 32));
+    }
+    if (t < 16) row(&s.pfy[0][0][0] + 8 * (t + 32), &raw.pfy[0][0][0] + 8 * (t + 32));
+    else if (t < 18) row(s.ub[t == 16 ? 90 : 9], raw.ub[t == 16 ? 90 : 9]);
+}
+
+// The same items loaded synchronously (through registers) into the float32 tiles.
+template <typename T>
+__device__ __forceinline__ void load_faces_balanced(const SweepArgs<T>& a, RowTiles& s, int t, const int* nb) {
+    auto p_row = [&](int k) {
+        int n, row, c;
+        p_row_item(nb, k, &n, &row, &c);
+        float q[8];
+        if (n >= 0) {
+            ld_row<T>(a.p_in + c * a.pstride + (size_t)n * kBlockVoxels + 8 * row, q);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+        }
+        sts_row(&s.pfy[0][0][0] + 8 * k, q);
+    };
+    if (t < 32) {
+        const FaceRow f = face_row(nb, t);
+        const unsigned om = load_face_row<T>(a, f.n, f.row, s.ub[f.d]);
+        unsigned bit;
+        const float v = load_voxel<T>(a, f.ne, f.le, &bit);
+        if (f.odd) s.xhm[f.d] = v;
+        else s.xhp[f.d] = v;
+        s.om[f.d] = (unsigned short)(om | (bit << (f.odd ? 9 : 8)));
+    } else {
+        p_row(t - 32);
+    }
+    if (t < 16) {
+        p_row(t + 32);
+    } else if (t < 18) {
+        const int d = t == 16 ? 90 : 9;
+        s.om[d] = (unsigned short)load_face_row<T>(a, t == 16 ? nb[9] : nb[11], t == 16 ? 7 : 56, s.ub[d]);
+    }
+}
+
 // Asynchronous halo staging of row r: the x halos, the face and edge rows and the old p
 // behind the low faces go straight from L2 into shared memory (cp.async, zeros for
 // absent neighbours), so that their latency overlaps the loads of the block's own rows.
 // Returns the Omega words of the tile rows the row fills: om[0] the x-halo bits of its
 // own row (bits 8 and 9), om[1] its y-face row, om[2] its z-face row, om[3] its edge row.
 // The x = 8 voxels sit at even offsets of their block, the x = -1 voxels at odd ones.
-template <typename T>
+template <typename T, bool BAL = false>
 __device__ __forceinline__ void issue_row_halos(const SweepArgs<T>& a, RowTiles& s, HaloRaw<T>& raw, int r, int ly,
                                                 int lz, const int* nb, unsigned* om) {
     constexpr bool kF = sizeof(T) == 4;
@@ -676,6 +811,11 @@ __device__ __forceinline__ void issue_row_halos(const SweepArgs<T>& a, RowTiles&
     }
     om[0] = (voxel_bit(a.bits, nb[0], 8 * r) << 8) | (voxel_bit(a.bits, nb[3], 8 * r + 7) << 9);
     om[1] = om[2] = om[3] = 0u;
+    if constexpr (BAL) {
+        issue_faces_balanced<T>(a, s, raw, r, nb);
+        cp_async_commit();
+        return;
+    }
     if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
         const int d = r10(8, lz);
         cp_row_z<T>(ub_row(d), ubs, nb[1], 8 * lz);
@@ -907,7 +1047,7 @@ __device__ __forceinline__ void rows_compute(const SweepArgs<T>& a, RowTiles& s,
 // One block of the row sweep: staging of the rows, faces and edges, the dual steps,
 // the primal step and the relaxation.  `stage` holds the block's own fields when they
 // were prefetched into shared memory (else they are read from global memory).
-template <typename T, bool ASYNC = false, bool PREFETCH = false>
+template <typename T, bool ASYNC = false, bool PREFETCH = false, bool BAL = false>
 __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, int b, int r, const char* stage,
                                            const int* nb, HaloRaw<T>* raw = nullptr, char* slot = nullptr,
                                            int b_next = -1) {
@@ -918,7 +1058,7 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
     // ---------------------------------------------------------- staging
     constexpr bool kAsync = ASYNC;
     unsigned hom[4] = {0u, 0u, 0u, 0u};
-    if constexpr (kAsync) issue_row_halos<T>(a, s, *raw, r, ly, lz, nb, hom);
+    if constexpr (kAsync) issue_row_halos<T, BAL>(a, s, *raw, r, ly, lz, nb, hom);
     float ub[8], p0[8], p1[8], p2[8], uo[8], fv[8], wv[8];
     unsigned om_r;
     if constexpr (PREFETCH) {  // this block's row r is in the thread's slot (copied one block ago)
@@ -963,12 +1103,14 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
         om_r |= hom[0];  // the dual and primal steps read the row's bits from this register
         sts_row(s.ub[rr], ub);
         s.om[rr] = (unsigned short)om_r;
-        if (ly == 7) s.om[r10(8, lz)] = (unsigned short)hom[1];
-        if (ly == 0) s.om[r10(-1, lz)] = (unsigned short)hom[1];
-        if (lz == 7) s.om[r10(ly, 8)] = (unsigned short)hom[2];
-        if (lz == 0) s.om[r10(ly, -1)] = (unsigned short)hom[2];
-        if (ly == 0 && lz == 7) s.om[r10(-1, 8)] = (unsigned short)hom[3];
-        if (ly == 7 && lz == 0) s.om[r10(8, -1)] = (unsigned short)hom[3];
+        if constexpr (!BAL) {  // (balanced items store their Omega words themselves)
+            if (ly == 7) s.om[r10(8, lz)] = (unsigned short)hom[1];
+            if (ly == 0) s.om[r10(-1, lz)] = (unsigned short)hom[1];
+            if (lz == 7) s.om[r10(ly, 8)] = (unsigned short)hom[2];
+            if (lz == 0) s.om[r10(ly, -1)] = (unsigned short)hom[2];
+            if (ly == 0 && lz == 7) s.om[r10(-1, 8)] = (unsigned short)hom[3];
+            if (ly == 7 && lz == 0) s.om[r10(8, -1)] = (unsigned short)hom[3];
+        }
         if constexpr (PREFETCH) {
             // the halo group is complete; the next block's rows (the newest group) may
             // still be in flight
@@ -976,7 +1118,18 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
         } else {
             cp_async_wait_all();
         }
-        if constexpr (sizeof(T) != 4) convert_row_halos<T>(s, *raw, r, ly, lz);
+        if constexpr (sizeof(T) != 4) {
+            if constexpr (BAL) {
+                const int rr0 = r10(ly, lz);
+                s.xhp[rr0] = word_half<T>(raw->xhp[rr0], 0);
+                s.xhm[rr0] = word_half<T>(raw->xhm[rr0], 1);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) s.phm[c][r] = word_half<T>(raw->phm[c][r], 1);
+                convert_faces_balanced<T>(s, *raw, r, nb);
+            } else {
+                convert_row_halos<T>(s, *raw, r, ly, lz);
+            }
+        }
     } else {
         {
             unsigned bit;
@@ -997,54 +1150,58 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
         sts_row(s.ub[rr], ub);
         s.om[rr] = (unsigned short)om_r;
         // faces and edges
-        if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
-            const int d = r10(8, lz);
-            unsigned om = load_face_row<T>(a, nb[1], 8 * lz, s.ub[d]), bit;
-            s.xhm[d] = load_voxel<T>(a, nb[6], 8 * (8 * lz) + 7, &bit);
-            s.om[d] = (unsigned short)(om | (bit << 9));
-        }
-        if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
-            const int d = r10(-1, lz);
-            const int n4 = nb[4];
-            unsigned om = load_face_row<T>(a, n4, 7 + 8 * lz, s.ub[d]), bit;
-            s.xhp[d] = load_voxel<T>(a, nb[8], 8 * (7 + 8 * lz), &bit);
-            s.om[d] = (unsigned short)(om | (bit << 8));
-            float q[8];
-    #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (n4 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n4 * kBlockVoxels + 8 * (7 + 8 * lz), q);
-                else
-    #pragma unroll
-                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
-                sts_row(s.pfy[c][lz], q);
+        if constexpr (BAL) {
+            load_faces_balanced<T>(a, s, r, nb);
+        } else {
+            if (ly == 7) {  // row (8, lz) <- block +y row (0, lz); edge (-1, 8, lz) <- block (-x,+y) voxel (7, 0, lz)
+                const int d = r10(8, lz);
+                unsigned om = load_face_row<T>(a, nb[1], 8 * lz, s.ub[d]), bit;
+                s.xhm[d] = load_voxel<T>(a, nb[6], 8 * (8 * lz) + 7, &bit);
+                s.om[d] = (unsigned short)(om | (bit << 9));
             }
-        }
-        if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
-            const int d = r10(ly, 8);
-            unsigned om = load_face_row<T>(a, nb[2], ly, s.ub[d]), bit;
-            s.xhm[d] = load_voxel<T>(a, nb[7], 8 * ly + 7, &bit);
-            s.om[d] = (unsigned short)(om | (bit << 9));
-        }
-        if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
-            const int d = r10(ly, -1);
-            const int n5 = nb[5];
-            unsigned om = load_face_row<T>(a, n5, ly + 56, s.ub[d]), bit;
-            s.xhp[d] = load_voxel<T>(a, nb[10], 8 * (ly + 56), &bit);
-            s.om[d] = (unsigned short)(om | (bit << 8));
-            float q[8];
-    #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (n5 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n5 * kBlockVoxels + 8 * (ly + 56), q);
-                else
-    #pragma unroll
-                    for (int i = 0; i < 8; ++i) q[i] = 0.0f;
-                sts_row(s.pfz[c][ly], q);
+            if (ly == 0) {  // row (-1, lz) <- block -y row (7, lz); edge (8, -1, lz) <- block (-y,+x) voxel (0, 7, lz)
+                const int d = r10(-1, lz);
+                const int n4 = nb[4];
+                unsigned om = load_face_row<T>(a, n4, 7 + 8 * lz, s.ub[d]), bit;
+                s.xhp[d] = load_voxel<T>(a, nb[8], 8 * (7 + 8 * lz), &bit);
+                s.om[d] = (unsigned short)(om | (bit << 8));
+                float q[8];
+        #pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (n4 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n4 * kBlockVoxels + 8 * (7 + 8 * lz), q);
+                    else
+        #pragma unroll
+                        for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+                    sts_row(s.pfy[c][lz], q);
+                }
             }
+            if (lz == 7) {  // row (ly, 8) <- block +z row (ly, 0); edge (-1, ly, 8) <- block (-x,+z) voxel (7, ly, 0)
+                const int d = r10(ly, 8);
+                unsigned om = load_face_row<T>(a, nb[2], ly, s.ub[d]), bit;
+                s.xhm[d] = load_voxel<T>(a, nb[7], 8 * ly + 7, &bit);
+                s.om[d] = (unsigned short)(om | (bit << 9));
+            }
+            if (lz == 0) {  // row (ly, -1) <- block -z row (ly, 7); edge (8, ly, -1) <- block (-z,+x) voxel (0, ly, 7)
+                const int d = r10(ly, -1);
+                const int n5 = nb[5];
+                unsigned om = load_face_row<T>(a, n5, ly + 56, s.ub[d]), bit;
+                s.xhp[d] = load_voxel<T>(a, nb[10], 8 * (ly + 56), &bit);
+                s.om[d] = (unsigned short)(om | (bit << 8));
+                float q[8];
+        #pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (n5 >= 0) ld_row<T>(a.p_in + c * ps + (size_t)n5 * kBlockVoxels + 8 * (ly + 56), q);
+                    else
+        #pragma unroll
+                        for (int i = 0; i < 8; ++i) q[i] = 0.0f;
+                    sts_row(s.pfz[c][ly], q);
+                }
+            }
+            if (ly == 0 && lz == 7)  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
+                s.om[r10(-1, 8)] = (unsigned short)load_face_row<T>(a, nb[9], 7, s.ub[r10(-1, 8)]);
+            if (ly == 7 && lz == 0)  // edge row (8, -1) <- block (-z,+y) row (0, 7)
+                s.om[r10(8, -1)] = (unsigned short)load_face_row<T>(a, nb[11], 56, s.ub[r10(8, -1)]);
         }
-        if (ly == 0 && lz == 7)  // edge row (-1, 8) <- block (-y,+z) row (7, 0)
-            s.om[r10(-1, 8)] = (unsigned short)load_face_row<T>(a, nb[9], 7, s.ub[r10(-1, 8)]);
-        if (ly == 7 && lz == 0)  // edge row (8, -1) <- block (-z,+y) row (0, 7)
-            s.om[r10(8, -1)] = (unsigned short)load_face_row<T>(a, nb[11], 56, s.ub[r10(8, -1)]);
     }
     __syncthreads();
     if constexpr (kAsync) hm0 = s.phm[0][r], hm1 = s.phm[1][r], hm2 = s.phm[2][r];
@@ -1059,7 +1216,7 @@ __device__ inline void load_nbr_row(const int32_t* __restrict__ nbr, int b, int*
     out[6] = y.z, out[7] = y.w, out[8] = z.x, out[9] = z.y, out[10] = z.z, out[11] = z.w;
 }
 
-template <typename T, int MINB, bool ASYNC = false>
+template <typename T, int MINB, bool ASYNC = false, bool BAL = false>
 __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs<T> a) {
     __shared__ RowTiles s;
     __shared__ HaloRaw<T> raw;
@@ -1078,7 +1235,7 @@ __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_kernel(SweepArgs
             b_next = a.order ? __ldg(a.order + kn) : kn;
             load_nbr_row(a.nbr, b_next, nb_next);
         }
-        rows_block<T, ASYNC>(a, s, b, threadIdx.x, nullptr, nb, &raw);
+        rows_block<T, ASYNC, false, BAL>(a, s, b, threadIdx.x, nullptr, nb, &raw);
         __syncthreads();  // the tiles are rewritten for the next block
         b = b_next;
 #pragma unroll
@@ -1445,6 +1602,16 @@ __global__ void convert_kernel(const void* src, void* dst, long long n, int to_f
     }
 }
 
+// Launches a row sweep with registers for MINB resident CTAs per SM, as many CTAs as are
+// resident at once (at most one per block).
+template <typename T, int MINB, bool ASYNC, bool BAL>
+void launch_rows(const SweepArgs<T>& a, int64_t nb, int sm_count, cudaStream_t s) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_kernel<T, MINB, ASYNC, BAL>, kRowThreads, 0);
+    const int grid = (int)std::min<int64_t>(nb, (int64_t)sm_count * std::max(per_sm, 1));
+    sweep_rows_kernel<T, MINB, ASYNC, BAL><<<grid, kRowThreads, 0, s>>>(a);
+}
+
 template <typename T>
 void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
     SweepArgs<T> a;
@@ -1536,6 +1703,19 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_prefetch_kernel<T, 8>, kRowThreads, 0);
             sweep_rows_prefetch_kernel<T, 8>
                 <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
+        }
+    } else if (c->sched.sweep_kernel == 7 || c->sched.sweep_kernel == 8) {
+        // row sweep with the face halos staged as balanced items: 7 asynchronously, 8
+        // through registers (ctas_per_sm 2: registers for 10 resident CTAs, 3: 12, else 8)
+        const int cps = c->sched.ctas_per_sm;
+        if (c->sched.sweep_kernel == 7) {
+            if (cps == 3) launch_rows<T, 12, true, true>(a, nb, c->sm_count, s);
+            else if (cps == 2) launch_rows<T, 10, true, true>(a, nb, c->sm_count, s);
+            else launch_rows<T, 8, true, true>(a, nb, c->sm_count, s);
+        } else {
+            if (cps == 3) launch_rows<T, 12, false, true>(a, nb, c->sm_count, s);
+            else if (cps == 2) launch_rows<T, 10, false, true>(a, nb, c->sm_count, s);
+            else launch_rows<T, 8, false, true>(a, nb, c->sm_count, s);
         }
     } else if (c->sched.sweep_kernel == 3) {
         int per_sm = 0;
