@@ -564,7 +564,7 @@ def main():
     kernel_name = ["sweep_kernel", "sweep_pipe_kernel", "sweep_rows_kernel", "sweep_rows_tma_kernel",
                    "sweep_rows_kernel", "sweep_rows_prefetch_kernel",
                    "sweep_rows_pipelined_kernel", "sweep_rows_kernel",
-                   "sweep_rows_kernel"][N.denser_get_schedule(ctx)["sweep_kernel"]]
+                   "sweep_rows_kernel", "sweep_rows_pipelined_kernel"][N.denser_get_schedule(ctx)["sweep_kernel"]]
 
     if rank != 0:
         if world > 1:

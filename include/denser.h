@@ -126,13 +126,14 @@ typedef struct {
  *                    for the rest) instead of one branch per face; the default for FP32
  *                    storage, with order 0 and ctas_per_sm 2,
  *                 8: as 2 with the same balanced face items; the default for 16-bit
- *                    storage, with order 0 and ctas_per_sm 2
+ *                    storage, with order 0 and ctas_per_sm 2,
+ *                 9: as 6 with the balanced face items
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)
  *   ctas_per_sm   resident CTAs per SM for the persistent grid (0: kernel default); for
  *                 the row kernels (2, 4, 7, 8) it picks the register budget: 0/1 -> 8 CTAs of
- *                 64 threads per SM, 2 -> 10, 3 -> 12 (kernel 5: 2 -> 10, else 8; kernel 6:
- *                 1 -> 5, 3 -> 7, else 6); for kernel 3 it caps CTAs at 2x this
+ *                 64 threads per SM, 2 -> 10, 3 -> 12 (kernel 5: 2 -> 10, else 8; kernels 6
+ *                 and 9: 1 -> 5, 3 -> 7, else 6); for kernel 3 it caps CTAs at 2x this
  *   use_graph     1: the iteration loop of denser_regularize runs as one CUDA graph: a
  *                 WHILE conditional node whose body is gap_every sweeps (10 when no gap
  *                 test is asked for) plus the FP64 gap evaluation, and whose condition is

@@ -28,6 +28,7 @@ DEFAULT_CANDIDATES = (
     (5, 0, 0, 1), (5, 1, 0, 1), (5, 0, 2, 1),
     (6, 0, 0, 1), (6, 1, 0, 1), (6, 0, 1, 1), (6, 0, 3, 1),
     (7, 0, 2, 1), (7, 0, 0, 1), (7, 0, 3, 1), (8, 0, 2, 1), (8, 0, 0, 1),
+    (9, 0, 0, 1), (9, 0, 1, 1), (9, 0, 3, 1),
 )
 
 _cache: dict = {}

@@ -202,7 +202,8 @@ __device__ bool band_keys_by_events(const AllocArgs& a, const AllocFrame& fr, in
         const float slope = a.hf * D[r];
         for (int v = klo[r] + step; v != khi[r] + step; v += step) {
             // increasing: the first n with q >= v; decreasing: the first n with q < v + 1
-            const float est = ((step > 0 ? (float)v : (float)(v + 1)) - q0) / slope;
+            // (an estimate only, confirmed below, so the fast approximate division serves)
+            const float est = __fdividef((step > 0 ? (float)v : (float)(v + 1)) - q0, slope);
             int nc = step > 0 ? (int)ceilf(fminf(fmaxf(est, -1.0e6f), 1.0e6f))
                                : (int)floorf(fminf(fmaxf(est, -1.0e6f), 1.0e6f)) + 1;
             nc = min(max(nc, -N + 1), N);

@@ -1046,7 +1046,7 @@ int denser_net_apply(denser_ctx* c, const int32_t* blocks, int64_t n, const floa
 
 int denser_set_schedule(denser_ctx* c, const denser_schedule* sch) {
     if (!c || !sch) return DENSER_ERR_INVALID_ARG;
-    if (sch->sweep_kernel < 0 || sch->sweep_kernel > 8 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
+    if (sch->sweep_kernel < 0 || sch->sweep_kernel > 9 || sch->order < 0 || sch->order > 1 || sch->ctas_per_sm < 0 ||
         sch->ctas_per_sm > 8 || sch->use_graph < 0 || sch->use_graph > 1)
         return set_error(c, DENSER_ERR_INVALID_ARG, "set_schedule: field out of range");
     c->sched = *sch;

@@ -62,6 +62,14 @@ __host__ __device__ inline uint32_t hash_key(unsigned long long k) {
            ((uint32_t)s * 2654435761u);
 }
 
+// The hardware's approximate reciprocal: at most 1 ulp from 1/x for normal x (denormal
+// inputs and results are flushed to zero, which no caller produces).
+__device__ inline float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;\n" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // --------------------------------------------------------- device-side words
 enum Counter {
     kNumBlocks = 0,    // allocated blocks

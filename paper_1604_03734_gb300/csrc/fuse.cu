@@ -271,14 +271,16 @@ __global__ void __launch_bounds__(128, 8) fuse_kernel(const float* __restrict__ 
                 if (z + dz <= 0.0f) {
                     decided = 1;  // certainly behind the camera
                 } else if (z - dz > 0.0f) {
-                    const float inv = __frcp_rn(z);
+                    const float inv = rcp_approx(z);  // z > dz > 2^-20 s: a normal number
                     const float rx = x * inv, ry = y * inv;
                     const float px = fmaf(a.fxf, rx, a.cxf);
                     const float py = fmaf(a.fyf, ry, a.cyf);
                     // |x/z - rx| <= (dx + |rx| dz) / (z - dz) from the coordinates, plus the
-                    // roundings of 1/z, x * (1/z), the fma and of fx, cx (below 2^-24 (|px| + |cx| +
-                    // 3 fx |rx|)); 2^-22 (fx |rx| + |px| + |cx|) covers those with margin.
-                    const float iz = __frcp_rn(z - dz);
+                    // error of the approximate 1/z (1 ulp) and the roundings of x * (1/z), the fma
+                    // and of fx, cx: below 2^-24 (|px| + |cx| + 4 fx |rx|), which
+                    // 2^-22 (fx |rx| + |px| + |cx|) covers.  The approximate 1/(z - dz) is within
+                    // 1 ulp, which the factor 1.01 covers.
+                    const float iz = rcp_approx(z - dz);
                     const float ex = a.fxf * (dx + fabsf(rx) * dz) * iz * 1.01f + eps22 * (a.fxf * fabsf(rx) + fabsf(px) + fabsf(a.cxf)) + 1e-6f;
                     const float ey = a.fyf * (dy + fabsf(ry) * dz) * iz * 1.01f + eps22 * (a.fyf * fabsf(ry) + fabsf(py) + fabsf(a.cyf)) + 1e-6f;
                     int pxi, pyi;

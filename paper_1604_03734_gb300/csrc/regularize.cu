@@ -164,14 +164,8 @@ __device__ inline float div_terms(bool ex, float px, bool exm, float pxm, bool e
     return __fadd_rn(__fadd_rn(d0, d1), d2);
 }
 
-// The hardware's approximate reciprocal (at most 1 ulp from 1/x); x >= 1 here.
-__device__ inline float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;\n" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Primal proximal step on Omega and the relaxation.
+// Primal proximal step on Omega and the relaxation (1 + tau lambda w >= 1: no denormal
+// reaches the approximate reciprocal).
 __device__ inline void primal_update(bool o, float uo, float dv, float fv, float wv, float tau, float tau_lam,
                                      float theta, float* un, float* ubn) {
     float u = uo;
@@ -751,6 +745,19 @@ __device__ __forceinline__ void convert_faces_balanced(RowTiles& s, const HaloRa
     else if (t < 18) row(s.ub[t == 16 ? 90 : 9], raw.ub[t == 16 ? 90 : 9]);
 }
 
+// 16-bit storage with balanced face items: converts the x halos of row r and thread r's
+// face items (after their copies have landed) into the float32 tiles.
+template <typename T>
+__device__ __forceinline__ void convert_halos_balanced(RowTiles& s, const HaloRaw<T>& raw, int r, int ly, int lz,
+                                                       const int* nb) {
+    const int rr = r10(ly, lz);
+    s.xhp[rr] = word_half<T>(raw.xhp[rr], 0);
+    s.xhm[rr] = word_half<T>(raw.xhm[rr], 1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s.phm[c][r] = word_half<T>(raw.phm[c][r], 1);
+    convert_faces_balanced<T>(s, raw, r, nb);
+}
+
 // The same items loaded synchronously (through registers) into the float32 tiles.
 template <typename T>
 __device__ __forceinline__ void load_faces_balanced(const SweepArgs<T>& a, RowTiles& s, int t, const int* nb) {
@@ -1119,16 +1126,8 @@ __device__ __forceinline__ void rows_block(const SweepArgs<T>& a, RowTiles& s, i
             cp_async_wait_all();
         }
         if constexpr (sizeof(T) != 4) {
-            if constexpr (BAL) {
-                const int rr0 = r10(ly, lz);
-                s.xhp[rr0] = word_half<T>(raw->xhp[rr0], 0);
-                s.xhm[rr0] = word_half<T>(raw->xhm[rr0], 1);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) s.phm[c][r] = word_half<T>(raw->phm[c][r], 1);
-                convert_faces_balanced<T>(s, *raw, r, nb);
-            } else {
-                convert_row_halos<T>(s, *raw, r, ly, lz);
-            }
+            if constexpr (BAL) convert_halos_balanced<T>(s, *raw, r, ly, lz, nb);
+            else convert_row_halos<T>(s, *raw, r, ly, lz);
         }
     } else {
         {
@@ -1330,7 +1329,7 @@ __device__ __forceinline__ void unpack_f4(const float4* q, float* v) {
 // data is therefore requested one whole block ahead, and a CTA's critical path is its
 // arithmetic rather than its memory round trips.  Same arithmetic as every other
 // variant (bit-identical iterates).
-template <typename T, int MINB>
+template <typename T, int MINB, bool BAL = false>
 __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_pipelined_kernel(SweepArgs<T> a) {
     __shared__ RowTiles tiles[2];
     __shared__ HaloRaw<T> raws[2];
@@ -1343,7 +1342,7 @@ __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_pipelined_kernel
     load_nbr_row(a.nbr, b, nb);
     OwnRows<T> own, own_next;
     unsigned hom[4], hom_next[4];
-    issue_row_halos<T>(a, tiles[0], raws[0], r, ly, lz, nb, hom);
+    issue_row_halos<T, BAL>(a, tiles[0], raws[0], r, ly, lz, nb, hom);
     load_own_rows<T>(a, b, r, own);
     for (int i = 0; k < a.n_blocks; k += G, ++i) {
         RowTiles& S = tiles[i & 1];
@@ -1365,21 +1364,26 @@ __global__ void __launch_bounds__(kRowThreads, MINB) sweep_rows_pipelined_kernel
         // the next block goes in flight: its halos into the other tile set (free since the
         // barrier that ended the previous block), its own row into registers
         if (b_next >= 0) {
-            issue_row_halos<T>(a, tiles[(i & 1) ^ 1], raws[(i & 1) ^ 1], r, ly, lz, nb_next, hom_next);
+            issue_row_halos<T, BAL>(a, tiles[(i & 1) ^ 1], raws[(i & 1) ^ 1], r, ly, lz, nb_next, hom_next);
             load_own_rows<T>(a, b_next, r, own_next);
         } else {
             cp_async_commit();  // an empty group: the wait below then always leaves the newest group
         }
         sts_row(S.ub[rr], ub);
         S.om[rr] = (unsigned short)om_r;
-        if (ly == 7) S.om[r10(8, lz)] = (unsigned short)hom[1];
-        if (ly == 0) S.om[r10(-1, lz)] = (unsigned short)hom[1];
-        if (lz == 7) S.om[r10(ly, 8)] = (unsigned short)hom[2];
-        if (lz == 0) S.om[r10(ly, -1)] = (unsigned short)hom[2];
-        if (ly == 0 && lz == 7) S.om[r10(-1, 8)] = (unsigned short)hom[3];
-        if (ly == 7 && lz == 0) S.om[r10(8, -1)] = (unsigned short)hom[3];
+        if constexpr (!BAL) {  // (balanced items stored their Omega words when issued)
+            if (ly == 7) S.om[r10(8, lz)] = (unsigned short)hom[1];
+            if (ly == 0) S.om[r10(-1, lz)] = (unsigned short)hom[1];
+            if (lz == 7) S.om[r10(ly, 8)] = (unsigned short)hom[2];
+            if (lz == 0) S.om[r10(ly, -1)] = (unsigned short)hom[2];
+            if (ly == 0 && lz == 7) S.om[r10(-1, 8)] = (unsigned short)hom[3];
+            if (ly == 7 && lz == 0) S.om[r10(8, -1)] = (unsigned short)hom[3];
+        }
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this block's halos have landed
-        if constexpr (sizeof(T) != 4) convert_row_halos<T>(S, raws[i & 1], r, ly, lz);
+        if constexpr (sizeof(T) != 4) {
+            if constexpr (BAL) convert_halos_balanced<T>(S, raws[i & 1], r, ly, lz, nb);
+            else convert_row_halos<T>(S, raws[i & 1], r, ly, lz);
+        }
         __syncthreads();
         const float hm0 = S.phm[0][r], hm1 = S.phm[1][r], hm2 = S.phm[2][r];
         rows_compute<T>(a, S, r, om_r, ub, p0, p1, p2, uo, fv, wv, hm0, hm1, hm2, (size_t)b * kBlockVoxels + 8 * r);
@@ -1702,6 +1706,22 @@ void sweep_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
         } else {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_prefetch_kernel<T, 8>, kRowThreads, 0);
             sweep_rows_prefetch_kernel<T, 8>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
+        }
+    } else if (c->sched.sweep_kernel == 9) {
+        // the software-pipelined row sweep with balanced face items (ctas_per_sm as for 6)
+        int per_sm = 0;
+        if (c->sched.ctas_per_sm == 1) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_pipelined_kernel<T, 5, true>, kRowThreads, 0);
+            sweep_rows_pipelined_kernel<T, 5, true>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
+        } else if (c->sched.ctas_per_sm == 3) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_pipelined_kernel<T, 7, true>, kRowThreads, 0);
+            sweep_rows_pipelined_kernel<T, 7, true>
+                <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_rows_pipelined_kernel<T, 6, true>, kRowThreads, 0);
+            sweep_rows_pipelined_kernel<T, 6, true>
                 <<<(int)std::min<int64_t>(nb, (int64_t)c->sm_count * std::max(per_sm, 1)), kRowThreads, 0, s>>>(a);
         }
     } else if (c->sched.sweep_kernel == 7 || c->sched.sweep_kernel == 8) {

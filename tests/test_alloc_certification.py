@@ -106,6 +106,9 @@ def events_path(S, dv, D, e, ez):
         slope = F32(S.hf * D[r])
         for v in range(klo[r] + step, khi[r] + step, step):
             est = F32(F32(F32(v if step > 0 else v + 1) - q0) / slope)
+            # the kernel divides approximately (within 2 ulps): est moved by S.est_ulps
+            for _ in range(abs(S.est_ulps)):
+                est = np.nextafter(est, F32(np.inf) if S.est_ulps > 0 else F32(-np.inf))
             est = min(max(est, F32(-1e6)), F32(1e6))
             nc = int(math.ceil(est)) if step > 0 else int(math.floor(est)) + 1
             nc = min(max(nc, -N + 1), N)
@@ -166,8 +169,9 @@ def oracle_ray_keys(K, T, prm, x, y, dv):
     return {k[1:] for k in O.frame_block_keys(depth, K, T, prm)}
 
 
-def check_rays(K, T, prm, pixels, depths, min_decided):
+def check_rays(K, T, prm, pixels, depths, min_decided, est_ulps=0):
     S = Setup(K, T, prm)
+    S.est_ulps = est_ulps
     decided = 0
     for (x, y), dv in zip(pixels, depths):
         got = ray_keys(S, x, y, F32(dv))
@@ -178,8 +182,9 @@ def check_rays(K, T, prm, pixels, depths, min_decided):
     assert decided >= min_decided * len(pixels), decided
 
 
+@pytest.mark.parametrize("est_ulps", [-2, 0, 2])
 @pytest.mark.parametrize("seed,far", [(0, 3.0), (1, 400.0), (2, 3000.0)])
-def test_certified_rays_match_the_oracle(seed, far):
+def test_certified_rays_match_the_oracle(seed, far, est_ulps):
     rng = np.random.default_rng(seed)
     prm = O.Params()
     K = O.Intrinsics(float(rng.uniform(150, 800)), float(rng.uniform(150, 800)), float(rng.uniform(100, 140)),
@@ -188,10 +193,11 @@ def test_certified_rays_match_the_oracle(seed, far):
     n = 1500
     pixels = list(zip(rng.integers(0, K.width, n).tolist(), rng.integers(0, K.height, n).tolist()))
     depths = rng.uniform(0.2, 45.0, n).astype(F32)
-    check_rays(K, T, prm, pixels, depths, 0.99)
+    check_rays(K, T, prm, pixels, depths, 0.99, est_ulps)
 
 
-def test_samples_on_block_faces():
+@pytest.mark.parametrize("est_ulps", [-2, 0, 2])
+def test_samples_on_block_faces(est_ulps):
     """Identity pose, principal point on a pixel centre: the central pixel's ray runs
     along +z and, for depths on a multiple of the sample spacing, its samples land on
     block faces; neighbouring pixels graze them."""
@@ -203,4 +209,4 @@ def test_samples_on_block_faces():
         for dx, dy in ((0, 0), (1, 0), (0, 1), (-1, -1), (2, -3)):
             pixels.append((60 + dx, 30 + dy))
             depths.append(F32(k * 0.05))
-    check_rays(K, T, prm, pixels, np.array(depths, F32), 0.05)
+    check_rays(K, T, prm, pixels, np.array(depths, F32), 0.05, est_ulps)

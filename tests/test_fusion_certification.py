@@ -37,19 +37,30 @@ def fma32(a, b, c):
     return np.where(at_mid, np.where(err > 0, hi, lo), r).astype(F32)
 
 
-def rcp32(z):
-    """Correctly rounded float32 reciprocal (float64 quotient rounded to float32; a tie
-    would need 1/z within 2^-53 of a float32 midpoint, which a float32 z cannot give)."""
-    return (1.0 / np.asarray(z, np.float64)).astype(F32)
+def rcp32(z, ulps=0):
+    """float32 reciprocal: the correctly rounded value (float64 quotient rounded to float32;
+    a tie would need 1/z within 2^-53 of a float32 midpoint, which a float32 z cannot
+    give) moved by `ulps` units in the last place.  The kernel uses the hardware's
+    approximate reciprocal, within 1 ulp of 1/z: one of the values at -1, 0, +1."""
+    r = (1.0 / np.asarray(z, np.float64)).astype(F32)
+    for _ in range(abs(ulps)):
+        r = np.nextafter(r, F32(np.inf) if ulps > 0 else F32(-np.inf))
+    return r.astype(F32)
+
+
+# the approximate reciprocal's possible values: 1/z at -1, 0 or +1 ulp, and 1/(z - dz)
+# one ulp low (the smaller bound; a larger one only defers more voxels)
+RCP_CASES = [(-1, -1), (0, -1), (1, -1)]
 
 
 def floor32(v):
     return np.floor(np.asarray(v, F32)).astype(np.int64)
 
 
-def kernel_decisions(keys, depth, K, T, prm):
+def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0)):
     """The float32 path of the fusion kernel for every voxel of `keys`: (decided, update,
-    u_tsdf) per voxel, each [nb, 512]."""
+    u_tsdf) per voxel, each [nb, 512].  rcp: the ulp offsets of the two reciprocals
+    (1/z, 1/(z - dz)) from their correctly rounded values."""
     s = prm.voxel_size
     Ri, ti = O.pose_inverse(T)
     keys = np.asarray(keys, np.int64)
@@ -82,10 +93,10 @@ def kernel_decisions(keys, depth, K, T, prm):
     decided |= behind
     front = (z - dz) > 0
     with np.errstate(all="ignore"):
-        inv = rcp32(z)
+        inv = rcp32(z, rcp[0])
         rx, ry = (x * inv).astype(F32), (y * inv).astype(F32)
         px, py = fma32(fxf, rx, cxf), fma32(fyf, ry, cyf)
-        iz = rcp32((z - dz).astype(F32))
+        iz = rcp32((z - dz).astype(F32), rcp[1])
         ex = (fxf * (dx + np.abs(rx) * dz) * iz * F32(1.01) + EPS22 * (fxf * np.abs(rx) + np.abs(px) + np.abs(cxf))
               + F32(1e-6)).astype(F32)
         ey = (fyf * (dy + np.abs(ry) * dz) * iz * F32(1.01) + EPS22 * (fyf * np.abs(ry) + np.abs(py) + np.abs(cyf))
@@ -121,8 +132,9 @@ def random_pose(rng, far):
     return T
 
 
+@pytest.mark.parametrize("rcp", RCP_CASES)
 @pytest.mark.parametrize("seed,far", [(0, 5.0), (1, 300.0), (2, 2000.0)])
-def test_certified_decisions_are_the_oracles(seed, far):
+def test_certified_decisions_are_the_oracles(seed, far, rcp):
     rng = np.random.default_rng(seed)
     prm = O.Params()
     W, H = 173, 61
@@ -142,7 +154,7 @@ def test_certified_decisions_are_the_oracles(seed, far):
     keys = sorted({(0,) + tuple(int(b) for b in np.floor(pg[:, i] / (8 * prm.voxel_size))) for i in range(n)})
     g = grid_from_blocks(keys)
     want = O.fuse_depth(g, depth, K, T)
-    decided, upd, ut = kernel_decisions(keys, depth, K, T, prm)
+    decided, upd, ut = kernel_decisions(keys, depth, K, T, prm, rcp)
     assert decided.mean() > 0.97, decided.mean()
     np.testing.assert_array_equal(upd[decided], want[decided])
     both = decided & upd
@@ -169,20 +181,22 @@ def _lattice_case():
     return prm, K, keys, g, zc, px, py
 
 
-def test_pixel_edges_are_deferred_or_right():
+@pytest.mark.parametrize("rcp", RCP_CASES)
+def test_pixel_edges_are_deferred_or_right(rcp):
     """Projections on pixel edges, against a checkerboard of valid and invalid pixels:
     a pixel off by one in either direction flips the update."""
     prm, K, keys, g, zc, px, py = _lattice_case()
     yy, xx = np.mgrid[0:K.height, 0:K.width]
     depth = np.where((xx + yy) % 2 == 0, F32(20.0), F32(0.0)).astype(F32)
     want = O.fuse_depth(g, depth, K, np.eye(4))
-    decided, upd, ut = kernel_decisions(keys, depth, K, np.eye(4), prm)
+    decided, upd, ut = kernel_decisions(keys, depth, K, np.eye(4), prm, rcp)
     assert 0.5 < decided.mean() < 1.0  # the edge cases are deferred to float64
     assert want.sum() > 2000
     np.testing.assert_array_equal(upd[decided], want[decided])
 
 
-def test_truncation_edges_are_deferred_or_right():
+@pytest.mark.parametrize("rcp", RCP_CASES)
+def test_truncation_edges_are_deferred_or_right(rcp):
     """Depths set to z - mu within a few float32 ulps put u_SDF on the truncation edge of
     Eq. 1 (one voxel per pixel)."""
     rng = np.random.default_rng(7)
@@ -195,7 +209,7 @@ def test_truncation_edges_are_deferred_or_right():
         b, v = divmod(int(f), 512)
         depth[py[b, v], px[b, v]] = F32(zc[b, v] - prm.mu) + F32(rng.integers(-3, 4)) * F32(2.0 ** -22)
     want = O.fuse_depth(g, depth, K, np.eye(4))
-    decided, upd, ut = kernel_decisions(keys, depth, K, np.eye(4), prm)
+    decided, upd, ut = kernel_decisions(keys, depth, K, np.eye(4), prm, rcp)
     assert 0.5 < decided.mean() < 1.0
     np.testing.assert_array_equal(upd[decided], want[decided])
     both = decided & upd

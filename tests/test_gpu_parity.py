@@ -291,7 +291,7 @@ def test_error_paths():
                                    (2, 1, 0, 0), (2, 1, 2, 1), (2, 1, 3, 1), (3, 1, 0, 1), (3, 0, 1, 0),
                                    (4, 1, 0, 1), (4, 0, 2, 0), (5, 0, 0, 1), (5, 1, 2, 0),
                                    (6, 0, 0, 1), (6, 1, 1, 0), (6, 0, 3, 1), (7, 0, 2, 1), (7, 1, 0, 0),
-                                   (7, 0, 3, 1), (8, 0, 2, 1), (8, 1, 0, 0)])
+                                   (7, 0, 3, 1), (8, 0, 2, 1), (8, 1, 0, 0), (9, 0, 0, 1), (9, 1, 3, 0)])
 def test_schedules_give_identical_iterates(tiny, sched):
     """Every sweep schedule (kernel variant, visiting order, CTAs per SM) computes the
     same Jacobi iterates bit for bit, and matches the oracle."""
@@ -319,7 +319,7 @@ def test_schedules_give_identical_iterates(tiny, sched):
 def test_schedule_rejects_bad_fields():
     with N.DenserMap() as m:
         with pytest.raises(N.DenserError):
-            N.denser_set_schedule(m.ctx, 9, 0, 0)
+            N.denser_set_schedule(m.ctx, 10, 0, 0)
         with pytest.raises(N.DenserError):
             N.denser_set_schedule(m.ctx, 1, 0, 9)
         with pytest.raises(N.DenserError):

@@ -157,7 +157,7 @@ def test_reduced_precision_schedules_identical(tiny, precision):
     K = N.intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
     outs = {}
     for sched in ((0, 1, 0, 0), (2, 1, 0, 0), (4, 0, 2, 1), (4, 1, 0, 0), (3, 1, 0, 1), (5, 0, 0, 1), (5, 1, 2, 0), (6, 0, 0, 1), (6, 1, 3, 0),
-                  (7, 0, 2, 1), (7, 1, 0, 0), (8, 0, 2, 1), (8, 1, 0, 0)):
+                  (7, 0, 2, 1), (7, 1, 0, 0), (8, 0, 2, 1), (8, 1, 0, 0), (9, 0, 0, 1), (9, 1, 1, 0)):
         with N.DenserMap(precision=precision) as m:
             for k in range(len(d)):
                 N.denser_integrate(m.ctx, torch.from_numpy(np.ascontiguousarray(d[k])).cuda(), K, s.poses[k], 0)
