@@ -301,8 +301,10 @@ def time_steps(pipeline, steps, warmup, stream):
 
 def precision_street(args, dev, stream, N, hbm, K, workers):
     """The 1 km street (2000 depth maps, the same generator) fused and regularised (200
-    iterations) with u, u_bar and p stored in FP32, FP16 and BF16."""
+    iterations) with u, u_bar and p stored in FP32, FP16 and BF16, each with the sweep
+    schedule the autotuner picks on that map and storage type."""
     import torch
+    from paper_1604_03734_gb300 import autotune as AT
     from synth.scenes import street_scene
     length = 1000.0
     sc = street_scene(seed=0, length=length)
@@ -325,6 +327,7 @@ def precision_street(args, dev, stream, N, hbm, K, workers):
         pipeline()
         nb = N.denser_num_blocks(m.ctx, stream)
         u_out = torch.empty((nb, 512), dtype=torch.float32, device=dev)
+        tune = AT.autotune(m.ctx, prec, iters=10, use_cache=False, stream=stream)
         ms, sweep_ms, launches = time_steps(pipeline, 3, 1, stream)
         bpv = BYTES_PER_VOXEL_ITER[prec]
         nvox = nb * 512
@@ -333,7 +336,9 @@ def precision_street(args, dev, stream, N, hbm, K, workers):
         rows[name] = {"ms_per_step": ms, "voxel_updates_per_s": nvox * args.iters / (ms / 1e3),
                       "sweep_ms": sweep_avg, "sweep_voxel_updates_per_s": nvox / (sweep_avg / 1e3),
                       "bytes_per_voxel": bpv, "sweep_gbs": gbs, "frac_of_measured_hbm": gbs / hbm,
-                      "schedule": N.denser_get_schedule(m.ctx)}
+                      "schedule": N.denser_get_schedule(m.ctx),
+                      "autotune": {"schedule": tune["schedule"], "ms_per_iter": tune["ms_per_iter"],
+                                   "candidates": len(tune["table"])}}
         m.close()
     del depths
     torch.cuda.empty_cache()
@@ -540,11 +545,12 @@ def main():
     updates_all = sum_over_ranks(updates, world, dev)  # each rank's street has its own block count
     value = updates_all / (step_ms / 1e3)
 
-    # end to end: host depth maps (pinned) in, host results out, through the C ABI; one
-    # untimed pass first (the library's host staging buffers are allocated on first use)
+    # end to end: host depth maps (pinned) in, host results out, through the C ABI, over
+    # the same K steps as the device-resident measurement; one untimed pass first (the
+    # library's host staging buffers are allocated on first use)
     pipeline(depths_host, out_host)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, args.steps)
     t0 = time.perf_counter()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)

@@ -174,12 +174,15 @@ __device__ __forceinline__ void push_key(const DeviceMap& m, RayKeys& rk, unsign
 // The distinct block keys of a ray's band without visiting every sample.  The real
 // coordinate q is linear in the sample index n, so each axis's floors are monotone along
 // the band: the floors at both ends, and for each axis that changes the first sample of
-// each new floor (estimated from the line, then confirmed by certified floors on both
-// sides), give every key in sample order.  Returns false, having pushed nothing, when a
-// floor is not certified, the nearest sample is not certainly in front of the camera, or
-// an axis changes more than twice; the per-sample path then takes the ray.
+// each new floor (estimated from the line, then confirmed by certified comparisons of q
+// with the new floor's boundary on both sides), give every key in sample order.
+// Returns false, having pushed nothing, when a decision is not certified, the nearest
+// sample is not certainly in front of the camera, or an axis changes more than twice;
+// the per-sample path then takes the ray.  Everything stays in registers: per axis the
+// samples of at most two floor changes, merged in sample order at the end.
 __device__ bool band_keys_by_events(const AllocArgs& a, const AllocFrame& fr, int frame, float dv, const float* D,
                                     const float* e, float ez, const DeviceMap& m, RayKeys& rk, bool* range_err) {
+    constexpr int kNone = INT_MAX;
     const int N = a.N;
     if (!(fmaf((float)(-N), a.hf, dv) > ez)) return false;
     bool ok = true;
@@ -190,30 +193,38 @@ __device__ bool band_keys_by_events(const AllocArgs& a, const AllocFrame& fr, in
         khi[r] = band_floor(dv, (float)N, a.hf, D[r], fr.tf[r], e[r], &ok);
     }
     if (!ok) return false;
-    int ev_n[6], ev_r[6], ev_v[6];
-    int ne = 0;
+    int n1[3], n2[3], st[3];  // per axis: the samples of its first and second floor change
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
+        n1[r] = kNone, n2[r] = kNone, st[r] = 0;
         const int span = khi[r] - klo[r];
         if (span == 0) continue;
-        if (span > 2 || span < -2) return false;
-        const int step = span > 0 ? 1 : -1;
-        const float q0 = fmaf(dv, D[r], fr.tf[r]);
         const float slope = a.hf * D[r];
-        for (int v = klo[r] + step; v != khi[r] + step; v += step) {
+        // consecutive samples move q by less than 1/2, so the floor takes every value
+        // between its ends and changes at most once between two samples
+        if (span > 2 || span < -2 || !(fabsf(slope) < 0.5f)) return false;
+        const int step = span > 0 ? 1 : -1;
+        st[r] = step;
+        const float q0 = fmaf(dv, D[r], fr.tf[r]);
+        for (int j = 1; j <= span * step; ++j) {
+            const int v = klo[r] + j * step;
             // increasing: the first n with q >= v; decreasing: the first n with q < v + 1
             // (an estimate only, confirmed below, so the fast approximate division serves)
-            const float est = __fdividef((step > 0 ? (float)v : (float)(v + 1)) - q0, slope);
+            const float T = step > 0 ? (float)v : (float)(v + 1);
+            const float est = __fdividef(T - q0, slope);
             int nc = step > 0 ? (int)ceilf(fminf(fmaxf(est, -1.0e6f), 1.0e6f))
                                : (int)floorf(fminf(fmaxf(est, -1.0e6f), 1.0e6f)) + 1;
             nc = min(max(nc, -N + 1), N);
             for (int tries = 0;; ++tries) {
-                bool ok2 = true;
-                const int fa = band_floor(dv, (float)(nc - 1), a.hf, D[r], fr.tf[r], e[r], &ok2);
-                const int fb = band_floor(dv, (float)nc, a.hf, D[r], fr.tf[r], e[r], &ok2);
+                // q at samples nc - 1 and nc (the band_floor expression) against the
+                // integer T: q - T is exact wherever it is below 1 in magnitude, and a side
+                // of T is certified when q is at least e from it
+                const float da = fmaf(fmaf((float)(nc - 1), a.hf, dv), D[r], fr.tf[r]) - T;
+                const float db = fmaf(fmaf((float)nc, a.hf, dv), D[r], fr.tf[r]) - T;
+                const bool ok2 = (da >= e[r] || da < -e[r]) && (db >= e[r] || db < -e[r]);
                 if (!ok2 || tries > 2) return false;
-                const bool at_b = step > 0 ? fb >= v : fb <= v;
-                const bool at_a = step > 0 ? fa >= v : fa <= v;
+                const bool at_b = step > 0 ? db >= 0.0f : db < 0.0f;
+                const bool at_a = step > 0 ? da >= 0.0f : da < 0.0f;
                 if (at_b && !at_a) break;
                 if (!at_b) {
                     if (nc >= N) return false;
@@ -223,25 +234,25 @@ __device__ bool band_keys_by_events(const AllocArgs& a, const AllocFrame& fr, in
                     --nc;
                 }
             }
-            ev_n[ne] = nc, ev_r[ne] = r, ev_v[ne] = v;
-            ++ne;
+            if (j == 1) n1[r] = nc;
+            else n2[r] = nc;
         }
     }
-    // events in sample order (insertion sort of at most six)
-    for (int i = 1; i < ne; ++i)
-        for (int j = i; j > 0 && ev_n[j - 1] > ev_n[j]; --j) {
-            const int tn = ev_n[j], tr = ev_r[j], tv = ev_v[j];
-            ev_n[j] = ev_n[j - 1], ev_r[j] = ev_r[j - 1], ev_v[j] = ev_v[j - 1];
-            ev_n[j - 1] = tn, ev_r[j - 1] = tr, ev_v[j - 1] = tv;
-        }
-    int k[3] = {klo[0], klo[1], klo[2]};
-    for (int i = 0;;) {
-        const int b0 = fr.Ti[0] + k[0], b1 = fr.Ti[1] + k[1], b2 = fr.Ti[2] + k[2];
+    // the keys in sample order: changes at the same sample make one key
+    int k0 = klo[0], k1 = klo[1], k2 = klo[2];
+    int c0 = 0, c1 = 0, c2 = 0;  // changes taken per axis
+    for (int it = 0;; ++it) {
+        const int b0 = fr.Ti[0] + k0, b1 = fr.Ti[1] + k1, b2 = fr.Ti[2] + k2;
         if (key_in_range(a.seg, b0, b1, b2)) push_key(m, rk, pack_key(a.seg, b0, b1, b2), frame);
         else *range_err = true;
-        if (i >= ne) break;
-        const int n = ev_n[i];
-        for (; i < ne && ev_n[i] == n; ++i) k[ev_r[i]] = ev_v[i];
+        const int x0 = c0 == 0 ? n1[0] : (c0 == 1 ? n2[0] : kNone);
+        const int x1 = c1 == 0 ? n1[1] : (c1 == 1 ? n2[1] : kNone);
+        const int x2 = c2 == 0 ? n1[2] : (c2 == 1 ? n2[2] : kNone);
+        const int n = min(x0, min(x1, x2));
+        if (n == kNone || it >= 6) break;
+        if (x0 == n) k0 += st[0], ++c0;
+        if (x1 == n) k1 += st[1], ++c1;
+        if (x2 == n) k2 += st[2], ++c2;
     }
     return true;
 }

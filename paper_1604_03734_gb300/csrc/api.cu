@@ -333,7 +333,7 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
                 {(void**)&c->d.new_keys, max_new * 8},
                 {(void**)&c->d.new_slots, max_new * 4},
                 {(void**)&c->d.visible, mb * 32},
-                {(void**)&c->d.vis_org, mb * 32},
+                {(void**)&c->d.vis_org, mb * 4 * kVisOriginFloats},
                 {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2) * 8},
                 {(void**)&c->order, mb * 4},
                 {(void**)&c->order_keys, mb * 8},

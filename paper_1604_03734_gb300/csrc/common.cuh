@@ -15,6 +15,7 @@ namespace denser {
 constexpr int kBlock = 8;
 constexpr int kBlockVoxels = 512;
 constexpr int kNeighbours = 12;
+constexpr int kVisOriginFloats = 12;      // words per (listed block, map) entry of the fusion origins
 constexpr int kMaxProbe = 512;             // linear-probe limit of the hash table
 constexpr int kSortChunk = 2048;           // keys sorted per CTA before the rank merge
 constexpr int kSweepThreads = 512;
@@ -150,8 +151,9 @@ struct DeviceMap {
     unsigned long long* new_keys;   // [max_new] inserted keys of the running call
     uint32_t* new_slots;            // [max_new]
     int32_t* visible;               // [max_blocks] fusion work list ({block, depth-map mask})
-    float* vis_org;                 // [max_blocks][org_frames][8] the listed blocks' camera-frame
-                                    // origins per depth map (float32 hi, lo, bound)
+    float* vis_org;                 // [max_blocks][org_frames][kVisOriginFloats] the listed blocks'
+                                    // camera-frame origins per depth map (float32 hi, lo, bound)
+                                    // and their voxels' shared projection bounds
     int32_t org_frames;             // depth maps per entry that vis_org holds
     double* partials;               // [kEnergyGrid][2] energy partial sums
     uint32_t max_blocks;

@@ -11,12 +11,15 @@
 //               After a batched allocation a block that the batch added takes only the
 //               maps from the first one that allocated it on, as one call per map would;
 //   origin      the float64 camera-frame origin of each listed (block, map) pair, as a
-//               float32 hi/lo pair with its bound;
+//               float32 hi/lo pair with its bound, and one bound on the projection error
+//               that every voxel of the pair can use (none for blocks that reach too
+//               close to the camera plane);
 //   fuse        one CTA per listed block, 128 threads x 4 consecutive voxels; f and w
 //               stay in registers while the block takes its maps in order, so they move
 //               once per call as float4.  Each integer decision (the pixel a voxel
 //               projects to, z_c > 0, u_SDF >= -mu) is first taken in float32 together
-//               with a forward error bound; when the bound cannot certify it, the voxel is
+//               with a forward error bound (the pair's shared projection bound, else the
+//               voxel's own); when the bound cannot certify it, the voxel is
 //               recomputed in float64 in the oracle's exact operation order.  So the set
 //               of updated voxels (and w) is bit-exact while float64, which runs at a
 //               small fraction of the float32 rate on this GPU, is used for well under
@@ -61,9 +64,11 @@ struct VisEntry {
 struct VisOrigin {
     float hi[3];
     float lo[3];
-    float delta;  // bound on |c0 - (hi + lo)| for the block
-    float pad;
+    float delta;   // bound on |c0 - (hi + lo)| for the block
+    float ex, ey;  // bounds on every voxel's projection error (pixels); ex < 0: none
+    float pad[3];
 };
+static_assert(sizeof(VisOrigin) == 4 * kVisOriginFloats, "fusion origin entry size");
 
 __global__ void __launch_bounds__(256) depth_max_kernel(const float* __restrict__ depth, int n, int32_t* out) {
     __shared__ float red[8];
@@ -98,6 +103,55 @@ __device__ inline void to_camera(const FuseFrame& fr, double gx, double gy, doub
                          fr.ti[r]);
 }
 
+// Bounds on the projection error (pixels, per image axis) shared by the 512 voxels of a
+// (block, map) pair, in float32 with every operation rounded explicitly, or -1 when the
+// block reaches too close to the camera plane to share them.  It dominates the bound the
+// fusion kernel's per-voxel path computes, so the decisions it certifies are the
+// float64 ones by the same argument; a larger bound only sends more voxels to float64.
+// Per axis r, the float32 coordinate of voxel l is (hi_r + (M_r . l)) + lo_r with
+// 0 <= l <= 7, so its magnitude is at most X_r = (|hi_r| + |lo_r| + 7 sum_j |M_rj|)
+// (1 + 2^-20) (the factor covers the roundings of both sides), which bounds the
+// per-voxel coordinate bound 2^-22 (|x| + 25 s) + delta.  Every voxel's z is at least
+// zlo = (hi_z + lo_z) + 7 sum_j min(M_zj, 0) - 2^-21 X_z; when zlo exceeds the z bound,
+// every voxel is certainly in front of the camera, its 1/(z - dz) is below
+// 1/(zlo - dz) and its |x / z| below X_x / zlo, and the bound follows from the
+// per-voxel formulas with those maxima (the final factor covers a different
+// contraction of their products into fused multiply-adds).
+__device__ inline void shared_projection_bound(const FuseArgs& a, const FuseFrame& fr, const float* hi,
+                                               const float* lo, float delta, float* bx, float* by) {
+    const float eps22 = 2.38418579e-7f, up = 1.00000095f;  // 2^-22; 1 + 2^-20 rounded up
+    const float s25 = __fmul_rn(25.0f, a.sf);
+    float X[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float ext = __fmul_rn(7.0f, __fadd_rn(__fadd_rn(fabsf(fr.M[3 * r]), fabsf(fr.M[3 * r + 1])),
+                                                  fabsf(fr.M[3 * r + 2])));
+        X[r] = __fmul_rn(__fadd_rn(__fadd_rn(fabsf(hi[r]), fabsf(lo[r])), ext), up);
+    }
+    const float dxb = __fmaf_rn(eps22, __fadd_rn(X[0], s25), delta);
+    const float dyb = __fmaf_rn(eps22, __fadd_rn(X[1], s25), delta);
+    const float dzb = __fmaf_rn(eps22, __fadd_rn(X[2], s25), delta);
+    const float mneg = __fmul_rn(7.0f, __fadd_rn(__fadd_rn(fminf(fr.M[6], 0.0f), fminf(fr.M[7], 0.0f)),
+                                               fminf(fr.M[8], 0.0f)));
+    const float zlo = __fsub_rn(__fadd_rn(__fadd_rn(hi[2], lo[2]), mneg), __fmul_rn(4.76837158e-7f, X[2]));
+    const float gap = __fsub_rn(zlo, dzb);
+    *bx = *by = -1.0f;
+    if (!(gap > 1.0e-30f)) return;
+    const float izb = __fmul_rn(rcp_approx(gap), up);
+    const float izl = __fmul_rn(rcp_approx(zlo), up);
+    const float rxb = __fmul_rn(__fmul_rn(X[0], izl), up), ryb = __fmul_rn(__fmul_rn(X[1], izl), up);
+    const float cx = fabsf(a.cxf), cy = fabsf(a.cyf);
+    const float pxb = __fmul_rn(__fmaf_rn(a.fxf, rxb, cx), up), pyb = __fmul_rn(__fmaf_rn(a.fyf, ryb, cy), up);
+    const float ex = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(__fmul_rn(a.fxf, __fmaf_rn(rxb, dzb, dxb)), izb), 1.01f),
+                                         __fmul_rn(eps22, __fadd_rn(__fadd_rn(__fmul_rn(a.fxf, rxb), pxb), cx))),
+                               1e-6f);
+    const float ey = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(__fmul_rn(a.fyf, __fmaf_rn(ryb, dzb, dyb)), izb), 1.01f),
+                                         __fmul_rn(eps22, __fadd_rn(__fadd_rn(__fmul_rn(a.fyf, ryb), pyb), cy))),
+                               1e-6f);
+    *bx = __fmul_rn(ex, up);
+    *by = __fmul_rn(ey, up);
+}
+
 // The float64 origin of block key k for map `fr`, as float32 hi + lo with its bound.
 __device__ inline VisOrigin block_origin(const FuseArgs& a, const FuseFrame& fr, int4 k) {
     double c0[3];
@@ -117,7 +171,8 @@ __device__ inline VisOrigin block_origin(const FuseArgs& a, const FuseFrame& fr,
     const double gmax = (8.0 * (fabs((double)k.y) + fabs((double)k.z) + fabs((double)k.w)) + 24.0) * a.s;
     const double tmax = fabs(fr.ti[0]) + fabs(fr.ti[1]) + fabs(fr.ti[2]);
     o.delta = (float)(ldexp(amax + gmax + tmax + 1.0, -44));
-    o.pad = 0.0f;
+    shared_projection_bound(a, fr, o.hi, o.lo, o.delta, &o.ex, &o.ey);
+    o.pad[0] = o.pad[1] = o.pad[2] = 0.0f;
     return o;
 }
 
@@ -246,11 +301,106 @@ __global__ void __launch_bounds__(128, 8) fuse_kernel(const float* __restrict__ 
             const int i = __ffs(mm) - 1;  // maps in order
             const FuseFrame& fr = a.fr[i];
             const VisOrigin vb = org[i];
+            const float bex = vb.ex, bey = vb.ey;
             const float* __restrict__ dm = depth + (size_t)i * npix;
             const float dl = vb.delta;
             // local offsets along y and z are shared by the thread's four voxels
             const float myz[3] = {fmaf(fr.M[1], lyf, fr.M[2] * lzf), fmaf(fr.M[4], lyf, fr.M[5] * lzf),
                                   fmaf(fr.M[7], lyf, fr.M[8] * lzf)};
+            // Decisions after the projection (px, py) of a voxel certainly in front of
+            // the camera, with its error bounds: outside the image, the pixel, a valid
+            // depth, u_SDF >= -mu.  Returns 1 when certified (upd, ut set), else 0.
+            auto project_rest = [&](float px, float py, float ex, float ey, float mz, bool* upd, float* ut) -> int {
+                int pxi, pyi;
+                if (px + ex < 0.0f || px - ex >= a.Wf || py + ey < 0.0f || py - ey >= a.Hf)
+                    return 1;  // the real projection is certainly outside the image
+                if (!(ex < 1048576.0f && ey < 1048576.0f && certified_floor(px, ex, &pxi) &&
+                      certified_floor(py, ey, &pyi)))
+                    return 0;
+                // certified and within (-e, W + e): the pixel lies in the image
+                const float d = __ldg(dm + pyi * a.W + pxi);
+                if (!(isfinite(d) && d > 0.0f)) return 1;
+                // u_SDF = d - z with z = hi + mz + lo: three roundings, the error of mz, the
+                // rounding of mu and of us + mu
+                const float dh = d - vb.hi[2];
+                const float us = (dh - mz) - vb.lo[2];
+                const float eu = eps22 * (fabsf(dh) + fabsf(mz) + fabsf(us) + a.muf + s25) + dl + 1e-7f;
+                if (!(fabsf(us + a.muf) > eu)) return 0;
+                *upd = us >= -a.muf;
+                *ut = fminf(1.0f, us * a.imuf);
+                return 1;
+            };
+            auto update = [&](int q, bool upd, float ut) {
+                if (upd) {
+                    const float wn = wv[q] + 1.0f;
+                    // the running mean of Eq. 1 (f is compared with a tolerance, so the fast
+                    // division's two ulps do not matter; the update decision is already taken)
+                    fv[q] = __fdividef(fmaf(wv[q], fv[q], ut), wn);
+                    wv[q] = wn;
+                    any = true;
+                }
+            };
+            if (bex >= 0.0f) {
+                // The shared bounds (the same branch for the whole CTA): every voxel of the
+                // block is certainly in front (shared_projection_bound).  In phases, so
+                // that the four depth reads are in flight together and the float64
+                // recomputation stays off the common path: pixels, reads, u_SDF tests,
+                // then the voxels left undecided.
+                int pix[4];
+                float mzq[4];
+                unsigned need = 0u, undec = 0u;  // bit q: depth read needed / undecided
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float lx = lx0f + (float)q;
+                    const float mx = fmaf(fr.M[0], lx, myz[0]);
+                    const float my = fmaf(fr.M[3], lx, myz[1]);
+                    const float mz = fmaf(fr.M[6], lx, myz[2]);
+                    const float x = (vb.hi[0] + mx) + vb.lo[0];
+                    const float y = (vb.hi[1] + my) + vb.lo[1];
+                    const float z = (vb.hi[2] + mz) + vb.lo[2];
+                    const float inv = rcp_approx(z);
+                    const float px = fmaf(a.fxf, x * inv, a.cxf), py = fmaf(a.fyf, y * inv, a.cyf);
+                    mzq[q] = mz;
+                    pix[q] = 0;
+                    int pxi, pyi;
+                    if (px + bex < 0.0f || px - bex >= a.Wf || py + bey < 0.0f || py - bey >= a.Hf) {
+                        // the real projection is certainly outside the image
+                    } else if (bex < 1048576.0f && bey < 1048576.0f && certified_floor(px, bex, &pxi) &&
+                               certified_floor(py, bey, &pyi)) {
+                        pix[q] = pyi * a.W + pxi;  // certified and within (-e, W + e): in the image
+                        need |= 1u << q;
+                    } else {
+                        undec |= 1u << q;
+                    }
+                }
+                float dq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dq[q] = ((need >> q) & 1u) ? __ldg(dm + pix[q]) : 0.0f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!((need >> q) & 1u)) continue;
+                    const float d = dq[q];
+                    if (!(isfinite(d) && d > 0.0f)) continue;
+                    // u_SDF = d - z with z = hi + mz + lo: three roundings, the error of mz, the
+                    // rounding of mu and of us + mu
+                    const float dh = d - vb.hi[2];
+                    const float us = (dh - mzq[q]) - vb.lo[2];
+                    const float eu = eps22 * (fabsf(dh) + fabsf(mzq[q]) + fabsf(us) + a.muf + s25) + dl + 1e-7f;
+                    if (fabsf(us + a.muf) > eu) update(q, us >= -a.muf, fminf(1.0f, us * a.imuf));
+                    else undec |= 1u << q;
+                }
+                if (undec) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (!((undec >> q) & 1u)) continue;
+                        float ut = 0.0f;
+                        const bool upd = fuse_voxel_f64(dm, a, fr, 8 * m.coords[4 * b + 1] + lx0 + q,
+                                                        8 * m.coords[4 * b + 2] + ly, 8 * m.coords[4 * b + 3] + lz, &ut);
+                        update(q, upd, ut);
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float lx = lx0f + (float)q;
@@ -260,14 +410,14 @@ __global__ void __launch_bounds__(128, 8) fuse_kernel(const float* __restrict__ 
                 const float x = (vb.hi[0] + mx) + vb.lo[0];
                 const float y = (vb.hi[1] + my) + vb.lo[1];
                 const float z = (vb.hi[2] + mz) + vb.lo[2];
-                // Error of each coordinate: two roundings of |x| (the sums), the rounding of
-                // M = s R^T and of its products with l <= 7 (|M l| <= 7 s sqrt(3)), the origin
-                // residual; 2^-22 (|x| + 25 s) is twice 2^-24 (2 |x| + 49 s).
-                const float dx = fmaf(eps22, fabsf(x) + s25, dl), dy = fmaf(eps22, fabsf(y) + s25, dl),
-                            dz = fmaf(eps22, fabsf(z) + s25, dl);
                 int decided = 0;  // 1: certified in float32
                 bool upd = false;
                 float ut = 0.0f;
+                // Error of each coordinate: two roundings of |x| (the sums), the rounding
+                // of M = s R^T and of its products with l <= 7 (|M l| <= 7 s sqrt(3)), the
+                // origin residual; 2^-22 (|x| + 25 s) is twice 2^-24 (2 |x| + 49 s).
+                const float dx = fmaf(eps22, fabsf(x) + s25, dl), dy = fmaf(eps22, fabsf(y) + s25, dl),
+                            dz = fmaf(eps22, fabsf(z) + s25, dl);
                 if (z + dz <= 0.0f) {
                     decided = 1;  // certainly behind the camera
                 } else if (z - dz > 0.0f) {
@@ -276,47 +426,19 @@ __global__ void __launch_bounds__(128, 8) fuse_kernel(const float* __restrict__ 
                     const float px = fmaf(a.fxf, rx, a.cxf);
                     const float py = fmaf(a.fyf, ry, a.cyf);
                     // |x/z - rx| <= (dx + |rx| dz) / (z - dz) from the coordinates, plus the
-                    // error of the approximate 1/z (1 ulp) and the roundings of x * (1/z), the fma
-                    // and of fx, cx: below 2^-24 (|px| + |cx| + 4 fx |rx|), which
-                    // 2^-22 (fx |rx| + |px| + |cx|) covers.  The approximate 1/(z - dz) is within
-                    // 1 ulp, which the factor 1.01 covers.
+                    // error of the approximate 1/z (1 ulp) and the roundings of x * (1/z), the
+                    // fma and of fx, cx: below 2^-24 (|px| + |cx| + 4 fx |rx|), which
+                    // 2^-22 (fx |rx| + |px| + |cx|) covers.  The approximate 1/(z - dz) is
+                    // within 1 ulp, which the factor 1.01 covers.
                     const float iz = rcp_approx(z - dz);
                     const float ex = a.fxf * (dx + fabsf(rx) * dz) * iz * 1.01f + eps22 * (a.fxf * fabsf(rx) + fabsf(px) + fabsf(a.cxf)) + 1e-6f;
                     const float ey = a.fyf * (dy + fabsf(ry) * dz) * iz * 1.01f + eps22 * (a.fyf * fabsf(ry) + fabsf(py) + fabsf(a.cyf)) + 1e-6f;
-                    int pxi, pyi;
-                    if (px + ex < 0.0f || px - ex >= a.Wf || py + ey < 0.0f || py - ey >= a.Hf) {
-                        decided = 1;  // the real projection is certainly outside the image
-                    } else if (ex < 1048576.0f && ey < 1048576.0f && certified_floor(px, ex, &pxi) &&
-                               certified_floor(py, ey, &pyi)) {
-                        // certified and within (-e, W + e): the pixel lies in the image
-                        const float d = __ldg(dm + pyi * a.W + pxi);
-                        if (!(isfinite(d) && d > 0.0f)) {
-                            decided = 1;
-                        } else {
-                            // u_SDF = d - z with z = hi + mz + lo: three roundings, the error of mz,
-                            // the rounding of mu and of us + mu
-                            const float dh = d - vb.hi[2];
-                            const float us = (dh - mz) - vb.lo[2];
-                            const float eu = eps22 * (fabsf(dh) + fabsf(mz) + fabsf(us) + a.muf + s25) + dl + 1e-7f;
-                            if (fabsf(us + a.muf) > eu) {
-                                decided = 1;
-                                upd = us >= -a.muf;
-                                ut = fminf(1.0f, us * a.imuf);
-                            }
-                        }
-                    }
+                    decided = project_rest(px, py, ex, ey, mz, &upd, &ut);
                 }
                 if (!decided)
                     upd = fuse_voxel_f64(dm, a, fr, 8 * m.coords[4 * b + 1] + lx0 + q, 8 * m.coords[4 * b + 2] + ly,
                                          8 * m.coords[4 * b + 3] + lz, &ut);
-                if (upd) {
-                    const float wn = wv[q] + 1.0f;
-                    // the running mean of Eq. 1 (f is compared with a tolerance, so the fast
-                    // division's two ulps do not matter; the update decision is already taken)
-                    fv[q] = __fdividef(fmaf(wv[q], fv[q], ut), wn);
-                    wv[q] = wn;
-                    any = true;
-                }
+                update(q, upd, ut);
             }
         }
         if (any) {

@@ -3,7 +3,7 @@
 The allocation kernel (Section III-A, reading R1) finds the block keys of a ray's band
 samples in float32: the certified floors at the band's two ends and, for each axis
 whose floor changes, the first sample of each new floor (estimated from the line, then
-confirmed by certified floors on both sides).  Floors that the error bound cannot
+confirmed by certified comparisons of q with the new floor's boundary on both sides).  Floors that the error bound cannot
 certify send the ray to a per-sample walk, and samples that stay uncertified there to
 float64.  This test restates the float32 path ray by ray in numpy (float32 operations
 rounded to nearest, fused multiply-adds rounded once) and checks that every ray it
@@ -99,13 +99,14 @@ def events_path(S, dv, D, e, ez):
         span = khi[r] - klo[r]
         if span == 0:
             continue
-        if abs(span) > 2:
+        slope = F32(S.hf * D[r])
+        if abs(span) > 2 or not abs(slope) < F32(0.5):
             return None
         step = 1 if span > 0 else -1
         q0 = fma(dv, D[r], S.tf[r])
-        slope = F32(S.hf * D[r])
         for v in range(klo[r] + step, khi[r] + step, step):
-            est = F32(F32(F32(v if step > 0 else v + 1) - q0) / slope)
+            T = F32(v if step > 0 else v + 1)
+            est = F32(F32(T - q0) / slope)
             # the kernel divides approximately (within 2 ulps): est moved by S.est_ulps
             for _ in range(abs(S.est_ulps)):
                 est = np.nextafter(est, F32(np.inf) if S.est_ulps > 0 else F32(-np.inf))
@@ -114,12 +115,13 @@ def events_path(S, dv, D, e, ez):
             nc = min(max(nc, -N + 1), N)
             tries = 0
             while True:
-                fa, oka = band_floor(dv, F32(nc - 1), S.hf, D[r], S.tf[r], e[r])
-                fb, okb = band_floor(dv, F32(nc), S.hf, D[r], S.tf[r], e[r])
-                if not (oka and okb) or tries > 2:
+                da = F32(fma(fma(F32(nc - 1), S.hf, dv), D[r], S.tf[r]) - T)
+                db = F32(fma(fma(F32(nc), S.hf, dv), D[r], S.tf[r]) - T)
+                ok2 = (da >= e[r] or da < -e[r]) and (db >= e[r] or db < -e[r])
+                if not ok2 or tries > 2:
                     return None
-                at_b = fb >= v if step > 0 else fb <= v
-                at_a = fa >= v if step > 0 else fa <= v
+                at_b = db >= 0 if step > 0 else db < 0
+                at_a = da >= 0 if step > 0 else da < 0
                 if at_b and not at_a:
                     break
                 if not at_b:

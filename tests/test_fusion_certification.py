@@ -2,8 +2,9 @@
 
 The fusion kernel (Section III-A, Eq. 1) takes each voxel's integer decisions (in front
 of the camera, inside the image, which pixel, u_SDF >= -mu) in float32 together with a
-forward error bound, and recomputes the voxel in float64 only when the bound cannot
-decide.  This test restates that float32 path in numpy (float32 operations round to
+forward error bound (one projection bound shared by a block's voxels where the block
+lies clear of the camera plane, else per voxel), and recomputes the voxel in float64
+only when the bound cannot decide.  This test restates that float32 path in numpy (float32 operations round to
 nearest like the GPU's; fused multiply-adds are rounded once, exactly) and checks, on
 random poses far from the origin and on depth maps whose neighbouring pixels disagree
 (so that a wrong pixel shows), that every decision it certifies is the oracle's
@@ -57,10 +58,38 @@ def floor32(v):
     return np.floor(np.asarray(v, F32)).astype(np.int64)
 
 
-def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0)):
+def shared_bound(hi, lo, dl, M, sf, fxf, fyf, cxf, cyf, rcp_ulps):
+    """The projection-error bounds (x, y) shared by a block's voxels, per block ([nb] each;
+    -1 where the block reaches too close to the camera plane), in the origin kernel's
+    float32 operations."""
+    up, eps22 = F32(1.00000095), EPS22
+    s25 = F32(F32(25.0) * sf)
+    X = []
+    for r in range(3):
+        ext = F32(F32(7.0) * F32(F32(abs(M[3 * r]) + abs(M[3 * r + 1])) + abs(M[3 * r + 2])))
+        X.append(F32(F32(F32(np.abs(hi[r]) + np.abs(lo[r])) + ext) * up))
+    dxb, dyb, dzb = [fma32(eps22, F32(Xr + s25), dl) for Xr in X]
+    mneg = F32(F32(7.0) * F32(F32(min(M[6], F32(0)) + min(M[7], F32(0))) + min(M[8], F32(0))))
+    zlo = F32(F32(F32(hi[2] + lo[2]) + mneg) - F32(F32(4.76837158e-7) * X[2]))
+    gap = F32(zlo - dzb)
+    ok = gap > F32(1e-30)
+    izb = F32(rcp32(np.where(ok, gap, F32(1)), rcp_ulps) * up)
+    izl = F32(rcp32(np.where(ok, zlo, F32(1)), rcp_ulps) * up)
+    rxb, ryb = F32(F32(X[0] * izl) * up), F32(F32(X[1] * izl) * up)
+    cx, cy = abs(cxf), abs(cyf)
+    pxb, pyb = F32(fma32(fxf, rxb, cx) * up), F32(fma32(fyf, ryb, cy) * up)
+    ex = F32(F32(F32(F32(F32(fxf * fma32(rxb, dzb, dxb)) * izb) * F32(1.01))
+                 + F32(eps22 * F32(F32(F32(fxf * rxb) + pxb) + cx))) + F32(1e-6))
+    ey = F32(F32(F32(F32(F32(fyf * fma32(ryb, dzb, dyb)) * izb) * F32(1.01))
+                 + F32(eps22 * F32(F32(F32(fyf * ryb) + pyb) + cy))) + F32(1e-6))
+    return (np.where(ok, F32(ex * up), F32(-1)).astype(F32), np.where(ok, F32(ey * up), F32(-1)).astype(F32))
+
+
+def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0), with_shared=False):
     """The float32 path of the fusion kernel for every voxel of `keys`: (decided, update,
-    u_tsdf) per voxel, each [nb, 512].  rcp: the ulp offsets of the two reciprocals
-    (1/z, 1/(z - dz)) from their correctly rounded values."""
+    u_tsdf) per voxel, each [nb, 512] (with_shared: also which blocks take the bound
+    shared by their voxels).  rcp: the ulp offsets of the two reciprocals (1/z,
+    1/(z - dz)) from their correctly rounded values."""
     s = prm.voxel_size
     Ri, ti = O.pose_inverse(T)
     keys = np.asarray(keys, np.int64)
@@ -89,9 +118,15 @@ def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0)):
     decided = np.zeros((nb, 512), bool)
     upd = np.zeros((nb, 512), bool)
     ut = np.zeros((nb, 512), F32)
-    behind = (z + dz) <= 0
+    with np.errstate(all="ignore"):
+        # the bound the origin kernel shares among a block's voxels (shared_projection_bound),
+        # every operation rounded as written there; its reciprocals one ulp low like 1/(z - dz)
+        ex_sh, ey_sh = shared_bound(hi, lo, dl[:, 0], M, sf, fxf, fyf, cxf, cyf, rcp[1])
+        ex_sh, ey_sh = ex_sh[:, None], ey_sh[:, None]
+    shared = np.broadcast_to(ex_sh >= 0, (nb, 512))
+    behind = ~shared & ((z + dz) <= 0)
     decided |= behind
-    front = (z - dz) > 0
+    front = shared | ((z - dz) > 0)
     with np.errstate(all="ignore"):
         inv = rcp32(z, rcp[0])
         rx, ry = (x * inv).astype(F32), (y * inv).astype(F32)
@@ -101,6 +136,8 @@ def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0)):
               + F32(1e-6)).astype(F32)
         ey = (fyf * (dy + np.abs(ry) * dz) * iz * F32(1.01) + EPS22 * (fyf * np.abs(ry) + np.abs(py) + np.abs(cyf))
               + F32(1e-6)).astype(F32)
+        ex = np.where(shared, ex_sh, ex).astype(F32)
+        ey = np.where(shared, ey_sh, ey).astype(F32)
         outside = front & (((px + ex) < 0) | ((px - ex) >= Wf) | ((py + ey) < 0) | ((py - ey) >= Hf))
         decided |= outside
         small = (ex < F32(2.0 ** 20)) & (ey < F32(2.0 ** 20))
@@ -116,6 +153,8 @@ def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0)):
         decided |= cert
         upd |= cert & (us >= -muf)
         ut = np.where(cert, np.minimum(F32(1.0), us * imuf), ut).astype(F32)
+    if with_shared:
+        return decided, upd, ut, ex_sh[:, 0] >= 0
     return decided, upd, ut
 
 
@@ -154,8 +193,9 @@ def test_certified_decisions_are_the_oracles(seed, far, rcp):
     keys = sorted({(0,) + tuple(int(b) for b in np.floor(pg[:, i] / (8 * prm.voxel_size))) for i in range(n)})
     g = grid_from_blocks(keys)
     want = O.fuse_depth(g, depth, K, T)
-    decided, upd, ut = kernel_decisions(keys, depth, K, T, prm, rcp)
+    decided, upd, ut, shared = kernel_decisions(keys, depth, K, T, prm, rcp, with_shared=True)
     assert decided.mean() > 0.97, decided.mean()
+    assert shared.mean() > 0.8, shared.mean()  # most blocks take the bound shared by their voxels
     np.testing.assert_array_equal(upd[decided], want[decided])
     both = decided & upd
     assert both.sum() > 1000

@@ -81,6 +81,29 @@ def test_conv3_forward_layer(layer_case):
     assert N.denser_net_check() == N.DENSER_OK   # every tensor-core wait completed
 
 
+def test_conv3_pipelined_samples():
+    """Several samples per CTA (700 samples; the grid has two CTAs per SM), so that each
+    CTA restages its planes and reuses its tensor-memory columns sample after sample:
+    sampled outputs (the first and last samples, and ones spread through every CTA's
+    turn) against the FP64 oracle at the per-layer tolerance, and two calls bit-equal."""
+    rng = np.random.default_rng(5)
+    n = 700
+    x = bf16_round(rng.standard_normal((n, 16, 10, 10, 10)))
+    W = bf16_round(rng.standard_normal((16, 16, 3, 3, 3)) * 0.1)
+    b = rng.standard_normal(16).astype(np.float32).astype(np.float64)
+    xd, wd, bd = dev(to_ours(x), torch.bfloat16), dev(w_ours(W), torch.bfloat16), dev(b)
+    y = torch.empty(n, 1000, 16, device="cuda")
+    y2 = torch.empty_like(y)
+    N.denser_conv3(xd, wd, bd, 1, None, y, n)
+    N.denser_conv3(xd, wd, bd, 1, None, y2, n)
+    assert N.denser_net_check() == N.DENSER_OK
+    assert torch.equal(y, y2)
+    idx = np.unique(np.concatenate([[0, 1, n - 1, n - 2], rng.choice(n, 24, replace=False)]))
+    ref = np.maximum(NO.conv3d_same(x[idx], W, b), 0)
+    got = from_ours(y[torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.float64), 16)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
 def test_conv3_gradients_layer(layer_case):
     n, x, W, b = layer_case
     rng = np.random.default_rng(1)
