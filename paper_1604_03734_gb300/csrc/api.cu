@@ -887,6 +887,40 @@ int denser_extract_surface(denser_ctx* c, float* tri_pos, int64_t* tri_ids, int6
         }
         long long total = 0;
         unsigned long long items = 0;
+        const bool device_out = (!tri_pos || is_device_ptr(tri_pos)) && (!tri_ids || is_device_ptr(tri_ids));
+        if ((tri_pos || tri_ids) && device_out && capacity > 0) {
+            // device outputs: count, scan and emit queued back to back, one wait at the end;
+            // a list that overflowed (the emit then wrote nothing) is grown and both redone
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                const long long need = attempt == 0 ? std::max<long long>((long long)nb * 32, c->surf_list_cap)
+                                                    : (long long)items;
+                if (c->surf_list_cap < need) {
+                    if (c->surf_list) cudaFree(c->surf_list);
+                    c->surf_list = nullptr;
+                    c->surf_list_cap = 0;
+                    if ((rc = cuda_check(c, cudaMalloc(&c->surf_list, (size_t)need * 8), "cudaMalloc(surface list)")))
+                        return rc;
+                    c->surf_list_cap = need;
+                }
+                if ((rc = launch_surface(c, nb, 0, nullptr, nullptr, 0, s))) return rc;
+                if ((rc = launch_surface(c, nb, 2, tri_pos, (long long*)tri_ids, capacity, s))) return rc;
+                if ((rc = copy_out(c, &total, c->surf_offsets + nb, 8, s, "read triangle count"))) return rc;
+                if ((rc = copy_out(c, &items, c->surf_cursor, 8, s, "read cube count"))) return rc;
+                if ((rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize"))) return rc;
+                if ((long long)items <= c->surf_list_cap) break;
+            }
+            c->surf_items = (long long)items;
+            *n_tri_out = total;
+            if (block_first) {
+                if ((rc = copy_out(c, block_first, c->surf_offsets, ((size_t)nb + 1) * 8, s, "copy block offsets")))
+                    return rc;
+                if ((rc = cuda_check(c, cudaStreamSynchronize(s), "stream synchronize"))) return rc;
+            }
+            if (total > capacity)
+                return set_error(c, DENSER_ERR_TOO_LARGE,
+                                 "extract_surface: more triangles than capacity (*n_tri_out holds the total)");
+            return DENSER_OK;
+        }
         for (int attempt = 0; attempt < 2; ++attempt) {
             // first a guess of 32 listed cubes per block, then exactly what the count found
             const long long need = attempt == 0 ? (long long)nb * 32 : (long long)items;

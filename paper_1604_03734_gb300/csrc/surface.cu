@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kSurfThreads, 12) surface_count_kernel(DeviceM
                                                                          unsigned long long* __restrict__ cursor) {
     __shared__ float su[kRegion];
     __shared__ unsigned char som[kRegion];
-    __shared__ int nbk[8];
+    __shared__ int nbk[2][8];  // this block's and the next block's upper neighbours
     __shared__ unsigned char lut[256];  // triangles of a cube by its negative-corner mask
     __shared__ int wsum[kSurfThreads / 32];
     __shared__ unsigned long long chunk;
@@ -105,12 +105,18 @@ __global__ void __launch_bounds__(kSurfThreads, 12) surface_count_kernel(DeviceM
         lut[i] = (unsigned char)n;
     }
     const int lx0 = (4 * t) & 7, ly = ((4 * t) >> 3) & 7, lz = (4 * t) >> 6;
+    // the next block's neighbour row is read one block ahead, so that a block's region
+    // loads do not wait behind it
+    int cur = 0;
+    if (t < 8 && (int)blockIdx.x < nb) nbk[0][t] = __ldg(up + 8 * (size_t)blockIdx.x + t);
     for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-        if (t < 8) nbk[t] = __ldg(up + 8 * (size_t)b + t);
+        const int bn = b + gridDim.x;
+        const int pre = (t < 8 && bn < nb) ? __ldg(up + 8 * (size_t)bn + t) : -1;
         __syncthreads();
+#pragma unroll
         for (int i = t; i < kRegion; i += kSurfThreads) {
             const int x = i % kR, y = (i / kR) % kR, z = i / (kR * kR);
-            const int nk = nbk[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
+            const int nk = nbk[cur][(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
             float uv = 0.0f;
             unsigned char o = 0;
             if (nk >= 0) {
@@ -184,7 +190,9 @@ __global__ void __launch_bounds__(kSurfThreads, 12) surface_count_kernel(DeviceM
             ++slot;
             tri += cnt[q];
         }
+        if (t < 8) nbk[cur ^ 1][t] = pre;
         __syncthreads();  // shared state is rewritten by the next block
+        cur ^= 1;
     }
 }
 
@@ -261,13 +269,22 @@ __device__ __forceinline__ int tet_edges(unsigned m4, int sg, int e[2][3][2]) {
 // Emit pass: one thread per listed cube.  It reads the cube's eight corner values
 // (from the block and its upper neighbours), and writes the triangles of its six
 // tetrahedra from the block's first triangle plus the cube's offset.
+// With n_items_dev, the count is read on the device (the count pass queued just before),
+// and nothing is written when the list overflowed (more than list_cap cubes: the host
+// then grows the list and runs both passes again).
 template <typename T>
 __global__ void __launch_bounds__(64) surface_emit_kernel(DeviceMap m, const T* __restrict__ u,
                                                            const int32_t* __restrict__ up,
                                                            const unsigned long long* __restrict__ list,
-                                                           long long n_items, const long long* __restrict__ offsets,
+                                                           long long n_items,
+                                                           const unsigned long long* __restrict__ n_items_dev,
+                                                           long long list_cap, const long long* __restrict__ offsets,
                                                            float s, long long capacity, float* __restrict__ tri_pos,
                                                            long long* __restrict__ tri_ids) {
+    if (n_items_dev) {
+        n_items = (long long)*n_items_dev;
+        if (n_items > list_cap) return;
+    }
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < n_items;
          it += (long long)gridDim.x * blockDim.x) {
         const unsigned long long w = list[it];
@@ -344,15 +361,21 @@ int surface_launch(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long lon
                                                               c->surf_list, c->surf_list_cap, c->surf_cursor);
         surface_scan_kernel<<<1, 1024, 0, s>>>(c->d, c->surf_counts, c->surf_offsets);
         c->launches += 3;
-    } else {
+    } else if (pass == 1) {
         const long long n_items = c->surf_items;
         if (n_items > 0) {
             // small CTAs: a few tens of thousands of listed cubes still spread over every SM
             surface_emit_kernel<T><<<grid_for(c->sm_count, n_items, 64, 16), 64, 0, s>>>(
-                c->d, (const T*)c->d.u, c->surf_up, c->surf_list, n_items, c->surf_offsets, (float)c->prm.voxel_size,
-                capacity, tri_pos, tri_ids);
+                c->d, (const T*)c->d.u, c->surf_up, c->surf_list, n_items, nullptr, 0, c->surf_offsets,
+                (float)c->prm.voxel_size, capacity, tri_pos, tri_ids);
             c->launches += 1;
         }
+    } else {
+        // the count still on the device: 16 CTAs of 64 threads per SM stride over it
+        surface_emit_kernel<T><<<c->sm_count * 16, 64, 0, s>>>(
+            c->d, (const T*)c->d.u, c->surf_up, c->surf_list, 0, c->surf_cursor, c->surf_list_cap, c->surf_offsets,
+            (float)c->prm.voxel_size, capacity, tri_pos, tri_ids);
+        c->launches += 1;
     }
     return cuda_check(c, cudaGetLastError(), "surface kernel");
 }
@@ -361,7 +384,9 @@ int surface_launch(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long lon
 
 // pass 0: neighbour rows, counts per block, the list of cubes with triangles, and the
 // scan into c->surf_offsets (offsets[nb] = total, *c->surf_cursor = listed cubes);
-// pass 1: write the first `capacity` triangles of the c->surf_items listed cubes.
+// pass 1: write the first `capacity` triangles of the c->surf_items listed cubes;
+// pass 2: the same with the listed cubes counted on the device (right after pass 0,
+// no host round trip between them).
 int launch_surface(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long long* tri_ids, int64_t capacity,
                    cudaStream_t s) {
     if (nb <= 0) return DENSER_OK;
