@@ -27,7 +27,7 @@ DEFAULT_CANDIDATES = (
     (4, 1, 0, 1), (4, 1, 2, 1), (4, 0, 2, 1), (4, 0, 0, 1), (4, 0, 3, 1),
     (5, 0, 0, 1), (5, 1, 0, 1), (5, 0, 2, 1),
     (6, 0, 0, 1), (6, 1, 0, 1), (6, 0, 1, 1), (6, 0, 3, 1),
-    (7, 0, 2, 1), (7, 0, 0, 1), (7, 0, 3, 1), (8, 0, 2, 1), (8, 0, 0, 1),
+    (7, 0, 2, 1), (7, 0, 0, 1), (7, 0, 3, 1), (8, 0, 2, 1), (8, 0, 0, 1), (8, 0, 3, 1),
     (9, 0, 0, 1), (9, 0, 1, 1), (9, 0, 3, 1),
 )
 

@@ -238,36 +238,21 @@ __device__ bool band_keys_by_events(const AllocArgs& a, const AllocFrame& fr, in
             else n2[r] = nc;
         }
     }
-    // The keys in sample order (changes at the same sample make one key).  Every key
-    // lies in the box between the end keys; when the whole box is in range, a floor
-    // change moves the packed key by +-1 in its axis's field (no field over- or
-    // underflows), else each key is checked and packed on its own.
-    const int lo0 = fr.Ti[0] + min(klo[0], khi[0]), hi0 = fr.Ti[0] + max(klo[0], khi[0]);
-    const int lo1 = fr.Ti[1] + min(klo[1], khi[1]), hi1 = fr.Ti[1] + max(klo[1], khi[1]);
-    const int lo2 = fr.Ti[2] + min(klo[2], khi[2]), hi2 = fr.Ti[2] + max(klo[2], khi[2]);
-    const bool box_ok = key_in_range(a.seg, lo0, lo1, lo2) && key_in_range(a.seg, hi0, hi1, hi2);
+    // the keys in sample order: changes at the same sample make one key
     int k0 = klo[0], k1 = klo[1], k2 = klo[2];
-    unsigned long long key = box_ok ? pack_key(a.seg, fr.Ti[0] + k0, fr.Ti[1] + k1, fr.Ti[2] + k2) : 0ull;
-    const long long d0 = st[0], d1 = (long long)st[1] << kCoordBits, d2 = (long long)st[2] << (2 * kCoordBits);
     int c0 = 0, c1 = 0, c2 = 0;  // changes taken per axis
     for (int it = 0;; ++it) {
-        if (box_ok) {
-            push_key(m, rk, key, frame);
-        } else {
-            const int b0 = fr.Ti[0] + k0, b1 = fr.Ti[1] + k1, b2 = fr.Ti[2] + k2;
-            if (key_in_range(a.seg, b0, b1, b2)) push_key(m, rk, pack_key(a.seg, b0, b1, b2), frame);
-            else *range_err = true;
-        }
+        const int b0 = fr.Ti[0] + k0, b1 = fr.Ti[1] + k1, b2 = fr.Ti[2] + k2;
+        if (key_in_range(a.seg, b0, b1, b2)) push_key(m, rk, pack_key(a.seg, b0, b1, b2), frame);
+        else *range_err = true;
         const int x0 = c0 == 0 ? n1[0] : (c0 == 1 ? n2[0] : kNone);
         const int x1 = c1 == 0 ? n1[1] : (c1 == 1 ? n2[1] : kNone);
         const int x2 = c2 == 0 ? n1[2] : (c2 == 1 ? n2[2] : kNone);
         const int n = min(x0, min(x1, x2));
         if (n == kNone || it >= 6) break;
-        long long dk = 0;
-        if (x0 == n) k0 += st[0], ++c0, dk += d0;
-        if (x1 == n) k1 += st[1], ++c1, dk += d1;
-        if (x2 == n) k2 += st[2], ++c2, dk += d2;
-        key += (unsigned long long)dk;
+        if (x0 == n) k0 += st[0], ++c0;
+        if (x1 == n) k1 += st[1], ++c1;
+        if (x2 == n) k2 += st[2], ++c2;
     }
     return true;
 }
