@@ -502,10 +502,13 @@ def main():
         if not overlap:
             if ev is not None:
                 # the call waits for the fusion before it queues the loop, so the first
-                # event lands after the fusion and the second after the loop
+                # event lands after the fusion and the second after the loop; then the
+                # FP64 primal and dual energies (the gap) of the result, as the
+                # statistics would give them
                 ev[0].record(stream)
                 N.denser_regularize(ctx, args.iters, 0.0, 0, stream, stats=False)
                 ev[1].record(stream)
+                N.denser_energy(ctx, stream)
                 st = None
             else:
                 st = N.denser_regularize(ctx, args.iters, 0.0, 0, stream)
@@ -518,6 +521,7 @@ def main():
         N.denser_regularize(ctx, args.iters, 0.0, 0, stream, stats=False)
         side.wait_event(fused)
         N.denser_extract(ctx, outs["coords"], outs["f"], outs["w"], outs["omega"], None, outs["cap"], side)
+        N.denser_energy(ctx, stream)
         N.denser_extract(ctx, None, None, None, None, outs["u"], outs["cap"], stream)
         return None
 

@@ -123,10 +123,9 @@ typedef struct {
  *                    the current block computes,
  *                 7: as 4 with the face and edge halos split into balanced items over
  *                    all 64 threads (82 row items: two per thread for 18 threads, one
- *                    for the rest) instead of one branch per face; the default for FP32
- *                    storage, with order 0 and ctas_per_sm 2,
- *                 8: as 2 with the same balanced face items; the default for 16-bit
- *                    storage, with order 0 and ctas_per_sm 2,
+ *                    for the rest) instead of one branch per face; the default, with
+ *                    order 0 and ctas_per_sm 2,
+ *                 8: as 2 with the same balanced face items,
  *                 9: as 6 with the balanced face items
  *   order         0: blocks in index order, 1: blocks sorted by (segment, bz, by, bx)
  *                 (neighbours are visited close together, so halos hit in L2)

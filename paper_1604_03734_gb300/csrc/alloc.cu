@@ -9,7 +9,7 @@
 //                 inserts it by CAS into the open-addressing table, appends it to the
 //                 call's new-key list when it is new, and lowers the slot's birth (the
 //                 first map of the batch that reached the key) by an atomic min;
-//   sort_chunks   bitonic sort of the new keys by (birth, key), kSortChunk keys per CTA
+//   sort_chunks   bitonic sort of the new keys by (birth, key), kNewKeyChunk keys per CTA
 //                 in shared memory;
 //   rank_assign   global rank of each new key = its rank in its chunk plus a binary
 //                 search in every other chunk; block index = blocks so far + rank, which
@@ -476,20 +476,21 @@ __global__ void __launch_bounds__(256) laser_keys_kernel(const float* __restrict
     if (range_err) report(m.counters, kErrRange);
 }
 
-// Sorts (key, val) pairs in place in chunks of kSortChunk (bitonic network in shared
+// Sorts (key, val) pairs in place in chunks of CHUNK (bitonic network in shared
 // memory over the next power of two >= the chunk's count).  *count may exceed
 // capacity; only the first `capacity` pairs exist.  With `birth` (the allocation's new
 // keys, val = hash slot), each key's segment bits are first replaced by its slot's
 // birth, so that the keys sort by (birth, key) and are stored that way.
+template <int CHUNK>
 __global__ void __launch_bounds__(1024) sort_chunks_kernel(unsigned long long* keys, uint32_t* vals,
                                                            const int32_t* count, int capacity,
                                                            const int32_t* __restrict__ birth) {
-    __shared__ unsigned long long sk[kSortChunk];
-    __shared__ uint32_t ss[kSortChunk];
+    __shared__ unsigned long long sk[CHUNK];
+    __shared__ uint32_t ss[CHUNK];
     const int n = min(*count, capacity);
-    const int base = blockIdx.x * kSortChunk;
+    const int base = blockIdx.x * CHUNK;
     if (base >= n) return;
-    const int cnt = min(kSortChunk, n - base);
+    const int cnt = min(CHUNK, n - base);
     int size = 64;
     while (size < cnt) size <<= 1;
     for (int i = threadIdx.x; i < size; i += blockDim.x) {
@@ -530,14 +531,14 @@ __global__ void __launch_bounds__(1024) sort_chunks_kernel(unsigned long long* k
 
 // Global rank of element i among n distinct keys sorted in chunks: its position in
 // its own chunk plus, for every other chunk, the number of keys below it.
-__device__ long long global_rank(const unsigned long long* keys, int n, int i) {
+__device__ long long global_rank(const unsigned long long* keys, int n, int i, int chunk) {
     const unsigned long long key = keys[i];
-    const int nchunks = (n + kSortChunk - 1) / kSortChunk;
-    const int c = i / kSortChunk;
-    long long rank = i - c * kSortChunk;
+    const int nchunks = (n + chunk - 1) / chunk;
+    const int c = i / chunk;
+    long long rank = i - c * chunk;
     for (int c2 = 0; c2 < nchunks; ++c2) {
         if (c2 == c) continue;
-        int lo = c2 * kSortChunk, hi = min(lo + kSortChunk, n);
+        int lo = c2 * chunk, hi = min(lo + chunk, n);
         const int first = lo;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -553,7 +554,7 @@ __global__ void order_scatter_kernel(const unsigned long long* keys, const uint3
                                      int capacity, int32_t* order) {
     const int n = min(*count, capacity);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        order[global_rank(keys, n, i)] = (int32_t)vals[i];
+        order[global_rank(keys, n, i, kSortChunk)] = (int32_t)vals[i];
 }
 
 __global__ void rank_assign_kernel(DeviceMap m) {
@@ -562,7 +563,7 @@ __global__ void rank_assign_kernel(DeviceMap m) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         // the list holds (birth, key without segment); the table holds the key itself
         const unsigned long long sorted = m.new_keys[i];
-        const long long idx = nb + global_rank(m.new_keys, n, i);
+        const long long idx = nb + global_rank(m.new_keys, n, i, kNewKeyChunk);
         const uint32_t slot = m.new_slots[i];
         if (idx < (long long)m.max_blocks) {
             int32_t s, x, y, z;
@@ -718,8 +719,8 @@ int launch_alloc(denser_ctx* c, const float* depth, int n_frames, const denser_i
 // The inserted keys of one allocation call become blocks: sorted (chunks, then ranks
 // across chunks), zeroed, counted.
 int finish_alloc(denser_ctx* c, cudaStream_t s) {
-    const int chunks = (int)((c->d.max_new + kSortChunk - 1) / kSortChunk);
-    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->d.new_keys, c->d.new_slots, c->d.counters + kNumNew,
+    const int chunks = (int)((c->d.max_new + kNewKeyChunk - 1) / kNewKeyChunk);
+    sort_chunks_kernel<kNewKeyChunk><<<chunks, kNewKeyChunk, 0, s>>>(c->d.new_keys, c->d.new_slots, c->d.counters + kNumNew,
                                                (int)c->d.max_new, c->d.hash_birth);
     rank_assign_kernel<<<grid_for(c->sm_count, c->d.max_new, 256, 4), 256, 0, s>>>(c->d);
     int nreg;
@@ -777,7 +778,7 @@ int launch_block_order(denser_ctx* c, int64_t n_blocks, cudaStream_t s) {
     order_keys_kernel<<<grid_for(c->sm_count, n_blocks, 256, 8), 256, 0, s>>>(c->d.coords, cnt, c->order_keys,
                                                                               c->order_vals);
     const int chunks = (int)((n_blocks + kSortChunk - 1) / kSortChunk);
-    sort_chunks_kernel<<<chunks, 1024, 0, s>>>(c->order_keys, c->order_vals, cnt, (int)c->d.max_blocks, nullptr);
+    sort_chunks_kernel<kSortChunk><<<chunks, 1024, 0, s>>>(c->order_keys, c->order_vals, cnt, (int)c->d.max_blocks, nullptr);
     order_scatter_kernel<<<grid_for(c->sm_count, n_blocks, 256, 8), 256, 0, s>>>(c->order_keys, c->order_vals, cnt,
                                                                                  (int)c->d.max_blocks, c->order);
     c->launches += 3;

@@ -17,7 +17,9 @@ constexpr int kBlockVoxels = 512;
 constexpr int kNeighbours = 12;
 constexpr int kVisOriginFloats = 12;      // words per (listed block, map) entry of the fusion origins
 constexpr int kMaxProbe = 512;             // linear-probe limit of the hash table
-constexpr int kSortChunk = 2048;           // keys sorted per CTA before the rank merge
+constexpr int kSortChunk = 2048;           // keys sorted per CTA before the rank merge (block order)
+constexpr int kNewKeyChunk = 512;          // the same for an allocation call's new keys (a few thousand:
+                                           // several CTAs sort at once)
 constexpr int kSweepThreads = 512;
 // Largest block pool a context accepts.  Voxel offsets (block * 512 + l) are computed in
 // 64 bits everywhere; block indices are 32-bit, and 2^24 blocks (8.6 G voxels, about
