@@ -142,11 +142,14 @@ __device__ inline void shared_projection_bound(const FuseArgs& a, const FuseFram
     const float rxb = __fmul_rn(__fmul_rn(X[0], izl), up), ryb = __fmul_rn(__fmul_rn(X[1], izl), up);
     const float cx = fabsf(a.cxf), cy = fabsf(a.cyf);
     const float pxb = __fmul_rn(__fmaf_rn(a.fxf, rxb, cx), up), pyb = __fmul_rn(__fmaf_rn(a.fyf, ryb, cy), up);
+    const float eps23 = 1.19209290e-7f;  // 2^-23
     const float ex = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(__fmul_rn(a.fxf, __fmaf_rn(rxb, dzb, dxb)), izb), 1.01f),
-                                         __fmul_rn(eps22, __fadd_rn(__fadd_rn(__fmul_rn(a.fxf, rxb), pxb), cx))),
+                                         __fadd_rn(__fmul_rn(eps22, __fmul_rn(a.fxf, rxb)),
+                                                   __fmul_rn(eps23, __fadd_rn(pxb, cx)))),
                                1e-6f);
     const float ey = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(__fmul_rn(a.fyf, __fmaf_rn(ryb, dzb, dyb)), izb), 1.01f),
-                                         __fmul_rn(eps22, __fadd_rn(__fadd_rn(__fmul_rn(a.fyf, ryb), pyb), cy))),
+                                         __fadd_rn(__fmul_rn(eps22, __fmul_rn(a.fyf, ryb)),
+                                                   __fmul_rn(eps23, __fadd_rn(pyb, cy)))),
                                1e-6f);
     *bx = __fmul_rn(ex, up);
     *by = __fmul_rn(ey, up);
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(128, 8) fuse_kernel(const float* __restrict__ 
     const int lx0 = l0 & 7, ly = (l0 >> 3) & 7, lz = l0 >> 6;
     const VisEntry* __restrict__ vis = reinterpret_cast<const VisEntry*>(m.visible);
     const float lyf = (float)ly, lzf = (float)lz, lx0f = (float)lx0;
-    const float eps22 = 2.38418579e-7f;  // 2^-22
+    const float eps22 = 2.38418579e-7f, eps23 = 1.19209290e-7f;  // 2^-22, 2^-23
     const float s25 = 25.0f * a.sf;
     const size_t npix = (size_t)a.W * a.H;
     // the next work-list entry is fetched one block ahead, so that a block's f, w and
@@ -428,11 +431,13 @@ __global__ void __launch_bounds__(128, 8) fuse_kernel(const float* __restrict__ 
                     // |x/z - rx| <= (dx + |rx| dz) / (z - dz) from the coordinates, plus the
                     // error of the approximate 1/z (1 ulp) and the roundings of x * (1/z), the
                     // fma and of fx, cx: below 2^-24 (|px| + |cx| + 4 fx |rx|), which
-                    // 2^-22 (fx |rx| + |px| + |cx|) covers.  The approximate 1/(z - dz) is
-                    // within 1 ulp, which the factor 1.01 covers.
+                    // 2^-22 fx |rx| + 2^-23 (|px| + |cx|) covers (twice on the second part).
+                    // The approximate 1/(z - dz) is within 1 ulp, which the factor 1.01 covers.
                     const float iz = rcp_approx(z - dz);
-                    const float ex = a.fxf * (dx + fabsf(rx) * dz) * iz * 1.01f + eps22 * (a.fxf * fabsf(rx) + fabsf(px) + fabsf(a.cxf)) + 1e-6f;
-                    const float ey = a.fyf * (dy + fabsf(ry) * dz) * iz * 1.01f + eps22 * (a.fyf * fabsf(ry) + fabsf(py) + fabsf(a.cyf)) + 1e-6f;
+                    const float ex = a.fxf * (dx + fabsf(rx) * dz) * iz * 1.01f + eps22 * (a.fxf * fabsf(rx)) +
+                                     eps23 * (fabsf(px) + fabsf(a.cxf)) + 1e-6f;
+                    const float ey = a.fyf * (dy + fabsf(ry) * dz) * iz * 1.01f + eps22 * (a.fyf * fabsf(ry)) +
+                                     eps23 * (fabsf(py) + fabsf(a.cyf)) + 1e-6f;
                     decided = project_rest(px, py, ex, ey, mz, &upd, &ut);
                 }
                 if (!decided)

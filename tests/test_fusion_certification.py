@@ -19,6 +19,7 @@ from tests.oracle_helpers import grid_from_blocks
 
 F32 = np.float32
 EPS22 = F32(2.0 ** -22)
+EPS23 = F32(2.0 ** -23)
 
 
 def fma32(a, b, c):
@@ -79,9 +80,9 @@ def shared_bound(hi, lo, dl, M, sf, fxf, fyf, cxf, cyf, rcp_ulps):
     cx, cy = abs(cxf), abs(cyf)
     pxb, pyb = F32(fma32(fxf, rxb, cx) * up), F32(fma32(fyf, ryb, cy) * up)
     ex = F32(F32(F32(F32(F32(fxf * fma32(rxb, dzb, dxb)) * izb) * F32(1.01))
-                 + F32(eps22 * F32(F32(F32(fxf * rxb) + pxb) + cx))) + F32(1e-6))
+                 + F32(F32(eps22 * F32(fxf * rxb)) + F32(EPS23 * F32(pxb + cx)))) + F32(1e-6))
     ey = F32(F32(F32(F32(F32(fyf * fma32(ryb, dzb, dyb)) * izb) * F32(1.01))
-                 + F32(eps22 * F32(F32(F32(fyf * ryb) + pyb) + cy))) + F32(1e-6))
+                 + F32(F32(eps22 * F32(fyf * ryb)) + F32(EPS23 * F32(pyb + cy)))) + F32(1e-6))
     return (np.where(ok, F32(ex * up), F32(-1)).astype(F32), np.where(ok, F32(ey * up), F32(-1)).astype(F32))
 
 
@@ -132,10 +133,10 @@ def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0), with_shared=False):
         rx, ry = (x * inv).astype(F32), (y * inv).astype(F32)
         px, py = fma32(fxf, rx, cxf), fma32(fyf, ry, cyf)
         iz = rcp32((z - dz).astype(F32), rcp[1])
-        ex = (fxf * (dx + np.abs(rx) * dz) * iz * F32(1.01) + EPS22 * (fxf * np.abs(rx) + np.abs(px) + np.abs(cxf))
-              + F32(1e-6)).astype(F32)
-        ey = (fyf * (dy + np.abs(ry) * dz) * iz * F32(1.01) + EPS22 * (fyf * np.abs(ry) + np.abs(py) + np.abs(cyf))
-              + F32(1e-6)).astype(F32)
+        ex = (fxf * (dx + np.abs(rx) * dz) * iz * F32(1.01) + EPS22 * (fxf * np.abs(rx))
+              + EPS23 * (np.abs(px) + np.abs(cxf)) + F32(1e-6)).astype(F32)
+        ey = (fyf * (dy + np.abs(ry) * dz) * iz * F32(1.01) + EPS22 * (fyf * np.abs(ry))
+              + EPS23 * (np.abs(py) + np.abs(cyf)) + F32(1e-6)).astype(F32)
         ex = np.where(shared, ex_sh, ex).astype(F32)
         ey = np.where(shared, ey_sh, ey).astype(F32)
         outside = front & (((px + ex) < 0) | ((px - ex) >= Wf) | ((py + ey) < 0) | ((py - ey) >= Hf))
