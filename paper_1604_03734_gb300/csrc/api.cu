@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 #include <string>
 
 #include <initializer_list>
@@ -335,7 +336,7 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
                 {(void**)&c->d.new_slots, max_new * 4},
                 {(void**)&c->d.visible, mb * 32},
                 {(void**)&c->d.vis_org, mb * 4 * kVisOriginFloats},
-                {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2) * 8},
+                {(void**)&c->d.partials, (2 * (size_t)kEnergyGrid + 2 + kInvWeights) * 8},
                 {(void**)&c->order, mb * 4},
                 {(void**)&c->order_keys, mb * 8},
                 {(void**)&c->order_vals, mb * 4},
@@ -364,7 +365,13 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
         delete c;
         return DENSER_ERR_CUDA;
     }
-    if (configure_kernels(c) != DENSER_OK || denser_reset(c, nullptr) != DENSER_OK ||
+    // after the energy partials: 1/(2 lambda w) for the counts w = 1 .. kInvWeights, each an
+    // IEEE float64 division, so that the dual energy multiplies where it would divide
+    std::vector<double> inv2lw(kInvWeights);
+    for (int i = 0; i < kInvWeights; ++i) inv2lw[i] = 1.0 / (2.0 * c->prm.lambda * (double)(i + 1));
+    if (cudaMemcpy(c->d.partials + 2 * kEnergyGrid + 2, inv2lw.data(), kInvWeights * sizeof(double),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        configure_kernels(c) != DENSER_OK || denser_reset(c, nullptr) != DENSER_OK ||
         cudaDeviceSynchronize() != cudaSuccess) {
         free_all(c);
         delete c;

@@ -21,6 +21,7 @@ constexpr int kSortChunk = 2048;           // keys sorted per CTA before the ran
 constexpr int kNewKeyChunk = 512;          // the same for an allocation call's new keys (a few thousand:
                                            // several CTAs sort at once)
 constexpr int kSweepThreads = 512;
+constexpr int kInvWeights = 4096;          // integer counts w whose 1/(2 lambda w) the energy reads from a table
 // Largest block pool a context accepts.  Voxel offsets (block * 512 + l) are computed in
 // 64 bits everywhere; block indices are 32-bit, and 2^24 blocks (8.6 G voxels, about
 // 400 GB of FP32 state) is beyond any one device's memory.

@@ -1491,13 +1491,26 @@ constexpr size_t sweep_pipe_smem() {
     return ((sizeof(Tiles) + 15) / 16) * 16 + 2 * StageLayout<T>::kBytes + 3 * kNeighbours * sizeof(int);
 }
 
+// sqrt(x) for the primal energy: the single-precision reciprocal square root (rsqrtf,
+// within 2 ulps) gives s0 = x r, one step of Heron's method (Newton's iteration for
+// s^2 = x), s1 = s0 + (x - s0^2) r / 2 in float64, squares its relative error (about
+// 2^-44 left, below the parity tolerance of the energies); x too small for single
+// precision takes the float64 square root.
+__device__ __forceinline__ double energy_sqrt(double x) {
+    if (!(x > 1.0e-30)) return sqrt(x);
+    const float r = rsqrtf((float)x);
+    const double s0 = (double)((float)x * r);
+    return fma(0.5 * (double)r, fma(-s0, s0, x), s0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kSweepThreads) energy_kernel(const T* __restrict__ u, const T* __restrict__ p,
                                                                const float* __restrict__ f,
                                                                const float* __restrict__ w,
                                                                const uint32_t* __restrict__ bits,
                                                                const int32_t* __restrict__ nbr, size_t pstride,
-                                                               int n_blocks, double lam, double* partials) {
+                                                               int n_blocks, double lam,
+                                                               const double* __restrict__ inv2lw, double* partials) {
     __shared__ Tiles s;
     __shared__ double red[2][kSweepThreads / 32];
     const int t = threadIdx.x;
@@ -1520,9 +1533,10 @@ __global__ void __launch_bounds__(kSweepThreads) energy_kernel(const T* __restri
                 }
             }
             const size_t v = (size_t)b * kBlockVoxels + t;
-            const double fv = f[v], wv = w[v];
+            const float wf = w[v];
+            const double fv = f[v], wv = wf;
             const double r = u0 - fv;
-            accP += sqrt(tv2) + 0.5 * lam * wv * r * r;
+            accP += energy_sqrt(tv2) + 0.5 * lam * wv * r * r;
             const int q = t9(lx, ly, lz);
             const int pstep[3] = {1, kPTile, kPTile * kPTile};
             double dv = 0.0;
@@ -1532,7 +1546,11 @@ __global__ void __launch_bounds__(kSweepThreads) energy_kernel(const T* __restri
                 const double back = s.om[c - step[a]] ? (double)s.p[a][q - pstep[a]] : 0.0;
                 dv += own - back;
             }
-            accD += -fv * dv - dv * dv / (2.0 * lam * wv);
+            // 1/(2 lambda w) from the table for integer counts (the fusion's weights), else divided
+            const int wi = (int)wf;
+            const double inv = ((float)wi == wf && wi >= 1 && wi <= kInvWeights) ? __ldg(inv2lw + wi - 1)
+                                                                                 : 1.0 / (2.0 * lam * wv);
+            accD += -fv * dv - dv * dv * inv;
         }
         __syncthreads();
     }
@@ -1756,7 +1774,8 @@ void energy_t(denser_ctx* c, int64_t nb, cudaStream_t s) {
     const int cur = c->cur;
     energy_kernel<T><<<kEnergyGrid, kSweepThreads, 0, s>>>(
         (const T*)c->d.u, (const T*)c->d.p[cur], c->d.f, c->d.w, c->d.omega_bits, c->d.nbr,
-        (size_t)c->d.max_blocks * kBlockVoxels, (int)nb, c->prm.lambda, c->d.partials);
+        (size_t)c->d.max_blocks * kBlockVoxels, (int)nb, c->prm.lambda, c->d.partials + 2 * kEnergyGrid + 2,
+        c->d.partials);
     energy_final_kernel<<<1, 1024, 0, s>>>(c->d.partials, kEnergyGrid);
 }
 
