@@ -204,10 +204,18 @@ __global__ void __launch_bounds__(1024) surface_scan_kernel(const DeviceMap m, c
     __shared__ long long part[1024];
     const int nb = m.counters[kNumBlocks];
     const int t = threadIdx.x;
-    const int chunk = (nb + 1023) / 1024;
+    // chunks of a multiple of 4 counts, read as int4 (counts is 16-byte aligned)
+    const int chunk = ((nb + 1023) / 1024 + 3) & ~3;
     const int lo = min(nb, t * chunk), hi = min(nb, lo + chunk);
     long long s = 0;
-    for (int i = lo; i < hi; ++i) s += counts[i];
+    {
+        int i = lo;
+        for (; i + 4 <= hi; i += 4) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(counts + i));
+            s += (long long)v.x + v.y + v.z + v.w;
+        }
+        for (; i < hi; ++i) s += counts[i];
+    }
     part[t] = s;
     __syncthreads();
     for (int d = 1; d < 1024; d <<= 1) {  // Hillis-Steele inclusive scan
@@ -266,6 +274,16 @@ __device__ __forceinline__ int tet_edges(unsigned m4, int sg, int e[2][3][2]) {
     return 2;
 }
 
+// Element i (0..7) of an array held in registers (selects, so that a runtime index does
+// not send the array to local memory).
+template <typename V>
+__device__ __forceinline__ V pick8(const V (&v)[8], int i) {
+    V r = v[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) r = i == k ? v[k] : r;
+    return r;
+}
+
 // Emit pass: one thread per listed cube.  It reads the cube's eight corner values
 // (from the block and its upper neighbours), and writes the triangles of its six
 // tetrahedra from the block's first triangle plus the cube's offset.
@@ -313,7 +331,8 @@ __global__ void __launch_bounds__(64) surface_emit_kernel(DeviceMap m, const T* 
             const unsigned m4 = tet_mask(neg8, q);
             const int k = __popc(m4);
             if (k == 0 || k == 4) continue;
-            const int code[4] = {0, kTetC1[q], kTetC2[q], 7};
+            const int c1 = kTetC1[q], c2 = kTetC2[q];
+            auto code = [&](int j) { return j == 0 ? 0 : (j == 1 ? c1 : (j == 2 ? c2 : 7)); };
             int e[2][3][2];
             const int ntri = tet_edges(m4, kTetSign[q], e);
 #pragma unroll
@@ -325,14 +344,14 @@ __global__ void __launch_bounds__(64) surface_emit_kernel(DeviceMap m, const T* 
 #pragma unroll
                     for (int v = 0; v < 3; ++v) {
                         // the vertex on the edge from corner ca (the lower end) to cb
-                        const int ca = code[e[tr][v][0]], cb = code[e[tr][v][1]];
+                        const int ca = code(e[tr][v][0]), cb = code(e[tr][v][1]);
                         const int dir = ca ^ cb;
-                        const float ua = cu[ca], ub = cu[cb];
+                        const float ua = pick8(cu, ca), ub = pick8(cu, cb);
                         const float tt = ua / (ua - ub);
                         pos[3 * v + 0] = (gx + (float)(ca & 1) + ((dir & 1) ? tt : 0.0f)) * s;
                         pos[3 * v + 1] = (gy + (float)((ca >> 1) & 1) + ((dir & 2) ? tt : 0.0f)) * s;
                         pos[3 * v + 2] = (gz + (float)((ca >> 2) & 1) + ((dir & 4) ? tt : 0.0f)) * s;
-                        id[v] = flat[ca] * 8 + dir;
+                        id[v] = pick8(flat, ca) * 8 + dir;
                     }
                     if (tri_pos) {
                         float* dst = tri_pos + out * 9;
@@ -371,8 +390,10 @@ int surface_launch(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long lon
             c->launches += 1;
         }
     } else {
-        // the count still on the device: 16 CTAs of 64 threads per SM stride over it
-        surface_emit_kernel<T><<<c->sm_count * 16, 64, 0, s>>>(
+        // the count still on the device: one thread per entry of the list's capacity (the
+        // threads past the count return at once), so that every listed cube starts at once
+        const long long grid = std::max<long long>(1, std::min<long long>((c->surf_list_cap + 63) / 64, 1ll << 30));
+        surface_emit_kernel<T><<<(unsigned)grid, 64, 0, s>>>(
             c->d, (const T*)c->d.u, c->surf_up, c->surf_list, 0, c->surf_cursor, c->surf_list_cap, c->surf_offsets,
             (float)c->prm.voxel_size, capacity, tri_pos, tri_ids);
         c->launches += 1;
