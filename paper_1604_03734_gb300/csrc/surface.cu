@@ -274,22 +274,25 @@ __device__ __forceinline__ int tet_edges(unsigned m4, int sg, int e[2][3][2]) {
     return 2;
 }
 
-// Element i (0..7) of an array held in registers (selects, so that a runtime index does
-// not send the array to local memory).
-template <typename V>
-__device__ __forceinline__ V pick8(const V (&v)[8], int i) {
-    V r = v[0];
-#pragma unroll
-    for (int k = 1; k < 8; ++k) r = i == k ? v[k] : r;
-    return r;
-}
+// A listed cube's data, staged per lane of a warp for the emit pass.
+struct EmitCube {
+    float cu[8];         // u at the eight corners
+    long long flat[8];   // flat voxel index of each corner
+    float g[3];          // voxel-unit position of corner 0 (+ 1/2)
+    unsigned neg8;       // negative-corner mask
+    long long out0;      // output index of the cube's first triangle
+};
 
-// Emit pass: one thread per listed cube.  It reads the cube's eight corner values
-// (from the block and its upper neighbours), and writes the triangles of its six
-// tetrahedra from the block's first triangle plus the cube's offset.
-// With n_items_dev, the count is read on the device (the count pass queued just before),
-// and nothing is written when the list overflowed (more than list_cap cubes: the host
-// then grows the list and runs both passes again).
+// Emit pass, one warp per 32 listed cubes.  Each lane reads its cube (eight corner
+// values, from the block and its upper neighbours) and counts its triangles; then the
+// warp's triangles, in output order, are dealt out one per lane: each lane computes one
+// triangle of whichever cube holds it (from the staged cube data) into a shared-memory
+// slot, and the warp writes the slots back as consecutive words, so that triangles that
+// are consecutive in the output (a block's cubes are) go out in whole sectors.  The
+// triangles of a cube come from its six tetrahedra in order, from the block's first
+// triangle plus the cube's offset.  With n_items_dev, the count is read on the device
+// (the count pass queued just before), and nothing is written when the list overflowed
+// (more than list_cap cubes: the host then grows the list and runs both passes again).
 template <typename T>
 __global__ void __launch_bounds__(64) surface_emit_kernel(DeviceMap m, const T* __restrict__ u,
                                                            const int32_t* __restrict__ up,
@@ -299,73 +302,121 @@ __global__ void __launch_bounds__(64) surface_emit_kernel(DeviceMap m, const T* 
                                                            long long list_cap, const long long* __restrict__ offsets,
                                                            float s, long long capacity, float* __restrict__ tri_pos,
                                                            long long* __restrict__ tri_ids) {
+    __shared__ EmitCube cubes[2][32];
+    __shared__ int first[2][33];          // prefix sums of the lanes' triangle counts
+    __shared__ float spos[2][32 * 9];
+    __shared__ long long sids[2][32 * 3];
+    __shared__ long long sout[2][32];
     if (n_items_dev) {
         n_items = (long long)*n_items_dev;
         if (n_items > list_cap) return;
     }
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < n_items;
-         it += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long w = list[it];
-        const int b = (int)(w >> 32);
-        const int l = (int)((w >> 23) & 511u);
-        const unsigned neg8 = (unsigned)((w >> 15) & 255u);
-        long long out = offsets[b] + (long long)(w & 32767u);
-        const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-        const int4 key = reinterpret_cast<const int4*>(m.coords)[b];
-        const int4 u0 = __ldg(reinterpret_cast<const int4*>(up) + 2 * (size_t)b);
-        const int4 u1 = __ldg(reinterpret_cast<const int4*>(up) + 2 * (size_t)b + 1);
-        const int nbk[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-        float cu[8];
-        long long flat[8];
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    EmitCube* cb = cubes[wp];
+    for (long long base = ((long long)blockIdx.x * 2 + wp) * 32; base < n_items; base += (long long)gridDim.x * 64) {
+        const long long it = base + lane;
+        int ntri = 0;
+        if (it < n_items) {
+            const unsigned long long w = list[it];
+            const int b = (int)(w >> 32);
+            const int l = (int)((w >> 23) & 511u);
+            const unsigned neg8 = (unsigned)((w >> 15) & 255u);
+            const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+            const int4 key = reinterpret_cast<const int4*>(m.coords)[b];
+            const int4 u0 = __ldg(reinterpret_cast<const int4*>(up) + 2 * (size_t)b);
+            const int4 u1 = __ldg(reinterpret_cast<const int4*>(up) + 2 * (size_t)b + 1);
+            EmitCube& c = cb[lane];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int ox = lx + (c & 1), oy = ly + ((c >> 1) & 1), oz = lz + ((c >> 2) & 1);
-            flat[c] = (long long)nbk[(ox >> 3) | ((oy >> 3) << 1) | ((oz >> 3) << 2)] * kBlockVoxels + (ox & 7) +
-                      8 * (oy & 7) + 64 * (oz & 7);
-            cu[c] = Store<T>::ld(u + flat[c]);
-        }
-        const float gx = (float)(8 * key.y + lx) + 0.5f, gy = (float)(8 * key.z + ly) + 0.5f,
-                    gz = (float)(8 * key.w + lz) + 0.5f;
-#pragma unroll 1
-        for (int q = 0; q < 6; ++q) {
-            const unsigned m4 = tet_mask(neg8, q);
-            const int k = __popc(m4);
-            if (k == 0 || k == 4) continue;
-            const int c1 = kTetC1[q], c2 = kTetC2[q];
-            auto code = [&](int j) { return j == 0 ? 0 : (j == 1 ? c1 : (j == 2 ? c2 : 7)); };
-            int e[2][3][2];
-            const int ntri = tet_edges(m4, kTetSign[q], e);
-#pragma unroll
-            for (int tr = 0; tr < 2; ++tr) {
-                if (tr >= ntri) continue;
-                if (out < capacity) {
-                    float pos[9];
-                    long long id[3];
-#pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        // the vertex on the edge from corner ca (the lower end) to cb
-                        const int ca = code(e[tr][v][0]), cb = code(e[tr][v][1]);
-                        const int dir = ca ^ cb;
-                        const float ua = pick8(cu, ca), ub = pick8(cu, cb);
-                        const float tt = ua / (ua - ub);
-                        pos[3 * v + 0] = (gx + (float)(ca & 1) + ((dir & 1) ? tt : 0.0f)) * s;
-                        pos[3 * v + 1] = (gy + (float)((ca >> 1) & 1) + ((dir & 2) ? tt : 0.0f)) * s;
-                        pos[3 * v + 2] = (gz + (float)((ca >> 2) & 1) + ((dir & 4) ? tt : 0.0f)) * s;
-                        id[v] = pick8(flat, ca) * 8 + dir;
-                    }
-                    if (tri_pos) {
-                        float* dst = tri_pos + out * 9;
-#pragma unroll
-                        for (int v = 0; v < 9; ++v) dst[v] = pos[v];
-                    }
-                    if (tri_ids) {
-                        long long* dst = tri_ids + out * 3;
-                        dst[0] = id[0], dst[1] = id[1], dst[2] = id[2];
-                    }
-                }
-                ++out;
+            for (int k = 0; k < 8; ++k) {
+                const int ox = lx + (k & 1), oy = ly + ((k >> 1) & 1), oz = lz + ((k >> 2) & 1);
+                // the corner's block: the cube's own or one of its upper neighbours (selects,
+                // so that the runtime index keeps the row in registers)
+                const int sel = (ox >> 3) | ((oy >> 3) << 1) | ((oz >> 3) << 2);
+                const int nk = sel < 4 ? (sel < 2 ? (sel ? u0.y : u0.x) : (sel == 2 ? u0.z : u0.w))
+                                       : (sel < 6 ? (sel == 4 ? u1.x : u1.y) : (sel == 6 ? u1.z : u1.w));
+                const long long f = (long long)nk * kBlockVoxels + (ox & 7) + 8 * (oy & 7) + 64 * (oz & 7);
+                c.flat[k] = f;
+                c.cu[k] = Store<T>::ld(u + f);
             }
+            c.g[0] = (float)(8 * key.y + lx) + 0.5f;
+            c.g[1] = (float)(8 * key.z + ly) + 0.5f;
+            c.g[2] = (float)(8 * key.w + lz) + 0.5f;
+            c.neg8 = neg8;
+            c.out0 = offsets[b] + (long long)(w & 32767u);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) ntri += tet_tris(tet_mask(neg8, q));
         }
+        // exclusive prefix of the lanes' counts
+        int inc = ntri;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        first[wp][lane + 1] = inc;
+        if (lane == 0) first[wp][0] = 0;
+        const int total = __shfl_sync(0xffffffffu, inc, 31);
+        __syncwarp();
+        for (int j0 = 0; j0 < total; j0 += 32) {
+            const int j = j0 + lane;
+            const int cnt = min(32, total - j0);
+            if (j < total) {
+                // the cube holding the warp's triangle j, and which of its triangles
+                int lo = 0, hi = 31;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (first[wp][mid] <= j) lo = mid;
+                    else hi = mid - 1;
+                }
+                const EmitCube& c = cb[lo];
+                int r = j - first[wp][lo];
+                const long long out = c.out0 + r;
+                int q = 0, tr = 0;
+#pragma unroll 1
+                for (; q < 6; ++q) {
+                    const int k = tet_tris(tet_mask(c.neg8, q));
+                    if (r < k) {
+                        tr = r;
+                        break;
+                    }
+                    r -= k;
+                }
+                const unsigned m4 = tet_mask(c.neg8, q);
+                const int c1 = kTetC1[q], c2 = kTetC2[q];
+                auto code = [&](int jj) { return jj == 0 ? 0 : (jj == 1 ? c1 : (jj == 2 ? c2 : 7)); };
+                int e[2][3][2];
+                tet_edges(m4, kTetSign[q], e);
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    // the vertex on the edge from corner ca (the lower end) to cb
+                    const int ca = code(tr ? e[1][v][0] : e[0][v][0]), cbn = code(tr ? e[1][v][1] : e[0][v][1]);
+                    const int dir = ca ^ cbn;
+                    const float ua = c.cu[ca], ub = c.cu[cbn];
+                    const float tt = ua / (ua - ub);
+                    spos[wp][9 * lane + 3 * v + 0] = (c.g[0] + (float)(ca & 1) + ((dir & 1) ? tt : 0.0f)) * s;
+                    spos[wp][9 * lane + 3 * v + 1] = (c.g[1] + (float)((ca >> 1) & 1) + ((dir & 2) ? tt : 0.0f)) * s;
+                    spos[wp][9 * lane + 3 * v + 2] = (c.g[2] + (float)((ca >> 2) & 1) + ((dir & 4) ? tt : 0.0f)) * s;
+                    sids[wp][3 * lane + v] = c.flat[ca] * 8 + dir;
+                }
+                sout[wp][lane] = out;
+            }
+            __syncwarp();
+            // consecutive words of the staged triangles to their output places
+            if (tri_pos)
+                for (int wd = lane; wd < 9 * cnt; wd += 32) {
+                    const int t = wd / 9;
+                    const long long o = sout[wp][t];
+                    if (o < capacity) tri_pos[o * 9 + (wd - 9 * t)] = spos[wp][wd];
+                }
+            if (tri_ids)
+                for (int wd = lane; wd < 3 * cnt; wd += 32) {
+                    const int t = wd / 3;
+                    const long long o = sout[wp][t];
+                    if (o < capacity) tri_ids[o * 3 + (wd - 3 * t)] = sids[wp][wd];
+                }
+            __syncwarp();
+        }
+        __syncwarp();  // the staged cubes are rewritten for the next 32
     }
 }
 
@@ -384,14 +435,14 @@ int surface_launch(denser_ctx* c, int64_t nb, int pass, float* tri_pos, long lon
         const long long n_items = c->surf_items;
         if (n_items > 0) {
             // small CTAs: a few tens of thousands of listed cubes still spread over every SM
-            surface_emit_kernel<T><<<grid_for(c->sm_count, n_items, 64, 16), 64, 0, s>>>(
+            surface_emit_kernel<T><<<(unsigned)std::max<long long>(1, (n_items + 63) / 64), 64, 0, s>>>(
                 c->d, (const T*)c->d.u, c->surf_up, c->surf_list, n_items, nullptr, 0, c->surf_offsets,
                 (float)c->prm.voxel_size, capacity, tri_pos, tri_ids);
             c->launches += 1;
         }
     } else {
-        // the count still on the device: one thread per entry of the list's capacity (the
-        // threads past the count return at once), so that every listed cube starts at once
+        // the count still on the device: one warp per 32 entries of the list's capacity
+        // (the warps past the count return at once), so that every listed cube starts at once
         const long long grid = std::max<long long>(1, std::min<long long>((c->surf_list_cap + 63) / 64, 1ll << 30));
         surface_emit_kernel<T><<<(unsigned)grid, 64, 0, s>>>(
             c->d, (const T*)c->d.u, c->surf_up, c->surf_list, 0, c->surf_cursor, c->surf_list_cap, c->surf_offsets,
