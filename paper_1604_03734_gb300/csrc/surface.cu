@@ -113,19 +113,42 @@ __global__ void __launch_bounds__(kSurfThreads, 12) surface_count_kernel(DeviceM
         const int bn = b + gridDim.x;
         const int pre = (t < 8 && bn < nb) ? __ldg(up + 8 * (size_t)bn + t) : -1;
         __syncthreads();
-#pragma unroll
-        for (int i = t; i < kRegion; i += kSurfThreads) {
-            const int x = i % kR, y = (i / kR) % kR, z = i / (kR * kR);
-            const int nk = nbk[cur][(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
-            float uv = 0.0f;
-            unsigned char o = 0;
-            if (nk >= 0) {
-                const size_t v = (size_t)nk * kBlockVoxels + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
-                o = __ldg(m.w + v) > 0.0f;
-                uv = Store<T>::ld(u + v);
+        // the corner region: the block's own rows in halves of four voxels (one per thread,
+        // w as one 16-byte load), then 115 items for the upper faces and edges: the +x plane
+        // voxel by voxel, the +y and +z planes and the (+y,+z) edge in halves of rows, the
+        // (+x,+y) and (+x,+z) edges voxel by voxel, and the far corner
+        {
+            const int r = t >> 1, hx = 4 * (t & 1), y = r & 7, z = r >> 3;
+            const size_t v = (size_t)nbk[cur][0] * kBlockVoxels + hx + 8 * y + 64 * z;
+            const float4 w4 = __ldg(reinterpret_cast<const float4*>(m.w + v));
+            const int d = ridx(hx, y, z);
+            su[d] = Store<T>::ld(u + v), su[d + 1] = Store<T>::ld(u + v + 1);
+            su[d + 2] = Store<T>::ld(u + v + 2), su[d + 3] = Store<T>::ld(u + v + 3);
+            som[d] = w4.x > 0.0f, som[d + 1] = w4.y > 0.0f, som[d + 2] = w4.z > 0.0f, som[d + 3] = w4.w > 0.0f;
+        }
+        if (t < 115) {
+            // item -> first region voxel (x, y, z), source block (upper-neighbour code), count
+            int x, y, z, sel, n;
+            if (t < 64) x = 8, y = t & 7, z = t >> 3, sel = 1, n = 1;
+            else if (t < 80) x = 4 * (t & 1), y = 8, z = (t - 64) >> 1, sel = 2, n = 4;
+            else if (t < 96) x = 4 * (t & 1), y = (t - 80) >> 1, z = 8, sel = 4, n = 4;
+            else if (t < 104) x = 8, y = 8, z = t - 96, sel = 3, n = 1;
+            else if (t < 112) x = 8, y = t - 104, z = 8, sel = 5, n = 1;
+            else if (t < 114) x = 4 * (t & 1), y = 8, z = 8, sel = 6, n = 4;
+            else x = 8, y = 8, z = 8, sel = 7, n = 1;
+            const int nk = nbk[cur][sel];
+            const int d = ridx(x, y, z);
+            const size_t v = (size_t)(nk >= 0 ? nk : 0) * kBlockVoxels + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+            for (int k = 0; k < n; ++k) {
+                float uv = 0.0f;
+                unsigned char o = 0;
+                if (nk >= 0) {
+                    o = __ldg(m.w + v + k) > 0.0f;
+                    uv = Store<T>::ld(u + v + k);
+                }
+                su[d + k] = uv;
+                som[d + k] = o;
             }
-            su[i] = uv;
-            som[i] = o;
         }
         __syncthreads();
         // rows (y, z), (y+1, z), (y, z+1), (y+1, z+1) of x = lx0 .. lx0 + 4: 5-bit masks
@@ -196,40 +219,61 @@ __global__ void __launch_bounds__(kSurfThreads, 12) surface_count_kernel(DeviceM
     }
 }
 
-// offsets[b] = sum of counts[0..b); offsets[nb] = total.  One CTA of 1024 threads:
-// each thread sums a contiguous chunk, the CTA scans the chunk sums, each thread
-// writes its chunk's running sums.
+// offsets[b] = sum of counts[0..b); offsets[nb] = total.  One CTA of 1024 threads walks
+// the counts in tiles of 4096: each thread reads four consecutive counts (one 16-byte
+// load; counts is 16-byte aligned), the warps scan their 128 counts with shuffles, one
+// warp scans the 32 warp totals, and each thread writes its four offsets; the tile's
+// total carries into the next tile.
 __global__ void __launch_bounds__(1024) surface_scan_kernel(const DeviceMap m, const int32_t* __restrict__ counts,
                                                             long long* __restrict__ offsets) {
-    __shared__ long long part[1024];
+    __shared__ long long wsum[32];
+    __shared__ long long carry_s;
     const int nb = m.counters[kNumBlocks];
-    const int t = threadIdx.x;
-    // chunks of a multiple of 4 counts, read as int4 (counts is 16-byte aligned)
-    const int chunk = ((nb + 1023) / 1024 + 3) & ~3;
-    const int lo = min(nb, t * chunk), hi = min(nb, lo + chunk);
-    long long s = 0;
-    {
-        int i = lo;
-        for (; i + 4 <= hi; i += 4) {
-            const int4 v = __ldg(reinterpret_cast<const int4*>(counts + i));
-            s += (long long)v.x + v.y + v.z + v.w;
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    long long carry = 0;
+    for (int tile = 0; tile < nb; tile += 4096) {
+        const int i0 = tile + 4 * t;
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        if (i0 + 3 < nb) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(counts + i0));
+            c0 = v.x, c1 = v.y, c2 = v.z, c3 = v.w;
+        } else {
+            if (i0 < nb) c0 = counts[i0];
+            if (i0 + 1 < nb) c1 = counts[i0 + 1];
+            if (i0 + 2 < nb) c2 = counts[i0 + 2];
         }
-        for (; i < hi; ++i) s += counts[i];
-    }
-    part[t] = s;
-    __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {  // Hillis-Steele inclusive scan
-        const long long v = t >= d ? part[t - d] : 0;
+        const long long s4 = (long long)c0 + c1 + c2 + c3;
+        long long inc = s4;  // inclusive scan of the four-count sums within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) wsum[wp] = inc;
         __syncthreads();
-        part[t] += v;
+        if (wp == 0) {
+            long long w = wsum[lane], wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long v = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += v;
+            }
+            wsum[lane] = wi - w;  // exclusive over the warps
+            if (lane == 31) carry_s = wi;
+        }
         __syncthreads();
+        long long run = carry + wsum[wp] + inc - s4;  // offset of count i0
+        if (i0 < nb) offsets[i0] = run;
+        run += c0;
+        if (i0 + 1 < nb) offsets[i0 + 1] = run;
+        run += c1;
+        if (i0 + 2 < nb) offsets[i0 + 2] = run;
+        run += c2;
+        if (i0 + 3 < nb) offsets[i0 + 3] = run;
+        carry += carry_s;
+        __syncthreads();  // wsum and carry_s are rewritten by the next tile
     }
-    long long run = part[t] - s;
-    for (int i = lo; i < hi; ++i) {
-        offsets[i] = run;
-        run += counts[i];
-    }
-    if (t == 1023) offsets[nb] = part[1023];
+    if (t == 0) offsets[nb] = carry;
 }
 
 // The edges (i, j), i < j, of the triangles of a tetrahedron with negative-corner mask
