@@ -4,9 +4,11 @@ Census signatures are bit-exact.  a-step decisions (given the same d) equal the 
 oracle's on every pixel that is not a near tie (reading D8: the best candidate's
 energy is not within float32 rounding of another's); near ties are counted.  The tensor agrees to 1e-6 (float32 exp/sqrt against
 float64).  Primal-dual iterations from the same state agree to 1e-4 of the fields'
-scale after 200 iterations (float32 against float64).  The whole estimate, where the
-a-step's integer decisions follow d, is compared by statistics: median difference and
-the share of pixels more than 0.5 px apart, and against the generator's true disparity.
+scale after 200 iterations (float32 against float64).  The whole estimate is checked
+stage by stage, each stage from the GPU's own input to it, and the chain of stages ends
+on denser_stereo_estimate's result bit for bit; run end to end, where the a-step's
+integer decisions follow d, it is also compared by statistics (median difference, share
+of pixels more than 0.5 px apart) and against the generator's true disparity.
 """
 
 import numpy as np
@@ -119,6 +121,57 @@ def test_estimate_against_oracle_and_truth(tiny_pair):
     v = dt > 0
     err = np.abs(d_gpu - dt)[v]
     assert np.median(err) < 0.02 and (err > 3).mean() < 0.03
+
+
+def test_estimate_stagewise_against_oracle(tiny_pair):
+    """The whole estimate stage by stage, each stage against the oracle from the GPU's own
+    input to it: the winner-takes-all start, then per outer step the a-step (equal on every
+    pixel that is not a near tie) and the inner primal-dual iterations (within 1e-4 of the
+    field's scale).  The chain of C-ABI stage calls ends on denser_stereo_estimate's
+    result bit for bit, so the estimate itself is what the stages check."""
+    IL, IR, _, _ = tiny_pair
+    prm = N.denser_stereo_default_params(max_disp=32)
+    D, lam = prm.max_disp, float(prm.lambda_)
+    H, W = IR.shape
+    sL, sR = sig_dev(IL), sig_dev(IR)
+    cL, cR = S.census(IL), S.census(IR)
+    T = torch.zeros((3, H, W), device="cuda")
+    N.denser_diffusion_tensor(dev(IR), T, float(prm.gamma), float(prm.beta))
+    t = T.cpu().numpy().astype(np.float64)   # planes T11, T12 = T21, T22
+    T64 = np.stack([np.stack([t[0], t[1]]), np.stack([t[1], t[2]])])
+    a = torch.zeros((H, W), device="cuda")
+    N.denser_disparity_assign(sL, sR, D, lam, 0.0, torch.zeros((H, W), device="cuda"), a)
+    np.testing.assert_array_equal(a.cpu().numpy(), S.assign((cL, cR, D), np.zeros((H, W)), lam, np.inf))
+    state = torch.zeros((24, H, W), device="cuda")
+    state[0] = a
+    state[1] = a
+    theta = float(prm.theta0)
+    near_total = 0
+    for _ in range(prm.outer):
+        d = state[0].clone()
+        N.denser_disparity_assign(sL, sR, D, lam, theta, d, a)
+        ref, near = S.assign((cL, cR, D), d.cpu().numpy(), lam, theta, with_flags=True)
+        got = a.cpu().numpy()
+        np.testing.assert_array_equal(got[~near], ref.astype(np.float32)[~near])
+        near_total += int(near.sum())
+        # the inner iterations from the GPU's state and a-step
+        g = state.cpu().numpy().astype(np.float64)
+        st = S.TGVState(g[0])
+        st.d_bar = g[1].copy()
+        st.w = g[2:4].copy()
+        st.w_bar = g[4:6].copy()
+        st.p = g[6:8].copy()
+        st.q = g[8:12].reshape(2, 2, H, W).copy()
+        a64 = got.astype(np.float64)
+        S.tgv_iterate(st, a64, T64, theta, float(prm.alpha1), float(prm.alpha2), prm.inner)
+        N.denser_tgv_iterate(a, T, float(prm.alpha1), float(prm.alpha2), theta, prm.inner, state)
+        out = state.cpu().numpy().astype(np.float64)
+        scale = max(np.abs(a64).max(), 1.0)
+        assert np.max(np.abs(out[0] - st.d)) <= 1e-4 * scale
+        assert np.max(np.abs(out[2:4] - st.w)) <= 1e-4 * scale
+        theta *= float(prm.theta_decay)
+    assert near_total <= 1e-3 * prm.outer * H * W
+    np.testing.assert_array_equal(state[0].cpu().numpy(), run_gpu_estimate(IL, IR, max_disp=32).astype(np.float32))
 
 
 def test_fullsize_street_pair():
