@@ -310,7 +310,11 @@ int denser_regularize(denser_ctx* ctx, int32_t max_iters, double gap_tol, int32_
 /* FP64 primal and dual energies of the current state (waits for the stream):
  *   P(u) = sum_Omega |grad u|_2 + (lambda/2) sum_Omega w (u - f)^2
  *   D(p) = sum_Omega [ -f div p - (div p)^2 / (2 lambda w) ]
- * primal, dual: host pointers (either may be NULL). */
+ * (Section III-B, Eq. 2 with the weighting of the update, and its dual).  Sums and
+ * terms in float64; each |grad u|_2 is a float32 reciprocal square root refined by one
+ * float64 Heron step (relative error below 2^-40), and 1/(2 lambda w) for integer counts
+ * w <= 4096 comes from a table of float64 quotients.  primal, dual: host pointers
+ * (either may be NULL). */
 int denser_energy(denser_ctx* ctx, double* primal, double* dual, void* stream);
 
 /* Copies the map out in block-index order (waits for the stream).  Any output may
