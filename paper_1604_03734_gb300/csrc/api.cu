@@ -287,7 +287,7 @@ int denser_create(const denser_params* prm, int32_t device, denser_ctx** out) {
     // the row sweep with balanced face items and asynchronous halos, 10 CTAs per SM,
     // blocks in index order: the autotuner's pick for every storage type on the 1 km
     // street (for 16-bit storage, halos through registers are 2% faster on the 100 m
-    // street but 12-17% slower there)
+    // street but 12-17% slower on the 1 km one)
     c->sched.sweep_kernel = 7;
     c->sched.order = 0;
     c->sched.ctas_per_sm = 2;
