@@ -1,5 +1,5 @@
-"""Host logic of bench.py that needs no GPU: the clock sampler's window and the
-roofline traffic lookup."""
+"""Host logic of bench.py that needs no GPU: the clock sampler's window, the
+roofline traffic lookup and the reference arm's line."""
 
 import datetime
 import json
@@ -61,3 +61,22 @@ def test_traffic_lookup_follows_kernel_workload_and_schedule():
     assert bench.measured_traffic("sweep_rows_kernel", 1, nvox, sch) is None  # another storage type
     other = dict(sch, ctas_per_sm=0)
     assert bench.measured_traffic("sweep_rows_kernel", 0, nvox, other) is None  # another schedule
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the C FP64 oracle on the host cores) prints one JSON
+    line with the keys the driver reads: impl, value, the e2e block with no copies and a
+    cpu_baseline describing the same run."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "voxel-updates/s" and d["dtype"] == "f64" and d["steps"] == 1 and d["n_gpus"] == 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["config"]["workload"] == bench.WORKLOAD
