@@ -9,8 +9,10 @@
   along grad I, 1 across;
 * the a-step: no coupling is the first argmin of the cost (numpy), strong coupling
   rounds d to the nearest integer (ties to the smaller);
+* the a-step's switching point between two candidates against its closed form;
 * the d-step converges to the minimiser of the same convex problem solved as a
-  quadratic programme by scipy (SLSQP) on a two-row image;
+  quadratic programme by scipy (trust-constr) on a two-row image, and its iterates keep the
+  contraction properties of Chambolle-Pock with over-relaxation 1 in the method's metric;
 * the whole estimate recovers an exact integer shift, and the synthetic street pair's
   true disparity (generator geometry) to sub-pixel median error.
 """
@@ -103,6 +105,71 @@ def test_assign_limits():
     d = np.array([[3.2, 7.5, 0.49, 12.51, 18.0]])
     hz = np.zeros((20, 1, 5), dtype=np.int64)
     np.testing.assert_array_equal(S.assign(hz, d, 0.5, 1e-3), [[3, 7, 0, 13, 18]])
+
+
+def test_assign_switching_point_closed_form():
+    """Two candidates, delta = 0 with Hamming cost h0 and delta = 1 with h1: by D5 the
+    a-step moves to 1 exactly when (d^2 - (d - 1)^2) / (2 theta) > lam (h1 - h0) / 62,
+    i.e. above d* = 1/2 + theta lam (h1 - h0) / 62 (worked out by hand from D5's energy,
+    which fixes the factor 1/(2 theta) of the coupling)."""
+    lam = 0.5
+    cases = [(2.0, 31), (0.5, 62), (1.0, 12), (4.0, -20), (0.25, 0)]  # theta, h1 - h0
+    for theta, dh in cases:
+        h0 = 30
+        h = np.array([[[h0, h0]], [[h0 + dh, h0 + dh]]], dtype=np.int64)  # [D = 2, 1, 2]
+        d_star = 0.5 + theta * lam * dh / S.BITS
+        d = np.array([[d_star - 1e-3, d_star + 1e-3]])
+        a, flag = S.assign(h, d, lam, theta, with_flags=True)
+        np.testing.assert_array_equal(a, [[0.0, 1.0]], err_msg=str((theta, dh)))
+        assert not flag.any()
+
+
+def test_tgv_steps_shrink_in_the_primal_dual_metric():
+    """D6 is Chambolle-Pock with over-relaxation 1: with x = (d, w) and y = (p, q), the
+    pairs v_k = (x_k, y_{k+1}) follow a proximal-point iteration in the metric
+    M = [[I/tau, -K^T], [-K, I/sigma]], positive semidefinite since sigma tau ||K||^2 <= 1
+    (He and Yuan's reading of the method).  Its resolvent is firmly nonexpansive in M, so
+    the step lengths |v_{k+1} - v_k|_M never grow, checked with the ball constraints
+    active (small alpha1, alpha2) on random data; and the distance |v_k - v*|_M to any
+    saddle point v* never grows, checked where v* = 0 is one: no data term (theta
+    infinite) and balls too large to bind.  Leaving out the over-relaxation of d or of w
+    makes the distance grow in the second case."""
+    tau = sigma = 1.0 / np.sqrt(12.0)
+    for seed in range(3):
+        rng = np.random.default_rng(40 + seed)
+        H, W = 5, 6
+        T = S.diffusion_tensor(rng.random((H, W)), 4.0, 1.0)
+        a = rng.random((H, W)) * 5.0
+        st = S.TGVState(rng.random((H, W)) * 5.0)
+        xs, ys = [(st.d.copy(), st.w.copy())], []
+        for _ in range(200):
+            S.tgv_iterate(st, a, T, 0.7, 0.05, 0.1, 1)
+            xs.append((st.d.copy(), st.w.copy()))
+            ys.append((st.p.copy(), st.q.copy()))
+
+        def m_norm2(dd, dw, dp, dq):
+            r = S.apply_T(T, S.grad(dd)) - dw
+            gw = np.stack([S.grad(dw[0]), S.grad(dw[1])])
+            return ((np.sum(dd * dd) + np.sum(dw * dw)) / tau + (np.sum(dp * dp) + np.sum(dq * dq)) / sigma
+                    - 2.0 * (np.sum(r * dp) + np.sum(gw * dq)))
+
+        steps = np.array([m_norm2(xs[k + 1][0] - xs[k][0], xs[k + 1][1] - xs[k][1],
+                                  ys[k + 1][0] - ys[k][0], ys[k + 1][1] - ys[k][1]) for k in range(len(ys) - 1)])
+        assert np.all(steps >= -1e-12), steps.min()
+        assert np.all(steps[1:] <= steps[:-1] * (1.0 + 1e-9) + 1e-18), np.max(steps[1:] / steps[:-1])
+        assert steps[-1] < 1e-3 * steps[0]
+
+        # the bilinear case: (d, w, p, q) = 0 is a saddle point
+        st = S.TGVState(rng.standard_normal((H, W)))
+        zero = np.zeros((H, W))
+        x_prev = (st.d.copy(), st.w.copy())
+        dist = []
+        for _ in range(300):
+            S.tgv_iterate(st, zero, T, np.inf, 1e12, 1e12, 1)
+            dist.append(m_norm2(x_prev[0], x_prev[1], st.p, st.q))  # v_k = (x_k, y_{k+1})
+            x_prev = (st.d.copy(), st.w.copy())
+        dist = np.array(dist)
+        assert np.all(dist[1:] <= dist[:-1] * (1.0 + 1e-9)), np.max(dist[1:] / dist[:-1])
 
 
 def qp_tgv_1d(a, theta, alpha1, alpha2):
