@@ -80,6 +80,23 @@ def test_rotated_camera_segment_and_wide_band_equal_numpy():
     _same_map(m.snapshot(), g)
 
 
+
+def test_fuse_into_one_of_two_segments_equals_numpy():
+    """The same blocks in segments 0 and 3; a depth map fused into segment 3 leaves
+    segment 0 untouched, as in the numpy oracle."""
+    s = tiny_scene(seed=1, n_frames=1)
+    d = s.depth_maps()
+    K = intrinsics_of(s.camera)
+    g = O.SparseGrid(P)
+    O.alloc_blocks(g, d[0], K, s.poses[0], 3)
+    keys = [(0,) + tuple(k[1:]) for k in g.keys] + list(g.keys)
+    both = grid_from_blocks(keys)
+    m = cmap_of(both)
+    O.fuse_depth(both, d[0], K, s.poses[0], 3)
+    m.fuse_depth(d[0], K, s.poses[0], 3)
+    _same_map(m.snapshot(), both, state=False)
+    assert np.all(both.w[:g.n_blocks] == 0) and np.count_nonzero(both.w) > 100
+
 def test_street_frames_equal_numpy():
     s = street_scene(seed=0)
     d = s.depth_maps(range(2))

@@ -220,3 +220,42 @@ def test_alloc_block_order_is_sorted_per_call():
     keys = [(k[0], k[3], k[2], k[1]) for k in g.keys]
     assert n == len(keys) and keys == sorted(keys)
     assert len(set(g.keys)) == n
+
+
+def test_fuse_invalid_depths_update_nothing():
+    """Pixels whose depth is not a finite positive number carry no observation: voxels
+    just in front of the camera (z_c below mu, where a depth of 0 would pass Eq. 1's
+    truncation test) stay unobserved under a map of zeros, negatives, NaN and infinities."""
+    K = Intrinsics(60.0, 60.0, 20.137, 15.291, 40, 30)
+    T = _pose(np.eye(3), (0.0123, 0.0071, 0.0037))
+    g = SparseGrid(P)
+    g.add_blocks([(0, bx, by, 0) for by in (-1, 0) for bx in (-1, 0)])
+    depth = np.zeros((K.height, K.width), np.float32)
+    depth[::3] = -1.0
+    depth[1::5] = np.nan
+    depth[:, ::7] = np.inf
+    depth[2::6, 1::4] = -0.0
+    mask = fuse_depth(g, depth, K, T)
+    assert not mask.any() and np.all(g.w == 0) and np.all(g.f == 0)
+    # the same blocks do see a valid map: the voxels in front of the camera are reachable
+    fuse_depth(g, np.full((K.height, K.width), 0.5, np.float32), K, T)
+    assert np.count_nonzero(g.w) > 40
+
+
+def test_fuse_touches_its_own_segment_only():
+    """Segments are separate maps that share the hash: a depth map fused into segment 1
+    leaves segment 0's blocks at the same coordinates untouched, and gives segment 1
+    what a map holding only those blocks gets."""
+    K = Intrinsics(60.0, 60.0, 20.137, 15.291, 40, 30)
+    T = _pose(_rot(0.05, -0.1, 0.02), (0.0123, 0.0071, 0.0037))
+    depth = np.random.default_rng(7).uniform(2.0, 4.0, (K.height, K.width)).astype(np.float32)
+    alone = SparseGrid(P)
+    alloc_blocks(alone, depth, K, T, segment=1)
+    both = SparseGrid(P)
+    both.add_blocks([(0,) + tuple(k[1:]) for k in alone.keys] + list(alone.keys))
+    fuse_depth(alone, depth, K, T, segment=1)
+    fuse_depth(both, depth, K, T, segment=1)
+    n = alone.n_blocks
+    assert np.all(both.w[:n] == 0) and np.all(both.f[:n] == 0)
+    assert np.array_equal(both.w[n:], alone.w) and np.array_equal(both.f[n:], alone.f)
+    assert np.count_nonzero(alone.w) > 1000

@@ -169,6 +169,11 @@ def test_allocation_band_axis_aligned():
         expect = {(0, int(np.floor(t[0] / bs)), int(np.floor(t[1] / bs)), bz)
                   for bz in range(int(np.floor(z_lo / bs)), int(np.floor(z_hi / bs)) + 1)}
         assert keys == expect, r
+    # a point closer than mu: band samples at or behind the sensor (rho <= 0) allocate
+    # nothing, so the block just behind the sensor (z < 0, the sensor at z = 0.0037) is
+    # not taken
+    keys = L.scan_block_keys(np.array([[0.0, 0.0, 0.1]], np.float32), T0, p)
+    assert keys == {(0, 0, 0, 0)}
     r = 5.4321
     rr = float(np.float32(r))
     keys = L.scan_block_keys(np.array([[0.0, 0.0, r]], np.float32), T0, p)

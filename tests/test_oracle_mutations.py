@@ -11,6 +11,10 @@ process (compiled from the changed text and installed under the oracle's module 
 before the pins are imported); a changed C oracle is written to a temporary directory
 and built into a library of its own there.  Every case states, as its reason, which
 part of the paper or of a stated reading the change breaks.
+
+Changes that leave the method's result as it is are not cases: taking the other
+diagonal of a surface quadrilateral, say, meshes the same plane (u is linear on each
+tetrahedron), and updating u on Omega-bar changes nothing there (w = 0 and div p = 0).
 """
 
 import os
@@ -214,6 +218,77 @@ CASES = [
     ("inner-divergence-sign", PY_NET, "out = out + (q[a] - back)", "out = out + (q[a] + back)", "Eq. 4"),
     ("loss-div-gradient", PY_NET, "(rd - nxt.reshape(-1, 512))", "(rd + nxt.reshape(-1, 512))",
      "adjoint of the inner divergence"),
+    # ------------------------------------------------------------------ a second pass
+    ("alloc-band-count", PY_DENSER, "return int(math.ceil(params.mu / h - 1e-9))",
+     "return int(math.floor(params.mu / h - 1e-9))", "reading R1: the band covers [d - mu, d + mu]"),
+    ("alloc-zero-depth", PY_DENSER, "valid = np.isfinite(d32) & (d32 > 0)", "valid = np.isfinite(d32)",
+     "invalid pixels allocate nothing"),
+    ("fuse-zero-depth", PY_DENSER, "valid = inside & np.isfinite(d) & (d > 0)", "valid = inside & np.isfinite(d)",
+     "invalid pixels fuse nothing"),
+    ("fuse-image-edge", PY_DENSER, "inside = front & (pxf >= 0) & (pxf < W)", "inside = front & (pxf >= 1) & (pxf < W)",
+     "the first pixel column is in the image"),
+    ("fuse-other-segments", PY_DENSER, "sel = [b for b, k in enumerate(grid.keys) if k[0] == segment]",
+     "sel = [b for b, k in enumerate(grid.keys) if True]", "a depth map fuses into its own segment"),
+    ("voxel-layout-transposed", PY_DENSER, "return l % BLOCK, (l // BLOCK) % BLOCK, l // (BLOCK * BLOCK)",
+     "return l // (BLOCK * BLOCK), (l // BLOCK) % BLOCK, l % BLOCK", "voxel l = lx + 8 ly + 64 lz"),
+    ("neighbour-face-swapped", PY_DENSER, "edge = (loc[a] == (BLOCK - 1)) if sign > 0 else (loc[a] == 0)",
+     "edge = (loc[a] == 0) if sign > 0 else (loc[a] == (BLOCK - 1))", "which face a step leaves by"),
+    ("dual-norm-xy", PY_DENSER, "nrm = np.sqrt(pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2])",
+     "nrm = np.sqrt(pt[0] * pt[0] + pt[1] * pt[1])", "the 3-vector norm of p"),
+    ("warm-relaxed-state", PY_DENSER, "grid.u.reshape(-1).copy(), grid.u_bar.reshape(-1).copy()",
+     "grid.u.reshape(-1).copy(), grid.u.reshape(-1).copy()", "a warm start resumes the relaxed primal"),
+    ("c-inverse-rotation", C_DENSER, "Ri[3 * r + c] = T[4 * c + r];", "Ri[3 * r + c] = T[4 * r + c];",
+     "global-to-camera rotation R^T"),
+    ("c-inverse-translation", C_DENSER, "ti[r] = -((T[0 * 4 + r]", "ti[r] = ((T[0 * 4 + r]", "-R^T t"),
+    ("c-no-clamp", C_DENSER, "const double utsdf = q < 1.0 ? q : 1.0;", "const double utsdf = q;",
+     "u_TSDF = min(1, u_SDF / mu)"),
+    ("c-other-segments", C_DENSER, "if (k[0] != segment) continue;\n        double *fb",
+     "if (0) continue;\n        double *fb", "a depth map fuses into its own segment"),
+    ("c-pixel-round", C_DENSER, "const double pxf = floor((fx * xc) / zc + cx)", "const double pxf = round((fx * xc) / zc + cx)",
+     "pixel (x, y) covers [x, x + 1)"),
+    ("c-no-truncation-test", C_DENSER, "if (!(usdf >= -mu)) continue;", "if (!(usdf >= 0.0)) continue;",
+     "Eq. 1 observes down to -mu"),
+    ("c-dual-norm-xy", C_DENSER, "const double nrm = sqrt((q0 * q0 + q1 * q1) + q2 * q2);",
+     "const double nrm = sqrt(q0 * q0 + q1 * q1);", "the 3-vector norm of p"),
+    ("c-energy-tv-xy", C_DENSER, "const double tv = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);",
+     "const double tv = sqrt(g[0] * g[0] + g[1] * g[1]);", "isotropic TV over three axes"),
+    ("laser-range-limit", PY_LASER, "valid &= np.floor((r + params.mu) / (0.5 * params.voxel_size)) < 2.0 ** 22",
+     "valid &= np.isfinite(r)", "L1 range limit"),
+    ("laser-block-truncation", PY_LASER, "blk = v // BLOCK", "blk = (v / BLOCK).astype(np.int64)",
+     "block of a negative voxel index"),
+    ("laser-behind-sensor", PY_LASER, "ok = rho > 0", "ok = rho > -np.inf", "L2 samples behind the sensor"),
+    ("tensor-anisotropic-norm", PY_STEREO, "mag = np.sqrt(g[0] ** 2 + g[1] ** 2)", "mag = np.abs(g[0]) + np.abs(g[1])",
+     "D4 |grad I|"),
+    ("tensor-normal-swapped", PY_STEREO, "nx = np.where(mag > 0, g[0] / mag, 0.0)",
+     "nx = np.where(mag > 0, g[1] / mag, 0.0)", "D4 n = grad I / |grad I|"),
+    ("tgv-q-from-w", PY_STEREO, "gw = np.stack([grad(st.w_bar[0]), grad(st.w_bar[1])])",
+     "gw = np.stack([grad(st.w[0]), grad(st.w[1])])", "D6 the dual step reads the relaxed primal"),
+    ("tgv-p-w-sign", PY_STEREO, "p = st.p + sigma * (apply_T(T, grad(st.d_bar)) - st.w_bar)",
+     "p = st.p + sigma * (apply_T(T, grad(st.d_bar)) + st.w_bar)", "D6 K (d, w) = (T grad d - w, grad w)"),
+    ("estimate-theta-grows", PY_STEREO, "theta *= prm.theta_decay", "theta /= prm.theta_decay",
+     "D5 theta shrinks"),
+    ("estimate-no-wta-start", PY_STEREO, "d0 = assign(hvol, np.zeros(IR.shape), prm.lam, np.inf)",
+     "d0 = np.zeros(IR.shape)", "D5 start from the winner-takes-all disparity"),
+    ("census-mirrored", PY_STEREO, "nb = I[np.clip(ys + dy, 0, H - 1), np.clip(xs + dx, 0, W - 1)]",
+     "nb = I[np.clip(ys - dy, 0, H - 1), np.clip(xs - dx, 0, W - 1)]", "D2 bit order over the window"),
+    ("surface-perm-sign", PY_SURFACE, "return -1 if inv % 2 else 1", "return 1", "S2 orientation of odd tetrahedra"),
+    ("surface-edge-id", PY_SURFACE, "ti.append(a * 8 + (codes[j] ^ codes[i]))", "ti.append(a * 8 + codes[j])",
+     "S4 a vertex is named by its lattice edge"),
+    ("surface-corner-layout", PY_SURFACE,
+     "nl = (nx % BLOCK) + BLOCK * (ny % BLOCK) + BLOCK * BLOCK * (nz % BLOCK)",
+     "nl = (nz % BLOCK) + BLOCK * (ny % BLOCK) + BLOCK * BLOCK * (nx % BLOCK)", "voxel l = lx + 8 ly + 64 lz"),
+    ("net-unrounded-activations", PY_NET, "h = bf16(np.maximum(z, 0.0)) if li < len(params) - 1 else z",
+     "h = np.maximum(z, 0.0) if li < len(params) - 1 else z", "hidden activations stored as BF16"),
+    ("net-unrounded-weights", PY_NET, "z = conv3d_same(h, bf16(W), np.asarray(b, dtype=np.float64))",
+     "z = conv3d_same(h, W, np.asarray(b, dtype=np.float64))", "weights stored as BF16"),
+    ("gather-axes-swapped", PY_NET, "nb = index.get((seg, bx + ox, by + oy, bz + oz))",
+     "nb = index.get((seg, bx + oz, by + oy, bz + ox))", "the halo's neighbouring blocks"),
+    ("gather-weight-scale", PY_NET, "wv / (wv + 8.0)", "wv / (wv + 1.0)", "input channel w / (w + 8)"),
+    ("warm-components-reversed", PY_NET, "p = np.where(edges, o[:, 1:].transpose(1, 0, 2), 0.0)",
+     "p = np.where(edges, o[:, :0:-1].transpose(1, 0, 2), 0.0)", "outputs (u, p_x, p_y, p_z)"),
+    ("loss-unmasked", PY_NET, "d = (out - target) * mask", "d = out - target", "the loss counts Omega only"),
+    ("loss-div-unmasked-u", PY_NET, "ru = np.where(om, out[:, 0] - target[:, 0], 0.0)", "ru = out[:, 0] - target[:, 0]",
+     "the divergence loss counts Omega only"),
 ]
 
 RUNNER = r"""

@@ -157,6 +157,31 @@ def test_forward_stored_wiring_and_rounding():
         assert np.array_equal(h, NO.bf16(h))
 
 
+
+def test_forward_stored_rounding_closed_forms():
+    """Centre taps only, so every voxel runs the chain on its own value x; worked out by
+    hand: a last-layer weight 1 + 2^-9 is stored as 1 (2^-9 is below half an ulp of BF16
+    at 1, 2^-8), so x = 1 gives 1; an activation (1 + 2^-7)^2 = 1 + 2^-6 + 2^-14 is stored
+    as 1 + 2^-6; the last layer's output keeps every bit."""
+
+    def chain(w_first, w_last):
+        params = []
+        for li, (cin, cout) in enumerate(zip(NO.CHANNELS[:-1], NO.CHANNELS[1:])):
+            W = np.zeros((cout, cin, 3, 3, 3))
+            W[0, 0, 1, 1, 1] = w_first if li == 0 else (w_last if li == len(NO.CHANNELS) - 2 else 1.0)
+            params.append((W, np.zeros(cout)))
+        return params
+
+    def run(params, x):
+        xin = np.zeros((1, 2, 10, 10, 10))
+        xin[:, 0] = x
+        return NO.forward_stored(params, xin)[0, 0]
+
+    a = 1.0 + 2.0 ** -7
+    assert np.all(run(chain(1.0, 1.0 + 2.0 ** -9), 1.0) == 1.0)                 # weight rounded
+    assert np.all(run(chain(a, 1.0), a) == 1.0 + 2.0 ** -6)                     # activation rounded
+    assert np.all(run(chain(1.0, a), a) == 1.0 + 2.0 ** -6 + 2.0 ** -14)        # output kept
+
 def test_warm_state_masks_and_projection():
     rng = np.random.default_rng(23)
     n = 3
@@ -221,6 +246,13 @@ def test_loss_div_gradient_by_finite_differences():
         o2[i, c, l] -= h
         fd = (NO.loss_div(o1, tgt, 6.0, 2.0)[0] - NO.loss_div(o2, tgt, 6.0, 2.0)[0]) / (2 * h)
         assert abs(fd - g[i, c, l]) <= 1e-6 * max(1.0, abs(fd)), (i, c, l, fd, g[i, c, l])
+    # only Omega counts: outputs and targets off Omega change neither the loss nor the
+    # gradient, which is zero there for u
+    o3, t3 = out.copy(), tgt.copy()
+    o3[:, 0][~om] += rng.standard_normal((~om).sum())
+    t3[:, 0][~om] += 1.0
+    L3, g3 = NO.loss_div(o3, t3, 6.0, 2.0)
+    assert L3 == L and np.array_equal(g3, g) and np.all(g[:, 0][~om] == 0)
     # targets of the exact state give zero loss
     u, p = rng.uniform(-1, 1, (n, 512)), rng.standard_normal((3, n, 512))
     t = NO.targets_div(u, p, om)

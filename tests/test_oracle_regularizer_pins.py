@@ -419,3 +419,21 @@ def test_printed_primal_sign_does_not_converge():
     P2, D2 = energies(prob, u2, p2, P)
     assert (P1 - D1) / P1 < 1e-6
     assert (P2 - D2) / P2 > 1e-2
+
+
+def test_warm_resume_continues_bit_for_bit():
+    """A run split in two (the second part started from the stored u, u^ and p) is the
+    same iteration as one run of the summed length: the state that carries over is
+    (u, u^, p), the relaxed primal included (step 1 of Section III-C starts a run, the
+    steps that follow read only that state)."""
+    rng = np.random.default_rng(12)
+    keys = box_keys(2, 1, 1)
+    f, w = random_fw(rng, len(keys), p_omega=0.8)
+    whole = grid_from_blocks(keys, f, w)
+    regularize(whole, 50)
+    split = grid_from_blocks(keys, f, w)
+    regularize(split, 30)
+    regularize(split, 20, warm=True)
+    assert np.array_equal(whole.u, split.u) and np.array_equal(whole.u_bar, split.u_bar)
+    assert np.array_equal(whole.p, split.p)
+    assert not np.array_equal(split.u, split.u_bar)  # u^ differs from u mid-run
