@@ -201,3 +201,22 @@ def test_invalid_points_are_skipped():
     assert L.alloc_scan(O.SparseGrid(O.Params()), pts, T0) == 0
     cnt = L.fuse_scan(g, pts, T0)
     assert cnt.sum() == 0 and np.all(g.w == 0)
+
+
+def test_scan_touches_its_own_segment_and_orders_new_blocks():
+    """A scan fused into segment 2 leaves the same blocks of segment 0 untouched and gives
+    segment 2 what a map holding only those blocks gets; the blocks a scan allocates are
+    appended in ascending (segment, bz, by, bx) order."""
+    rng = np.random.default_rng(12)
+    pts = (rng.standard_normal((60, 3)) * np.array([1.5, 0.6, 0.4]) + np.array([0.0, 0.5, 4.0])).astype(np.float32)
+    T = T0.copy()
+    alone = O.SparseGrid(O.Params())
+    n = L.alloc_scan(alone, pts, T, segment=2)
+    keys = [(k[0], k[3], k[2], k[1]) for k in alone.keys]
+    assert n == len(keys) > 4 and keys == sorted(keys)
+    both = O.SparseGrid(O.Params())
+    both.add_blocks([(0,) + tuple(k[1:]) for k in alone.keys] + list(alone.keys))
+    L.fuse_scan(alone, pts, T, segment=2)
+    L.fuse_scan(both, pts, T, segment=2)
+    assert np.all(both.w[:n] == 0) and np.array_equal(both.w[n:], alone.w) and np.array_equal(both.f[n:], alone.f)
+    assert np.count_nonzero(alone.w) > 100

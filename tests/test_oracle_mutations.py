@@ -289,6 +289,35 @@ CASES = [
     ("loss-unmasked", PY_NET, "d = (out - target) * mask", "d = out - target", "the loss counts Omega only"),
     ("loss-div-unmasked-u", PY_NET, "ru = np.where(om, out[:, 0] - target[:, 0], 0.0)", "ru = out[:, 0] - target[:, 0]",
      "the divergence loss counts Omega only"),
+    # ------------------------------------------------------------------- a third pass
+    ("laser-other-segment", PY_LASER, "idx = np.array([grid.index.get((segment, int(a), int(b), int(c)), -1)",
+     "idx = np.array([grid.index.get((0, int(a), int(b), int(c)), -1)", "a scan fuses into its own segment"),
+    ("laser-key-order", PY_LASER, "key=lambda k: (k[0], k[3], k[2], k[1]))", "key=lambda k: (k[0], k[1], k[2], k[3]))",
+     "new blocks in (segment, bz, by, bx) order"),
+    ("estimate-alphas-swapped", PY_STEREO, "tgv_iterate(st, a, T, theta, prm.alpha1, prm.alpha2, prm.inner)",
+     "tgv_iterate(st, a, T, theta, prm.alpha2, prm.alpha1, prm.inner)", "Table I's alpha1 and alpha2"),
+    ("estimate-tensor-of-left", PY_STEREO, "T = diffusion_tensor(IR, prm.gamma, prm.beta)",
+     "T = diffusion_tensor(IL, prm.gamma, prm.beta)", "D4 the tensor of the reference image I_R"),
+    ("estimate-images-swapped", PY_STEREO, "sL, sR = census(IL), census(IR)", "sL, sR = census(IR), census(IL)",
+     "D1 I_L(x + d) against I_R(x)"),
+    ("assign-flags-everything", PY_STEREO, "flag |= close & (arg != k)", "flag |= close",
+     "D8 a near tie needs another candidate"),
+    ("surface-blocks-ignored", PY_SURFACE, "crossing &= np.repeat(chosen, BLOCK_VOXELS)", "crossing &= True",
+     "only the chosen blocks' cubes are meshed"),
+    ("targets-edges-reversed", PY_NET, "t[:, 3:6] = e.transpose(1, 0, 2)", "t[:, 3:6] = e.transpose(1, 0, 2)[:, ::-1]",
+     "target channels (u, Omega, div p, e_x, e_y, e_z)"),
+    ("inner-edges-shifted", PY_NET, "e[0][..., :-1] = om[..., :-1] & om[..., 1:]", "e[0][..., 1:] = om[..., :-1] & om[..., 1:]",
+     "Eq. 3 edge e_x(v) stored at v"),
+    ("c-key-order", C_DENSER, "if (a[3] != b[3]) return a[3] < b[3];", "if (a[3] != b[3]) return a[3] > b[3];",
+     "new blocks in (segment, bz, by, bx) order"),
+    ("c-band-step", C_DENSER, "const double h = 0.5 * m->s, bs = 8.0 * m->s;", "const double h = m->s, bs = 8.0 * m->s;",
+     "band samples half a voxel apart"),
+    ("c-row-centre", C_DENSER, "const double vv = ((double)y + 0.5) - cy;", "const double vv = (double)y - cy;",
+     "rays through pixel centres"),
+    ("c-back-edge", C_DENSER, "if (edge(m, nbr, vb / BV, (int)(vb % BV), a, &f2)) back = pa[vb];", "back = pa[vb];",
+     "Eq. 4 cases at the Omega boundary"),
+    ("c-face-carry", C_DENSER, "if ((dir > 0 && c < 7) || (dir < 0 && c > 0))", "if ((dir > 0 && c < 7) || (dir < 0 && c >= 0))",
+     "a step out of the block's low face"),
 ]
 
 RUNNER = r"""
@@ -339,7 +368,7 @@ def _run_case(case, workdir):
 @pytest.fixture(scope="module")
 def outcomes():
     with tempfile.TemporaryDirectory() as workdir:
-        with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as ex:
+        with ThreadPoolExecutor(max_workers=max(1, min(12, os.cpu_count() or 1))) as ex:
             res = list(ex.map(lambda c: _run_case(c, workdir), CASES))
     return {cid: (rc, tail) for cid, rc, tail in res}
 

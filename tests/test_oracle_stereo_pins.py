@@ -254,3 +254,30 @@ def test_synthetic_street_pair_against_ground_truth():
     v = dt > 0
     err = np.abs(d - dt)[v]
     assert np.median(err) < 0.02 and (err > 3).mean() < 0.03, (np.median(err), (err > 3).mean())
+
+
+def test_estimate_composes_the_pinned_stages():
+    """D5 as a schedule of the stages pinned above: winner-takes-all start from the
+    Census costs of (I_L, I_R), the tensor of the reference image I_R, then per outer
+    step an a-step at the current theta and `inner` d-step iterations with (alpha1,
+    alpha2) in that order, theta shrinking by theta_decay.  The recorded trace matches
+    the stages run one by one, bit for bit."""
+    rng = np.random.default_rng(6)
+    IR = smooth_texture(rng, (10, 24))
+    IL = smooth_texture(rng, (10, 24))
+    IL[:, 3:] = IR[:, :-3]
+    prm = S.StereoParams(max_disp=8, outer=3, inner=7, alpha1=0.7, alpha2=3.0, theta0=1.5, theta_decay=0.4)
+    trace = []
+    d = S.estimate(IL, IR, prm, trace=trace)
+    h = S.hamming_volume(S.census(IL), S.census(IR), prm.max_disp)
+    T = S.diffusion_tensor(IR, prm.gamma, prm.beta)
+    st = S.TGVState(np.argmin(h, axis=0).astype(np.float64))  # no coupling: first argmin
+    theta = prm.theta0
+    assert len(trace) == prm.outer
+    for th, a_got, d_got in trace:
+        assert th == theta
+        a = S.assign(h, st.d, prm.lam, theta)
+        S.tgv_iterate(st, a, T, theta, prm.alpha1, prm.alpha2, prm.inner)
+        assert np.array_equal(a_got, a) and np.array_equal(d_got, st.d)
+        theta *= prm.theta_decay
+    assert np.array_equal(d, st.d)

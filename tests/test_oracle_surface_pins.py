@@ -238,3 +238,20 @@ def test_zero_corner_is_non_negative():
     lower = ids // 8
     assert np.all(lower // 64 == 3)
     assert abs(S.mesh_area(pos) - (7 * s) ** 2) < 1e-10
+
+
+def test_blocks_partition_the_mesh():
+    """Meshing the blocks one call at a time (each call takes the cubes whose lower
+    corner lies in its block) gives the whole mesh's triangles, split by block, in the
+    same order."""
+    rng = np.random.default_rng(31)
+    s = 0.1
+    keys = box_keys(2, 2, 1)
+    u = rng.normal(0.1, 1.0, size=(len(keys), 512))
+    om = rng.random((len(keys), 512)) < 0.95
+    pos, ids = S.extract_surface(keys, u, om, s)
+    parts = [S.extract_surface(keys, u, om, s, blocks=[b]) for b in range(len(keys))]
+    assert sum(len(pp) for pp, _ in parts) == len(pos)
+    assert sum(len(pp) > 0 for pp, _ in parts) >= 3
+    assert np.array_equal(np.concatenate([pp for pp, _ in parts]), pos)
+    assert np.array_equal(np.concatenate([ii for _, ii in parts]), ids)
