@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle.denser_oracle import (BLOCK, Intrinsics, Params, SparseGrid, alloc_blocks,
-                                  frame_block_keys, fuse_depth, local_offsets)
+                                  frame_block_keys, fuse_depth, local_offsets, run_pipeline)
 
 P = Params()
 
@@ -259,3 +259,16 @@ def test_fuse_touches_its_own_segment_only():
     assert np.all(both.w[:n] == 0) and np.all(both.f[:n] == 0)
     assert np.array_equal(both.w[n:], alone.w) and np.array_equal(both.f[n:], alone.f)
     assert np.count_nonzero(alone.w) > 1000
+
+
+def test_pipeline_allocates_before_it_fuses():
+    """Section III-A takes each depth map through allocation and then fusion, so a single
+    map already observes the blocks it allocates: the pipeline of one wall map gives the
+    wall's closed-form field."""
+    K = Intrinsics(60.0, 60.0, 20.137, 15.291, 40, 30)
+    T = _pose(np.eye(3), (0.0123, 0.0071, 0.0037))
+    depth = np.full((K.height, K.width), 6.0, np.float32)
+    g = run_pipeline([depth], K, [T], P, 0)
+    ref = _fuse_one(depth, K, T)
+    assert g.keys == ref.keys and np.array_equal(g.w, ref.w) and np.array_equal(g.f, ref.f)
+    assert np.count_nonzero(g.w) > 1000

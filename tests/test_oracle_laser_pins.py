@@ -55,9 +55,11 @@ def test_ray_along_negative_x_closed_form():
     np.testing.assert_allclose(g.f.reshape(-1)[flat], np.minimum(1.0, usdf / 0.3), atol=2.0 ** -30)
 
 
-def test_axis_aligned_ray_closed_form():
+@pytest.mark.parametrize("r", [3.4567, 3.448])
+def test_axis_aligned_ray_closed_form(r):
+    """With r = 3.448 the last sample (n = M = 74, at z = t_z + 3.7) is the first one in
+    its voxel, whose centre is still within mu of the hit: the walk must reach it."""
     g = box_grid((-1, -1, -1), (1, 1, 8))
-    r = 3.4567
     cnt = L.fuse_scan(g, np.array([[0.0, 0.0, r]], np.float32), T0)
     flat = np.nonzero(cnt.reshape(-1))[0]
     c, ijk = voxel_centre(flat, g)

@@ -318,6 +318,25 @@ CASES = [
      "Eq. 4 cases at the Omega boundary"),
     ("c-face-carry", C_DENSER, "if ((dir > 0 && c < 7) || (dir < 0 && c > 0))", "if ((dir > 0 && c < 7) || (dir < 0 && c >= 0))",
      "a step out of the block's low face"),
+    # ------------------------------------------------------------------ a fourth pass
+    ("pipeline-fuse-first", PY_DENSER, """        alloc_blocks(grid, dm, K, T, segment)
+        fuse_depth(grid, dm, K, T, segment)""", """        fuse_depth(grid, dm, K, T, segment)
+        alloc_blocks(grid, dm, K, T, segment)""", "Section III-A: allocate, then fuse, per depth map"),
+    ("grid-index-off-by-one", PY_DENSER, "self.index[k] = len(self.keys)\n", "self.index[k] = len(self.keys) + 1\n",
+     "block b owns voxels b*512 .. b*512 + 511"),
+    ("laser-last-sample", PY_LASER, "rho = np.arange(M + 1, dtype=np.float64) * h", "rho = np.arange(M, dtype=np.float64) * h",
+     "L3 samples n = 0..M"),
+    ("conv-bias-dropped", PY_NET, "y = np.zeros((n, W.shape[0], D, H, Wd)) + b[None, :, None, None, None]",
+     "y = np.zeros((n, W.shape[0], D, H, Wd))", "the bias of each output channel"),
+    ("net-backward-offset", PY_NET, "dh[:, :, 1:-1, 1:-1, 1:-1] = dout", "dh[:, :, :-2, :-2, :-2] = dout",
+     "the loss reads the centre 8^3"),
+    ("tensor-apply-swapped", PY_STEREO, "T[1, 0] * v[0] + T[1, 1] * v[1]", "T[1, 0] * v[1] + T[1, 1] * v[0]",
+     "D4 T grad d"),
+    ("div-first-column", PY_STEREO, "dx[:, 0] = px[:, 0]", "dx[:, 0] = 0.0", "D7 div = -grad^T"),
+    ("c-energy-residual", C_DENSER, "const double r = m->u[v] - m->f[v];", "const double r = m->u[v] + m->f[v];",
+     "the data term (u - f)^2"),
+    ("c-dual-step-size", C_DENSER, "const double q0 = p0[v] + sg * g[0],", "const double q0 = p0[v] + g[0],",
+     "the dual step sigma"),
 ]
 
 RUNNER = r"""
