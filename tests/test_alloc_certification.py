@@ -58,6 +58,7 @@ class Setup:
         tb = T[:3, 3] / self.bs
         self.Ti = [int(max(-2.0 * COORD_BIAS, min(2.0 * COORD_BIAS, math.floor(v)))) for v in tb]
         self.tf = [f32(tb[r] - self.Ti[r]) for r in range(3)]
+        self.e_scale = F32(1)  # the kernel's bounds; 0 only to show the checks catch an unsound bound
 
 
 def ray_keys(S, x, y, dv):
@@ -68,7 +69,7 @@ def ray_keys(S, x, y, dv):
     va = F32(F32(F32(F32(y) + F32(0.5)) - S.cy_hi) - S.cy_lo)
     ax, ay = F32(ua * S.ifx), F32(va * S.ify)
     zmax, zmin = F32(dv + S.nhf), F32(dv - S.nhf)
-    ez = F32(eps * zmax + F32(1e-30))
+    ez = F32(F32(eps * zmax + F32(1e-30)) * S.e_scale)
     D, e = [], []
     for r in range(3):
         R0, R1, R2 = S.Rf[3 * r], S.Rf[3 * r + 1], S.Rf[3 * r + 2]
@@ -77,7 +78,7 @@ def ray_keys(S, x, y, dv):
         qm = max(abs(fma(zmin, D[r], S.tf[r])), abs(fma(zmax, D[r], S.tf[r])))
         if not qm < F32(2.0 ** 21):
             return None
-        e.append(fma(F32(1.25) * eps, F32(DA * F32(zmax + S.nhf)), F32(0.25) * eps * F32(qm + F32(1))))
+        e.append(F32(fma(F32(1.25) * eps, F32(DA * F32(zmax + S.nhf)), F32(0.25) * eps * F32(qm + F32(1))) * S.e_scale))
     keys = events_path(S, dv, D, e, ez)
     return keys if keys is not None else per_sample_path(S, dv, D, e, ez)
 
@@ -212,3 +213,21 @@ def test_samples_on_block_faces(est_ulps):
             pixels.append((60 + dx, 30 + dy))
             depths.append(F32(k * 0.05))
     check_rays(K, T, prm, pixels, np.array(depths, F32), 0.05, est_ulps)
+
+
+def test_the_block_faces_catch_an_unsound_bound():
+    """The face case has teeth: with no error bound (float32 floors taken as final) some
+    ray it decides gets a key set other than the oracle's."""
+    prm = O.Params()
+    K = O.Intrinsics(500.0, 500.0, 60.5, 30.5, 121, 61)
+    T = np.eye(4)
+    S = Setup(K, T, prm)
+    S.est_ulps = 0
+    S.e_scale = F32(0)
+    wrong = 0
+    for k in range(1, 60):
+        for dx, dy in ((0, 0), (1, 0), (0, 1), (-1, -1), (2, -3)):
+            x, y, dv = 60 + dx, 30 + dy, F32(k * 0.05)
+            got = ray_keys(S, x, y, dv)
+            wrong += got is not None and got != oracle_ray_keys(K, T, prm, x, y, dv)
+    assert wrong > 0

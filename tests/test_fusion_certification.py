@@ -86,11 +86,13 @@ def shared_bound(hi, lo, dl, M, sf, fxf, fyf, cxf, cyf, rcp_ulps):
     return (np.where(ok, F32(ex * up), F32(-1)).astype(F32), np.where(ok, F32(ey * up), F32(-1)).astype(F32))
 
 
-def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0), with_shared=False):
+def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0), with_shared=False, bound_scale=1.0):
     """The float32 path of the fusion kernel for every voxel of `keys`: (decided, update,
     u_tsdf) per voxel, each [nb, 512] (with_shared: also which blocks take the bound
     shared by their voxels).  rcp: the ulp offsets of the two reciprocals (1/z,
-    1/(z - dz)) from their correctly rounded values."""
+    1/(z - dz)) from their correctly rounded values.  bound_scale multiplies the pixel and
+    truncation bounds (1: the kernel's; 0 only to show that the checks below catch an
+    unsound bound)."""
     s = prm.voxel_size
     Ri, ti = O.pose_inverse(T)
     keys = np.asarray(keys, np.int64)
@@ -139,6 +141,7 @@ def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0), with_shared=False):
               + EPS23 * (np.abs(py) + np.abs(cyf)) + F32(1e-6)).astype(F32)
         ex = np.where(shared, ex_sh, ex).astype(F32)
         ey = np.where(shared, ey_sh, ey).astype(F32)
+        ex, ey = (ex * F32(bound_scale)).astype(F32), (ey * F32(bound_scale)).astype(F32)
         outside = front & (((px + ex) < 0) | ((px - ex) >= Wf) | ((py + ey) < 0) | ((py - ey) >= Hf))
         decided |= outside
         small = (ex < F32(2.0 ** 20)) & (ey < F32(2.0 ** 20))
@@ -150,6 +153,7 @@ def kernel_decisions(keys, depth, K, T, prm, rcp=(0, 0), with_shared=False):
         dh = (d - hi[2][:, None]).astype(F32)
         us = ((dh - m[2][None, :]) - lo[2][:, None]).astype(F32)
         eu = (EPS22 * (np.abs(dh) + np.abs(m[2][None, :]) + np.abs(us) + muf + s25) + dl + F32(1e-7)).astype(F32)
+        eu = (eu * F32(bound_scale)).astype(F32)
         cert = pix_ok & ~invalid & (np.abs(us + muf) > eu)
         decided |= cert
         upd |= cert & (us >= -muf)
@@ -255,3 +259,25 @@ def test_truncation_edges_are_deferred_or_right(rcp):
     np.testing.assert_array_equal(upd[decided], want[decided])
     both = decided & upd
     assert np.max(np.abs(ut[both].astype(np.float64) - g.f[both])) <= 2e-6
+
+
+def test_the_edge_cases_catch_an_unsound_bound():
+    """The checks above have teeth: with no error bound (float32 decisions taken as
+    final) the pixel-edge and truncation-edge cases certify decisions that differ from
+    the oracle's."""
+    prm, K, keys, g, zc, px, py = _lattice_case()
+    yy, xx = np.mgrid[0:K.height, 0:K.width]
+    depth = np.where((xx + yy) % 2 == 0, F32(20.0), F32(0.0)).astype(F32)
+    want = O.fuse_depth(g, depth, K, np.eye(4))
+    decided, upd, _ = kernel_decisions(keys, depth, K, np.eye(4), prm, bound_scale=0.0)
+    assert np.any(upd[decided] != want[decided])
+    rng = np.random.default_rng(7)
+    ok = (px >= 0) & (px < K.width) & (py >= 0) & (py < K.height)
+    depth = rng.uniform(0.3, 3.0, (K.height, K.width)).astype(F32)
+    for f in np.flatnonzero(ok.reshape(-1)):
+        b, v = divmod(int(f), 512)
+        depth[py[b, v], px[b, v]] = F32(zc[b, v] - prm.mu) + F32(rng.integers(-3, 4)) * F32(2.0 ** -22)
+    g2 = grid_from_blocks(keys)
+    want = O.fuse_depth(g2, depth, K, np.eye(4))
+    decided, upd, _ = kernel_decisions(keys, depth, K, np.eye(4), prm, bound_scale=0.0)
+    assert np.any(upd[decided] != want[decided])
