@@ -14,7 +14,9 @@ part of the paper or of a stated reading the change breaks.
 
 Changes that leave the method's result as it is are not cases: taking the other
 diagonal of a surface quadrilateral, say, meshes the same plane (u is linear on each
-tetrahedron), and updating u on Omega-bar changes nothing there (w = 0 and div p = 0).
+tetrahedron), updating u on Omega-bar changes nothing there (w = 0 and div p = 0), and
+the segment's place in the key order never shows (one allocation call adds keys of one
+segment).
 """
 
 import os
@@ -337,6 +339,16 @@ CASES = [
      "the data term (u - f)^2"),
     ("c-dual-step-size", C_DENSER, "const double q0 = p0[v] + sg * g[0],", "const double q0 = p0[v] + g[0],",
      "the dual step sigma"),
+    # ------------------------------------------------------------------- a fifth pass
+    ("surface-corner-axes", PY_SURFACE, "return (code & 1, (code >> 1) & 1, (code >> 2) & 1)",
+     "return ((code >> 2) & 1, (code >> 1) & 1, code & 1)", "S2 corner code bit a = axis a"),
+    ("div-interior-shift", PY_STEREO, "dx[:, 1:-1] = px[:, 1:-1] - px[:, :-2]", "dx[:, 1:-1] = px[:, 2:] - px[:, 1:-1]",
+     "D7 div = -grad^T (backward difference)"),
+    ("div-y-rows", PY_STEREO, "dy[1:-1, :] = py[1:-1, :] - py[:-2, :]", "dy[1:-1, :] = py[1:-1, :] - py[2:, :]",
+     "D7 div = -grad^T"),
+    ("census-bit-stride", PY_STEREO, "            b += 1\n", "            b += 2\n", "D2 62 distinct bits"),
+    ("c-sort-descending", C_DENSER, "return key_less(a, b) ? -1 : (key_less(b, a) ? 1 : 0);",
+     "return key_less(a, b) ? 1 : (key_less(b, a) ? -1 : 0);", "new blocks in ascending key order"),
 ]
 
 RUNNER = r"""
